@@ -1,0 +1,165 @@
+/*
+ * komega_gb300.h - C ABI of the GB300 shifted Krylov (shifted COCG) solver.
+ *
+ * Problem (Komega paper, arXiv:2001.08707, Sec. 1, Eq. 4-5):
+ *     (z_k I - H) x^(k) = b,   k = 0 .. nshift-1,
+ * with H real symmetric (M x M, CSR), b real, z_k complex.  The matrix
+ * z_k I - H is complex symmetric, so the method is shifted COCG (Table 1,
+ * Appendix A): one seed Krylov iteration (sparse H r, unconjugated dots,
+ * three-term recurrence Eq. 16-17) drives every shift through the
+ * collinearity factors pi_k (Eq. 19-22).  Outputs are the full x^(k)
+ * (Eq. 23-24) or only the projections a_l^T x^(k) (Eq. 25-26, Sec. 2.2.3),
+ * with seed switching after every update (Sec. 2.2.4).
+ *
+ * Conventions used by every call:
+ *   - "_dev" pointers are CUDA device pointers on the context's device; "_host"
+ *     pointers are ordinary host memory.  The caller owns every buffer passed
+ *     in and keeps it alive until the call returns.
+ *   - Complex vectors are interleaved (re, im): kw_c128 / double2 in KW_F64,
+ *     float2 (8 bytes) in KW_C32V_F64S.
+ *   - All device work is issued on the context's stream.  Calls that return
+ *     results return after synchronising that stream.
+ *   - Errors are status codes only.  No call exits, aborts or traps; a failed
+ *     call leaves the context usable.  kw_last_error() gives a message.
+ *   - A context is not thread-safe; separate contexts are independent.
+ */
+#ifndef KOMEGA_GB300_H
+#define KOMEGA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KW_ABI_VERSION 1
+/* Largest number of projection rows (b plus left vectors) in projected mode. */
+#define KW_MAX_PROJ 32
+
+typedef struct kw_ctx kw_ctx;
+
+typedef enum {
+    KW_OK = 0,
+    KW_ERR_ARG = 1,          /* invalid argument (null pointer, size, non-finite shift) */
+    KW_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    KW_ERR_OOM = 3,          /* device allocation failed */
+    KW_ERR_BREAKDOWN = 4,    /* rho_n = 0, zero alpha denominator (Eq. 17) or pi_{n+1} = 0 (Eq. 20) */
+    KW_ERR_NONFINITE = 5,    /* a seed scalar became Inf/NaN */
+    KW_ERR_CALLBACK = 6,     /* reserved: user matvec callback failure */
+    KW_ERR_TIMEOUT = 7,      /* reserved: bounded device wait expired */
+    KW_NOT_CONVERGED = 8     /* maxiter reached; outputs hold the last iterates */
+} kw_status;
+
+typedef enum {
+    KW_F64 = 0,         /* complex FP64 vectors, FP64 matrix values, FP64 scalars */
+    KW_C32V_F64S = 1    /* complex FP32 vectors and FP32 matrix values; dots
+                           accumulated in FP64 over FP32 chunk partials; every
+                           seed and shift scalar (alpha, beta, rho, pi) and the
+                           convergence test in FP64 */
+} kw_precision;
+
+typedef struct { double re, im; } kw_c128;
+
+typedef struct {
+    kw_precision prec;
+    double tol;          /* per shift: stop updating shift k once ||r_n|| / |pi_n^k| <= tol * ||b||
+                            (the convergence criterion of Sec. 3.2.2, read per shift and relative) */
+    int64_t maxiter;     /* seed iterations (matrix-vector products) at most */
+    int seed_switch;     /* 1: switch the seed after every update (Sec. 2.2.4); 0: fixed seed z_0 */
+    int64_t hist_stride; /* record the per-shift residual every hist_stride iterations (0 = never) */
+    int64_t hist_max;    /* records kept at most */
+} kw_options;
+
+typedef struct {
+    int64_t iters;          /* seed iterations performed */
+    int64_t n_converged;    /* shifts that met the tolerance */
+    double max_res;         /* max over shifts of the last residual estimate ||r||/|pi| */
+    int64_t n_seed_switch;  /* seed switches performed */
+    int64_t updates;        /* sum over iterations of the active shift count; x M = shift-row updates */
+    int64_t seed;           /* index of the seed shift at exit */
+    kw_status status;
+} kw_solve_info;
+
+/* ABI version of the loaded library (KW_ABI_VERSION it was built with). */
+int kw_abi_version(void);
+
+/* Fill *opt with defaults: KW_F64, tol 1e-10, maxiter 100000, seed_switch 1,
+ * hist_stride 0, hist_max 0. */
+void kw_default_options(kw_options* opt);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* kw_status_string(kw_status s);
+
+/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) on which all work is issued.  Errors:
+ * KW_ERR_ARG (out or opt NULL, tol < 0, maxiter < 1, hist_stride < 0, bad
+ * precision), KW_ERR_CUDA. */
+kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream);
+
+/* Release the context and every device buffer it owns.  NULL is ignored. */
+void kw_destroy(kw_ctx* ctx);
+
+/* Copy the last error message (NUL-terminated, truncated to n) into buf. */
+kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
+
+/* Set the operator H (real symmetric, M x M) as a device CSR matrix:
+ * rowptr_dev int64 [m+1] (rowptr[0] = 0, nondecreasing, rowptr[m] = nnz),
+ * col_dev int32 [nnz] in [0, m), val_dev float64 [nnz].  The pointers are
+ * borrowed in KW_F64 mode (they must stay valid until the next kw_set_csr or
+ * kw_destroy); in KW_C32V_F64S mode the context keeps its own FP32 copy of the
+ * values.  Symmetry is the caller's promise and is not checked.  Errors:
+ * KW_ERR_ARG (m < 1, nnz < 0, nnz >= 2^31, NULL pointer), KW_ERR_OOM. */
+kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev,
+                     const int32_t* col_dev, const double* val_dev);
+
+/* Solve (z_k I - H) x_k = b for all nshift shifts (Eq. 4) by shifted COCG.
+ *   b_dev       float64 [m], real right-hand side (||b|| > 0).
+ *   z_host      kw_c128 [nshift], finite shifts; the initial seed is z_0 (Eq. 6).
+ *   nleft       number of left vectors a_l (0 .. KW_MAX_PROJ-1).
+ *   left_dev    float64 [nleft][m] row-major, or NULL when nleft = 0.
+ *   x_out_dev   full mode: [nshift][m] complex in the context precision
+ *               (kw_c128 for KW_F64, float2 for KW_C32V_F64S), receives x_k.
+ *               NULL selects projected mode (Eq. 25-26): no x_k is formed.
+ *   proj_out_host kw_c128 [nshift][nleft+1] or NULL; column 0 = b^T x_k,
+ *               column l = a_{l-1}^T x_k (a real, so a^dagger = a^T).
+ *   info        optional summary.
+ * Returns KW_OK when every shift met the tolerance, KW_NOT_CONVERGED at
+ * maxiter (outputs then hold the last iterates), KW_ERR_BREAKDOWN /
+ * KW_ERR_NONFINITE with the outputs of the last completed iteration, or an
+ * argument/CUDA error.  kw_set_csr must have been called. */
+kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host,
+                   int64_t nleft, const double* left_dev, void* x_out_dev,
+                   kw_c128* proj_out_host, kw_solve_info* info);
+
+/* kw_solve with every array in host memory: copies H (CSR as in kw_set_csr),
+ * b and the left vectors to the device, solves, and copies x (if x_out_host is
+ * not NULL; same layout as x_out_dev) and the projections back.  The device
+ * copies are owned by the context and reused by later calls. */
+kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_host,
+                        const int32_t* col_host, const double* val_host, const double* b_host,
+                        int64_t nshift, const kw_c128* z_host, int64_t nleft,
+                        const double* left_host, void* x_out_host, kw_c128* proj_out_host,
+                        kw_solve_info* info);
+
+/* Per-shift results of the last solve: the iteration at which shift k met the
+ * tolerance (-1 if never) and its last residual estimate ||r_n||/|pi_n^k|.
+ * Either pointer may be NULL.  Arrays have the last solve's nshift entries. */
+kw_status kw_get_shift_status(kw_ctx* ctx, int64_t* conv_iter_host, double* final_res_host);
+
+/* Residual history of the last solve: *n_rec records of nshift doubles,
+ * record i taken after iteration (i+1)*hist_stride.  hist_host may be NULL to
+ * query *n_rec; otherwise it must hold hist_max * nshift doubles. */
+kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec);
+
+/* One seed matrix-vector step (Alg. 1 "q = H r" combined with the seed shift,
+ * and the first dot of Eq. 17): q = zs r - H r and t = r^T q (unconjugated),
+ * with the context's operator and precision.  r_dev, q_dev: [m] complex in the
+ * context precision; t_host receives the FP64 dot. */
+kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KOMEGA_GB300_H */

@@ -1,0 +1,460 @@
+// C ABI and host driver of the shifted COCG solver (see include/komega_gb300.h).
+//
+// The driver validates arguments, sizes the device workspace (kept across
+// calls), uploads the shifts and the initial state, enqueues the iteration
+// kernels in chunks and polls the device stop flag one chunk behind, so the
+// GPU always has the next chunk queued.  Iterations enqueued after the stop
+// flag is set return at their first instruction.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "komega_gb300.h"
+#include "kw_internal.cuh"
+
+namespace {
+
+// Device buffer that only grows.
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct kw_ctx {
+  kw_options opt;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  char err[512];
+  // operator
+  int64_t m = 0, nnz = 0;
+  const int64_t* rowptr = nullptr;
+  const int32_t* col = nullptr;
+  const double* val = nullptr;
+  DBuf val32;
+  // host-solve copies
+  DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
+  // workspace
+  DBuf rA, rB, q, proj_rows, z, pi1, pi0, active, conv_iter, final_res, coef, Y, U, w, w0, hist, list, X, P,
+      part, st, projx, tdot;
+  kw::State* st_host = nullptr;   // pinned
+  int* flags_host = nullptr;      // pinned, two slots
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // last solve
+  int64_t last_K = 0;
+  int64_t last_nrec = 0;
+};
+
+static kw_status fail(kw_ctx* c, kw_status s, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+static kw_status cuda_fail(kw_ctx* c, cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) return fail(c, KW_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(c, KW_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define KW_CUDA(call, where)                          \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+static int pick_lanes(int64_t m, int64_t nnz) {
+  const double avg = m > 0 ? (double)nnz / (double)m : 1.0;
+  int g = 2;
+  while (g < 32 && g * 2 <= avg) g *= 2;   // about two non-zeros per lane
+  return g;
+}
+
+extern "C" {
+
+int kw_abi_version(void) { return KW_ABI_VERSION; }
+
+void kw_default_options(kw_options* opt) {
+  if (!opt) return;
+  opt->prec = KW_F64;
+  opt->tol = 1e-10;
+  opt->maxiter = 100000;
+  opt->seed_switch = 1;
+  opt->hist_stride = 0;
+  opt->hist_max = 0;
+}
+
+const char* kw_status_string(kw_status s) {
+  switch (s) {
+    case KW_OK: return "KW_OK";
+    case KW_ERR_ARG: return "KW_ERR_ARG";
+    case KW_ERR_CUDA: return "KW_ERR_CUDA";
+    case KW_ERR_OOM: return "KW_ERR_OOM";
+    case KW_ERR_BREAKDOWN: return "KW_ERR_BREAKDOWN";
+    case KW_ERR_NONFINITE: return "KW_ERR_NONFINITE";
+    case KW_ERR_CALLBACK: return "KW_ERR_CALLBACK";
+    case KW_ERR_TIMEOUT: return "KW_ERR_TIMEOUT";
+    case KW_NOT_CONVERGED: return "KW_NOT_CONVERGED";
+  }
+  return "KW_UNKNOWN";
+}
+
+kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
+  if (!out || !opt) return KW_ERR_ARG;
+  *out = nullptr;
+  if (!(opt->tol >= 0.0) || opt->maxiter < 1 || opt->hist_stride < 0 || opt->hist_max < 0 ||
+      (opt->prec != KW_F64 && opt->prec != KW_C32V_F64S))
+    return KW_ERR_ARG;
+  kw_ctx* ctx = new kw_ctx();
+  ctx->opt = *opt;
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->err[0] = 0;
+  cudaError_t e = cudaGetDevice(&ctx->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->st_host, sizeof(kw::State));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->flags_host, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev[0], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev[1], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    kw_destroy(ctx);
+    return KW_ERR_CUDA;
+  }
+  *out = ctx;
+  return KW_OK;
+}
+
+void kw_destroy(kw_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  DBuf* bufs[] = {&ctx->val32, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
+                  &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
+                  &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
+                  &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot};
+  for (DBuf* b : bufs) b->release();
+  if (ctx->st_host) cudaFreeHost(ctx->st_host);
+  if (ctx->flags_host) cudaFreeHost(ctx->flags_host);
+  for (int i = 0; i < 2; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  delete ctx;
+}
+
+kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n) {
+  if (!ctx || !buf || n == 0) return KW_ERR_ARG;
+  snprintf(buf, n, "%s", ctx->err);
+  return KW_OK;
+}
+
+kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev, const int32_t* col_dev,
+                     const double* val_dev) {
+  if (!ctx) return KW_ERR_ARG;
+  if (m < 1 || m > 0x7fffffffLL || nnz < 0 || nnz > 0x7fffffffLL || !rowptr_dev ||
+      (nnz > 0 && (!col_dev || !val_dev)))
+    return fail(ctx, KW_ERR_ARG, "kw_set_csr: need 1 <= m < 2^31, 0 <= nnz < 2^31 and non-NULL arrays");
+  ctx->m = m;
+  ctx->nnz = nnz;
+  ctx->rowptr = rowptr_dev;
+  ctx->col = col_dev;
+  ctx->val = val_dev;
+  if (ctx->opt.prec == KW_C32V_F64S && nnz > 0) {
+    KW_CUDA(ctx->val32.ensure((size_t)nnz * sizeof(float)), "kw_set_csr: FP32 value copy");
+    KW_CUDA(kw::launch_convert_f64_to_f32(val_dev, (float*)ctx->val32.p, nnz, ctx->stream), "kw_set_csr: convert");
+  }
+  return KW_OK;
+}
+
+}  // extern "C"
+
+// Allocate the workspace of one solve and fill the Work descriptor.
+static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t K, const kw_c128* z_host,
+                         int64_t nleft, const double* left_dev, void* x_out_dev) {
+  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
+  const size_t vs = c32 ? 8 : 16, rs = c32 ? 4 : 8;
+  const int64_t m = ctx->m;
+  memset(&w, 0, sizeof(w));
+  w.prec = c32 ? kw::PREC_C32 : kw::PREC_F64;
+  w.m = m;
+  w.K = (int)K;
+  w.full = x_out_dev != nullptr;
+  w.nout = (int)nleft + 1;
+  w.nproj = w.full ? 0 : (int)nleft + 1;
+  w.tol = ctx->opt.tol;
+  w.rowptr = ctx->rowptr;
+  w.col = ctx->col;
+  w.val = c32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
+  w.spmv_lanes = pick_lanes(m, ctx->nnz);
+  w.b = b_dev;
+  w.left = left_dev;
+  w.stream = ctx->stream;
+  w.num_sms = ctx->num_sms;
+  w.nblk_spmv = 8 * ctx->num_sms;
+  w.nblk_seed = 2 * ctx->num_sms;
+  w.nblk_shift = (int)((K + 63) / 64);
+  w.nblk_xp = 8 * ctx->num_sms;
+
+  const int npw = std::max(w.nproj, 1);
+  const int64_t nrecmax = ctx->opt.hist_stride > 0 ? ctx->opt.hist_max : 0;
+  const size_t part_d = std::max<size_t>({(size_t)w.nblk_spmv * 2, (size_t)w.nblk_seed * (3 + 2 * KW_MAX_PROJ),
+                                          (size_t)w.nblk_shift * 4, (size_t)4 * ctx->num_sms * (KW_MAX_PROJ + 1)});
+  const size_t Ks = (size_t)K, Ms = (size_t)m;
+  struct {
+    DBuf* b;
+    size_t bytes;
+  } plan[] = {
+      {&ctx->rA, Ms * vs},
+      {&ctx->rB, Ms * vs},
+      {&ctx->q, Ms * vs},
+      {&ctx->proj_rows, (size_t)std::max(w.nproj, 1) * Ms * rs},
+      {&ctx->z, Ks * 16},
+      {&ctx->pi1, Ks * 16},
+      {&ctx->pi0, Ks * 16},
+      {&ctx->active, Ks * 4},
+      {&ctx->conv_iter, Ks * 8},
+      {&ctx->final_res, Ks * 8},
+      {&ctx->coef, Ks * 48},
+      {&ctx->Y, Ks * npw * 16},
+      {&ctx->U, Ks * npw * 16},
+      {&ctx->w, (size_t)KW_MAX_PROJ * 16},
+      {&ctx->w0, (size_t)KW_MAX_PROJ * 16},
+      {&ctx->hist, std::max<size_t>((size_t)nrecmax * Ks, 1) * 8},
+      {&ctx->list, Ks * 4},
+      {&ctx->P, w.full ? Ks * Ms * vs : 16},
+      {&ctx->part, part_d * 8},
+      {&ctx->st, sizeof(kw::State)},
+      {&ctx->projx, Ks * w.nout * 16},
+  };
+  for (auto& pl : plan) KW_CUDA(pl.b->ensure(pl.bytes), "workspace allocation");
+  w.rA = ctx->rA.p;
+  w.rB = ctx->rB.p;
+  w.q = ctx->q.p;
+  w.proj_rows = ctx->proj_rows.p;
+  w.z = (double2*)ctx->z.p;
+  w.pi1 = (double2*)ctx->pi1.p;
+  w.pi0 = (double2*)ctx->pi0.p;
+  w.active = (int*)ctx->active.p;
+  w.conv_iter = (long long*)ctx->conv_iter.p;
+  w.final_res = (double*)ctx->final_res.p;
+  w.coef = (double2*)ctx->coef.p;
+  w.Y = (double2*)ctx->Y.p;
+  w.U = (double2*)ctx->U.p;
+  w.w = (double2*)ctx->w.p;
+  w.w0 = (double2*)ctx->w0.p;
+  w.hist = (double*)ctx->hist.p;
+  w.list = (int*)ctx->list.p;
+  w.X = x_out_dev;
+  w.P = ctx->P.p;
+  w.part = (double*)ctx->part.p;
+  w.st = (kw::State*)ctx->st.p;
+
+  KW_CUDA(cudaMemcpyAsync(w.z, z_host, K * 16, cudaMemcpyHostToDevice, ctx->stream), "upload shifts");
+  kw::State& s = *ctx->st_host;
+  memset(&s, 0, sizeof(s));
+  s.zs = make_double2(z_host[0].re, z_host[0].im);
+  s.boa = make_double2(0.0, 0.0);
+  s.scale_rn = s.scale_rnm1 = make_double2(1.0, 0.0);
+  s.seed = 0;
+  s.seed_switch = ctx->opt.seed_switch ? 1 : 0;
+  s.status = KW_NOT_CONVERGED;
+  s.n_active = (int)K;
+  s.maxiter = ctx->opt.maxiter;
+  s.hist_stride = ctx->opt.hist_stride;
+  s.hist_max = nrecmax;
+  KW_CUDA(cudaMemcpyAsync(w.st, &s, sizeof(s), cudaMemcpyHostToDevice, ctx->stream), "upload state");
+  return KW_OK;
+}
+
+template <int P>
+static kw_status run(kw_ctx* ctx, kw::Work& w) {
+  KW_CUDA(kw::launch_init<P>(w), "init kernels");
+  const int CH = 16;
+  int64_t launched = 0;
+  int slot = 0;
+  bool have_prev = false;
+  for (;;) {
+    for (int i = 0; i < CH; ++i) {
+      KW_CUDA(kw::launch_iteration<P>(w, (int)(launched & 1)), "iteration launch");
+      ++launched;
+    }
+    KW_CUDA(cudaMemcpyAsync(ctx->flags_host + slot, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+            "flag copy");
+    KW_CUDA(cudaEventRecord(ctx->ev[slot], ctx->stream), "event record");
+    if (have_prev) {
+      KW_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]), "event sync");
+      if (ctx->flags_host[slot ^ 1]) break;
+    }
+    have_prev = true;
+    slot ^= 1;
+    if (launched > ctx->opt.maxiter + 2 * CH) break;   // the device stops at maxiter; never loop forever
+  }
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
+  return KW_OK;
+}
+
+extern "C" {
+
+kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
+                   const double* left_dev, void* x_out_dev, kw_c128* proj_out_host, kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_solve: kw_set_csr has not been called");
+  if (!b_dev || !z_host || nshift < 1 || nshift > 0x7fffffffLL)
+    return fail(ctx, KW_ERR_ARG, "kw_solve: need b, z and 1 <= nshift < 2^31");
+  if (nleft < 0 || nleft >= KW_MAX_PROJ || (nleft > 0 && !left_dev))
+    return fail(ctx, KW_ERR_ARG, "kw_solve: need 0 <= nleft < %d and left vectors when nleft > 0", KW_MAX_PROJ);
+  for (int64_t k = 0; k < nshift; ++k)
+    if (!isfinite(z_host[k].re) || !isfinite(z_host[k].im))
+      return fail(ctx, KW_ERR_ARG, "kw_solve: shift %lld is not finite", (long long)k);
+  kw::Work w;
+  kw_status s = prepare(ctx, w, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
+  if (s != KW_OK) return s;
+  s = (w.prec == kw::PREC_C32) ? run<kw::PREC_C32>(ctx, w) : run<kw::PREC_F64>(ctx, w);
+  if (s != KW_OK) return s;
+  KW_CUDA(cudaMemcpy(ctx->st_host, w.st, sizeof(kw::State), cudaMemcpyDeviceToHost), "read state");
+  const kw::State& st = *ctx->st_host;
+  ctx->last_K = nshift;
+  ctx->last_nrec = st.n_rec;
+  if (proj_out_host) {
+    if (w.full) {
+      cudaError_t e = (w.prec == kw::PREC_C32) ? kw::launch_project_x<kw::PREC_C32>(w, (double2*)ctx->projx.p)
+                                                : kw::launch_project_x<kw::PREC_F64>(w, (double2*)ctx->projx.p);
+      KW_CUDA(e, "projection of x");
+      KW_CUDA(cudaMemcpyAsync(proj_out_host, ctx->projx.p, (size_t)nshift * w.nout * 16, cudaMemcpyDeviceToHost,
+                              ctx->stream), "copy projections");
+    } else {
+      KW_CUDA(cudaMemcpyAsync(proj_out_host, w.Y, (size_t)nshift * w.nout * 16, cudaMemcpyDeviceToHost, ctx->stream),
+              "copy projections");
+    }
+    KW_CUDA(cudaStreamSynchronize(ctx->stream), "projection sync");
+  }
+  if (info) {
+    std::vector<double> res(nshift);
+    std::vector<long long> ci(nshift);
+    KW_CUDA(cudaMemcpy(res.data(), w.final_res, nshift * 8, cudaMemcpyDeviceToHost), "read residuals");
+    KW_CUDA(cudaMemcpy(ci.data(), w.conv_iter, nshift * 8, cudaMemcpyDeviceToHost), "read convergence");
+    info->iters = st.iter;
+    info->n_seed_switch = st.n_seed_switch;
+    info->updates = st.updates;
+    info->seed = st.seed;
+    info->status = (kw_status)st.status;
+    int64_t nc = 0;
+    double mx = 0.0;
+    for (int64_t k = 0; k < nshift; ++k) {
+      nc += ci[k] >= 0;
+      mx = std::max(mx, res[k]);
+    }
+    info->n_converged = nc;
+    info->max_res = mx;
+  }
+  if (st.status != KW_OK) {
+    fail(ctx, (kw_status)st.status, "kw_solve: %s after %lld iterations", kw_status_string((kw_status)st.status),
+         (long long)st.iter);
+  }
+  return (kw_status)st.status;
+}
+
+kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_host, const int32_t* col_host,
+                        const double* val_host, const double* b_host, int64_t nshift, const kw_c128* z_host,
+                        int64_t nleft, const double* left_host, void* x_out_host, kw_c128* proj_out_host,
+                        kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  if (m < 1 || nnz < 0 || !rowptr_host || (nnz > 0 && (!col_host || !val_host)) || !b_host || nshift < 1 ||
+      nleft < 0 || (nleft > 0 && !left_host))
+    return fail(ctx, KW_ERR_ARG, "kw_solve_host: invalid sizes or NULL host arrays");
+  const size_t vs = ctx->opt.prec == KW_C32V_F64S ? 8 : 16;
+  KW_CUDA(ctx->h_rowptr.ensure((m + 1) * 8), "alloc rowptr");
+  KW_CUDA(ctx->h_col.ensure(std::max<int64_t>(nnz, 1) * 4), "alloc col");
+  KW_CUDA(ctx->h_val.ensure(std::max<int64_t>(nnz, 1) * 8), "alloc val");
+  KW_CUDA(ctx->h_b.ensure(m * 8), "alloc b");
+  KW_CUDA(ctx->h_left.ensure(std::max<int64_t>(nleft * m, 1) * 8), "alloc left");
+  if (x_out_host) KW_CUDA(ctx->h_x.ensure((size_t)nshift * m * vs), "alloc x");
+  cudaStream_t s = ctx->stream;
+  KW_CUDA(cudaMemcpyAsync(ctx->h_rowptr.p, rowptr_host, (m + 1) * 8, cudaMemcpyHostToDevice, s), "copy rowptr");
+  if (nnz > 0) {
+    KW_CUDA(cudaMemcpyAsync(ctx->h_col.p, col_host, nnz * 4, cudaMemcpyHostToDevice, s), "copy col");
+    KW_CUDA(cudaMemcpyAsync(ctx->h_val.p, val_host, nnz * 8, cudaMemcpyHostToDevice, s), "copy val");
+  }
+  KW_CUDA(cudaMemcpyAsync(ctx->h_b.p, b_host, m * 8, cudaMemcpyHostToDevice, s), "copy b");
+  if (nleft > 0) KW_CUDA(cudaMemcpyAsync(ctx->h_left.p, left_host, nleft * m * 8, cudaMemcpyHostToDevice, s), "copy left");
+  kw_status st = kw_set_csr(ctx, m, nnz, (const int64_t*)ctx->h_rowptr.p, (const int32_t*)ctx->h_col.p,
+                            (const double*)ctx->h_val.p);
+  if (st != KW_OK) return st;
+  st = kw_solve(ctx, (const double*)ctx->h_b.p, nshift, z_host, nleft, nleft > 0 ? (const double*)ctx->h_left.p : nullptr,
+                x_out_host ? ctx->h_x.p : nullptr, proj_out_host, info);
+  if (x_out_host && (st == KW_OK || st == KW_NOT_CONVERGED || st == KW_ERR_BREAKDOWN || st == KW_ERR_NONFINITE))
+    KW_CUDA(cudaMemcpy(x_out_host, ctx->h_x.p, (size_t)nshift * m * vs, cudaMemcpyDeviceToHost), "copy x");
+  return st;
+}
+
+kw_status kw_get_shift_status(kw_ctx* ctx, int64_t* conv_iter_host, double* final_res_host) {
+  if (!ctx) return KW_ERR_ARG;
+  if (ctx->last_K == 0) return fail(ctx, KW_ERR_ARG, "kw_get_shift_status: no solve yet");
+  if (conv_iter_host)
+    KW_CUDA(cudaMemcpy(conv_iter_host, ctx->conv_iter.p, ctx->last_K * 8, cudaMemcpyDeviceToHost), "read conv_iter");
+  if (final_res_host)
+    KW_CUDA(cudaMemcpy(final_res_host, ctx->final_res.p, ctx->last_K * 8, cudaMemcpyDeviceToHost), "read final_res");
+  return KW_OK;
+}
+
+kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec) {
+  if (!ctx || !n_rec) return KW_ERR_ARG;
+  *n_rec = ctx->last_nrec;
+  if (hist_host && ctx->last_nrec > 0)
+    KW_CUDA(cudaMemcpy(hist_host, ctx->hist.p, (size_t)ctx->last_nrec * ctx->last_K * 8, cudaMemcpyDeviceToHost),
+            "read history");
+  return KW_OK;
+}
+
+kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host) {
+  if (!ctx) return KW_ERR_ARG;
+  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: kw_set_csr has not been called");
+  if (!r_dev || !q_dev || !t_host) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: NULL pointer");
+  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
+  kw::Work w;
+  memset(&w, 0, sizeof(w));
+  w.prec = c32 ? kw::PREC_C32 : kw::PREC_F64;
+  w.m = ctx->m;
+  w.rowptr = ctx->rowptr;
+  w.col = ctx->col;
+  w.val = c32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
+  w.spmv_lanes = pick_lanes(ctx->m, ctx->nnz);
+  w.stream = ctx->stream;
+  w.num_sms = ctx->num_sms;
+  w.nblk_spmv = 8 * ctx->num_sms;
+  KW_CUDA(ctx->part.ensure(std::max<size_t>(ctx->part.cap, (size_t)w.nblk_spmv * 2 * 8)), "alloc partials");
+  KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "alloc state");
+  KW_CUDA(ctx->tdot.ensure(16), "alloc dot");
+  w.part = (double*)ctx->part.p;
+  w.st = (kw::State*)ctx->st.p;
+  KW_CUDA(cudaMemsetAsync(&w.st->cnt_spmv, 0, sizeof(unsigned int), ctx->stream), "reset counter");
+  const double2 z2 = make_double2(zs.re, zs.im);
+  cudaError_t e = c32 ? kw::launch_spmv_dot<kw::PREC_C32>(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p)
+                      : kw::launch_spmv_dot<kw::PREC_F64>(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p);
+  KW_CUDA(e, "kw_spmv_dot launch");
+  KW_CUDA(cudaMemcpyAsync(t_host, ctx->tdot.p, 16, cudaMemcpyDeviceToHost, ctx->stream), "read dot");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_spmv_dot sync");
+  return KW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal definitions shared by the kernels and the host driver.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "komega_gb300.h"
+
+namespace kw {
+
+// Iteration state kept in device memory for the whole solve.  Every scalar of
+// the seed recurrence (Eq. 16-17) and of the seed switch lives here in FP64,
+// in both precision modes.
+struct State {
+  double2 zs;        // current seed shift z_s (Eq. 6)
+  double2 rho;       // rho_n = r_n^T r_n (unconjugated, Appendix A)
+  double2 rho1;      // rho_{n+1}
+  double2 boa;       // beta_{n-1} / alpha_{n-1}
+  double2 alpha;     // alpha_n (Eq. 17)
+  double2 c;         // alpha_n beta_{n-1} / alpha_{n-1}
+  double2 beta;      // beta_n = rho_{n+1} / rho_n
+  double2 t;         // r_n^T A r_n
+  double nu;         // ||r_{n+1}||_2^2
+  double thresh;     // tol * ||b||
+  double norm_b;
+  // Lazy seed switch: the stored r_n / r_{n-1} are still in the old seed's
+  // normalisation; the next K1/K2 multiply them by these factors and K2 writes
+  // the rescaled r_n back.
+  double2 scale_rn, scale_rnm1;
+  double2 inv_pj1, inv_pj0;  // 1/pi^j_{n+1}, 1/pi^j_n for the lazy pi rescale in K3
+  int vec_scale_pending;
+  int pi_rescale_pending;
+  int new_seed;
+  int seed;
+  int seed_switch;
+  int done;
+  int status;
+  int n_active;
+  int n_list;        // shifts processed in the current iteration (compacted list length)
+  int xp_pending;    // full-mode x/p update of the current iteration not yet applied
+  int n_seed_switch;
+  int pad0;
+  long long iter, maxiter, updates;
+  long long hist_stride, hist_max, n_rec;
+  unsigned int cnt_spmv, cnt_seed, cnt_shift, cnt_xp, cnt_init;
+  unsigned int pad1;
+};
+
+enum Prec { PREC_F64 = 0, PREC_C32 = 1 };
+
+// Device buffers of one solve.  Vector buffers are void* and typed by precision.
+struct Work {
+  int prec;
+  int64_t m;
+  int K;           // shifts
+  int nproj;       // projection rows used by the iteration incl. b (0 in full mode)
+  int nout;        // output columns: b plus the left vectors
+  double tol;
+  bool full;
+  // operator
+  const int64_t* rowptr;
+  const int32_t* col;
+  const void* val;   // double* (F64) or float* (C32)
+  int spmv_lanes;    // lanes per row in K1
+  // seed vectors
+  void* rA;          // two rotating residual buffers and q
+  void* rB;
+  void* q;
+  const double* b;   // caller's b (FP64)
+  const double* left;  // caller's left vectors (FP64) [nproj-1][m]
+  void* proj_rows;   // [nproj][m] real, vector precision (b then left vectors)
+  // shift state
+  double2* z;
+  double2* pi1;      // pi_n
+  double2* pi0;      // pi_{n-1}
+  int* active;
+  long long* conv_iter;
+  double* final_res;
+  double2* coef;     // full mode: [K][3] = alpha^k, beta^k, 1/pi^k_{n+1}
+  double2* Y;        // projected: [K][nproj]
+  double2* U;
+  double2* w;        // [nproj] = P r_{n+1}
+  double2* w0;       // [nproj] = P b
+  double* hist;
+  int* list;
+  void* X;           // full mode [K][m]
+  void* P;           // full mode [K][m]
+  // reduction scratch
+  double* part;
+  int nblk_spmv, nblk_seed, nblk_shift, nblk_xp;
+  State* st;
+  cudaStream_t stream;
+  int num_sms;
+};
+
+// Launchers implemented per precision (kw_kernels_f64.cu / kw_kernels_c32.cu).
+template <int P> cudaError_t launch_init(Work& w);
+template <int P> cudaError_t launch_iteration(Work& w, int parity);
+template <int P> cudaError_t launch_project_x(Work& w, double2* out);
+template <int P> cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, double2* t_dev);
+cudaError_t launch_convert_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+
+// Scratch needed by the reduction kernels (doubles).
+int64_t part_doubles(const Work& w);
+void choose_grids(Work& w);
+
+}  // namespace kw

@@ -1,0 +1,774 @@
+// Kernels of one shifted-COCG iteration (Komega paper, Sec. 2.2, Appendix A).
+//
+//   K1 k_spmv_dot     q = A r_n = z_s r_n - H r_n and t_n = r_n^T q (Alg. 1 "q = H r",
+//                     Eq. 17); last block: alpha_n, c_n = alpha_n beta_{n-1}/alpha_{n-1}.
+//   K2 k_seed_update  r_{n+1} = (1+c_n) r_n - alpha_n q - c_n r_{n-1} (Eq. 16), with
+//                     rho_{n+1} = r^T r, nu = r^dagger r and w_l = a_l^T r_{n+1} (the
+//                     P r_{n+1} of Eq. 26); last block: beta_n = rho_{n+1}/rho_n.
+//   K3 k_shift        per active shift: pi_{n+1} (Eq. 20), alpha^k, beta^k (Eq. 21-22),
+//                     projected y/u update (Eq. 25-26), residual ||r||/|pi|, freeze,
+//                     compaction; last block: seed switch (Sec. 2.2.4), stop flag.
+//   K4 k_update_xp    full mode: x^k += alpha^k p^k; p^k = r_{n+1}/pi^k + beta^k p^k
+//                     (Eq. 23-24) for the compacted active shifts.
+//
+// Every kernel reads the iteration state from device memory, so the host only
+// enqueues launches; no host synchronisation happens inside the loop.
+// Reductions are deterministic: fixed per-block partials summed in a fixed
+// order by the last block to finish (arrival counter, no spin-wait).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "kw_internal.cuh"
+
+namespace kw {
+
+#define KW_FULL_MASK 0xffffffffu
+
+template <int P> struct PT;
+template <> struct PT<PREC_F64> {
+  typedef double2 V;   // complex vector element
+  typedef double R;    // matrix value / projection row element
+  typedef double A;    // in-block accumulator
+  static const int CHUNK = 1 << 30;  // no chunking needed in FP64
+};
+template <> struct PT<PREC_C32> {
+  typedef float2 V;
+  typedef float R;
+  typedef float A;
+  static const int CHUNK = 16;       // FP32 partial over at most 16 terms per lane
+};
+
+// ---------------------------------------------------------------- complex helpers
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+template <class V> __device__ __forceinline__ V vmake(double2 a);
+template <> __device__ __forceinline__ double2 vmake<double2>(double2 a) { return a; }
+template <> __device__ __forceinline__ float2 vmake<float2>(double2 a) {
+  return make_float2((float)a.x, (float)a.y);
+}
+template <class V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+
+// Complex division a/b in FP64 (Smith's algorithm).
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  if (fabs(b.x) >= fabs(b.y)) {
+    double r = b.y / b.x, d = b.x + b.y * r;
+    return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+  } else {
+    double r = b.x / b.y, d = b.x * r + b.y;
+    return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+  }
+}
+__device__ __forceinline__ double2 crecip(double2 b) { return cdiv(make_double2(1.0, 0.0), b); }
+__device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// ---------------------------------------------------------------- reductions
+template <class T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(KW_FULL_MASK, v, off);
+  return v;
+}
+
+// Sum N per-thread values over the block (FP32 or FP64 warp tree, then the
+// warps combined in FP64 in a fixed order).  Result valid in threads < N of
+// `out` (shared).  Requires blockDim.x a multiple of 32, <= 1024.
+template <int N, class T>
+__device__ __forceinline__ void block_sum(const T (&v)[N], int n, double* out) {
+  __shared__ double sh[32][N > 0 ? N : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (i < n) {
+      T s = warp_sum(v[i]);
+      if (lane == 0) sh[warp][i] = (double)s;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sh[k][i];
+    out[i] = s;
+  }
+  __syncthreads();
+}
+
+// Arrival counter: true in the one block that finishes last.  Every block's
+// partials are fenced before it arrives, so the last block sees all of them.
+__device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int prev = atomicAdd(cnt, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// In the last block: out[i] = sum over blocks b of part[b*stride + i], FP64, fixed order.
+template <int N>
+__device__ __forceinline__ void reduce_partials(const double* part, int nblk, int stride, int n, double* out) {
+  double acc[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+      if (i < n) acc[i] += __ldcg(part + (size_t)b * stride + i);
+  }
+  block_sum<N, double>(acc, n, out);
+}
+
+__device__ __forceinline__ void set_fail(State* st, int status) {
+  if (st->status == KW_OK || st->status == KW_NOT_CONVERGED) st->status = status;
+  st->done = 1;
+}
+
+// ================================================================ K1: SpMV + first dot
+struct SpmvMode {
+  int solver;        // 1: inside the solve (reads z_s, pending scale, computes alpha)
+  double2 zs;        // standalone: seed shift
+  double2* t_out;    // standalone: result
+};
+
+template <int P, int G>
+__global__ void __launch_bounds__(256)
+k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+           const typename PT<P>::R* __restrict__ val, const typename PT<P>::V* __restrict__ r,
+           typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  typedef typename PT<P>::A A;
+  double2 zs, sc = make_double2(1.0, 0.0);
+  if (mode.solver) {
+    if (st->done) return;
+    zs = st->zs;
+    if (st->vec_scale_pending) sc = st->scale_rn;
+  } else {
+    zs = mode.zs;
+  }
+  const V zsv = vmake<V>(zs), scv = vmake<V>(sc);
+  const int lane = threadIdx.x & 31, sub = lane % G, gw = lane / G;
+  const int RPW = 32 / G;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+
+  A c_re = 0, c_im = 0;      // FP32 (or FP64) partial over <= CHUNK rows
+  double t_re = 0, t_im = 0; // FP64 total, only lane 0 of each warp uses it
+  int in_chunk = 0;
+  for (int base = warp_global * RPW; base < m; base += nwarps * RPW) {
+    const int row = base + gw;
+    V acc = vzero<V>();
+    if (row < m) {
+      const int beg = (int)rowptr[row], end = (int)rowptr[row + 1];
+      for (int j = beg + sub; j < end; j += G) {
+        const R v = val[j];
+        const V x = r[col[j]];
+        acc.x += v * x.x;
+        acc.y += v * x.y;
+      }
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      acc.x += __shfl_xor_sync(KW_FULL_MASK, acc.x, off);
+      acc.y += __shfl_xor_sync(KW_FULL_MASK, acc.y, off);
+    }
+    if (sub == 0 && row < m) {
+      const V ri = r[row];
+      const V qi = cmul(scv, csub(cmul(zsv, ri), acc));   // s (z_s r - H r)
+      q[row] = qi;
+      const V pr = cmul(cmul(scv, ri), qi);               // (s r)^T q, unconjugated
+      c_re += pr.x;
+      c_im += pr.y;
+    }
+    if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
+      A s_re = warp_sum(c_re), s_im = warp_sum(c_im);
+      t_re += (double)s_re;
+      t_im += (double)s_im;
+      c_re = c_im = 0;
+      in_chunk = 0;
+    }
+  }
+  {
+    A s_re = warp_sum(c_re), s_im = warp_sum(c_im);
+    t_re += (double)s_re;
+    t_im += (double)s_im;
+  }
+  __shared__ double red[2];
+  {
+    double v2[2] = {lane == 0 ? t_re : 0.0, lane == 0 ? t_im : 0.0};
+    block_sum<2, double>(v2, 2, red);
+  }
+  if (threadIdx.x < 2) part[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+  if (!arrive_last(&st->cnt_spmv)) return;
+
+  __shared__ double tot[2];
+  reduce_partials<2>(part, gridDim.x, 2, 2, tot);
+  if (threadIdx.x == 0) {
+    st->cnt_spmv = 0;
+    const double2 t = make_double2(tot[0], tot[1]);
+    if (!mode.solver) {
+      *mode.t_out = t;
+      return;
+    }
+    st->t = t;
+    const double2 rho = st->rho, boa = st->boa;
+    // alpha_n = rho_n / (r_n^T A r_n - (beta_{n-1}/alpha_{n-1}) rho_n)   (Eq. 17)
+    const double2 denom = csub(t, cmul(boa, rho));
+    if ((rho.x == 0.0 && rho.y == 0.0) || (denom.x == 0.0 && denom.y == 0.0)) {
+      set_fail(st, KW_ERR_BREAKDOWN);
+      return;
+    }
+    const double2 alpha = cdiv(rho, denom);
+    const double2 c = cmul(alpha, boa);
+    if (!cfinite(alpha) || !cfinite(c)) {
+      set_fail(st, KW_ERR_NONFINITE);
+      return;
+    }
+    st->alpha = alpha;
+    st->c = c;
+    st->n_list = 0;
+  }
+}
+
+// ================================================================ K2: three-term update + dots
+// Values per block: [rho.re, rho.im, nu, w_0.re, w_0.im, ..., w_{np-1}.re, w_{np-1}.im]
+template <int P, int NP>
+__global__ void __launch_bounds__(256)
+k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
+              typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int np,
+              State* st, double* __restrict__ part, double2* __restrict__ w_out) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  typedef typename PT<P>::A A;
+  constexpr int N = 3 + 2 * NP;
+  if (st->done) return;
+  const double2 alpha = st->alpha, c = st->c;
+  const int pend = st->vec_scale_pending;
+  const V s1 = vmake<V>(st->scale_rn), s0 = vmake<V>(st->scale_rnm1);
+  const V opc = vmake<V>(make_double2(1.0 + c.x, c.y)), av = vmake<V>(alpha), cv = vmake<V>(c);
+  const int n = 3 + 2 * np;
+
+  constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
+  A chunk[N], tot[N];
+#pragma unroll
+  for (int i = 0; i < N; ++i) chunk[i] = tot[i] = 0;
+  int in_chunk = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+    V rn = rn_buf[i];
+    V rm = rm_buf[i];
+    const V qi = q[i];
+    if (pend) {               // lazy seed switch: bring r_n, r_{n-1} to the new seed
+      rn = cmul(s1, rn);
+      rm = cmul(s0, rm);
+      rn_buf[i] = rn;
+    }
+    const V r1 = csub(csub(cmul(opc, rn), cmul(av, qi)), cmul(cv, rm));
+    rm_buf[i] = r1;
+    chunk[0] += r1.x * r1.x - r1.y * r1.y;   // r^T r (unconjugated)
+    chunk[1] += 2 * r1.x * r1.y;
+    chunk[2] += r1.x * r1.x + r1.y * r1.y;   // r^dagger r
+#pragma unroll
+    for (int l = 0; l < NP; ++l) {
+      if (l < np) {
+        const R a = proj[(size_t)l * m + i];
+        chunk[3 + 2 * l] += a * r1.x;
+        chunk[4 + 2 * l] += a * r1.y;
+      }
+    }
+    if (CHUNKED && ++in_chunk == PT<P>::CHUNK) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) { tot[k] += chunk[k]; chunk[k] = 0; }
+      in_chunk = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) tot[k] = CHUNKED ? tot[k] + chunk[k] : chunk[k];
+
+  __shared__ double red[N];
+  block_sum<N, A>(tot, n, red);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) part[(size_t)blockIdx.x * n + k] = red[k];
+  if (!arrive_last(&st->cnt_seed)) return;
+
+  __shared__ double all[N];
+  reduce_partials<N>(part, gridDim.x, n, n, all);
+  for (int l = threadIdx.x; l < np; l += blockDim.x) w_out[l] = make_double2(all[3 + 2 * l], all[4 + 2 * l]);
+  if (threadIdx.x == 0) {
+    st->cnt_seed = 0;
+    st->vec_scale_pending = 0;
+    const double2 rho1 = make_double2(all[0], all[1]);
+    const double2 beta = cdiv(rho1, st->rho);          // beta_n = rho_{n+1} / rho_n
+    st->rho1 = rho1;
+    st->beta = beta;
+    st->nu = all[2];
+    if (!cfinite(beta) || !isfinite(all[2])) set_fail(st, KW_ERR_NONFINITE);
+  }
+}
+
+// ================================================================ K3: shift scalars
+struct ShiftArgs {
+  int K, np, full;
+  const double2* z;
+  double2* pi1;      // pi_n on entry, pi_{n+1} on exit
+  double2* pi0;      // pi_{n-1} on entry, pi_n on exit
+  int* active;
+  long long* conv_iter;
+  double* final_res;
+  double2* coef;     // full mode [K][3]
+  double2* Y;
+  double2* U;
+  const double2* w;  // P r_{n+1}
+  double* hist;
+  int* list;
+  double* part;      // per block: [best |pi|^2, best index, n still active]
+};
+
+static __global__ void __launch_bounds__(64) k_shift(ShiftArgs a, State* st) {
+  if (st->done) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double2 alpha = st->alpha, c = st->c, beta = st->beta, zs = st->zs;
+  const double sqrt_nu = sqrt(st->nu);
+  const int pend = st->pi_rescale_pending, jnew = st->new_seed;
+  const long long iter = st->iter;
+  const bool rec = st->hist_stride > 0 && ((iter + 1) % st->hist_stride) == 0 && st->n_rec < st->hist_max;
+
+  double best = INFINITY;
+  int best_k = 0x7fffffff, still = 0, brk = 0;
+  if (k < a.K && a.active[k]) {
+    // warp-aggregated slot in the compacted list of shifts updated this iteration
+    const unsigned act = __activemask();
+    const int leader = __ffs(act) - 1, rank = __popc(act & ((1u << (threadIdx.x & 31)) - 1));
+    int basepos = 0;
+    if ((int)(threadIdx.x & 31) == leader) basepos = atomicAdd(&st->n_list, __popc(act));
+    basepos = __shfl_sync(act, basepos, leader);
+    a.list[basepos + rank] = k;
+
+    double2 p1 = a.pi1[k], p0 = a.pi0[k];
+    if (pend) {                       // lazy rescale after a seed switch
+      if (k == jnew) {
+        p1 = p0 = make_double2(1.0, 0.0);
+      } else {
+        p1 = cmul(p1, st->inv_pj1);
+        p0 = cmul(p0, st->inv_pj0);
+      }
+    }
+    const double2 sigma = csub(a.z[k], zs);
+    // pi_{n+1} = (1 + c_n + alpha_n sigma) pi_n - c_n pi_{n-1}          (Eq. 20)
+    const double2 f = cadd(make_double2(1.0 + c.x, c.y), cmul(alpha, sigma));
+    const double2 pn = csub(cmul(f, p1), cmul(c, p0));
+    if (pn.x == 0.0 && pn.y == 0.0) {
+      brk = 1;
+    } else {
+      const double2 ratio = cdiv(p1, pn);             // pi_n / pi_{n+1}
+      const double2 ak = cmul(ratio, alpha);          // Eq. 21
+      const double2 bk = cmul(cmul(ratio, ratio), beta);  // Eq. 22
+      const double2 ipn = crecip(pn);
+      if (a.full) {
+        a.coef[3 * k + 0] = ak;
+        a.coef[3 * k + 1] = bk;
+        a.coef[3 * k + 2] = ipn;
+      } else {
+        for (int l = 0; l < a.np; ++l) {              // Eq. 25-26
+          const size_t o = (size_t)k * a.np + l;
+          const double2 u = a.U[o];
+          a.Y[o] = cadd(a.Y[o], cmul(ak, u));
+          a.U[o] = cadd(cmul(a.w[l], ipn), cmul(bk, u));
+        }
+      }
+      a.pi0[k] = p1;
+      a.pi1[k] = pn;
+      const double res = sqrt_nu / hypot(pn.x, pn.y);
+      a.final_res[k] = res;
+      if (res <= st->thresh) {
+        a.active[k] = 0;
+        a.conv_iter[k] = iter + 1;
+      } else {
+        still = 1;
+        best = __dadd_rn(__dmul_rn(pn.x, pn.x), __dmul_rn(pn.y, pn.y));
+        best_k = k;
+      }
+    }
+  }
+  if (rec && k < a.K) a.hist[(size_t)st->n_rec * a.K + k] = a.final_res[k];
+
+  // block argmin of |pi_{n+1}|^2 over still-active shifts (ties: lowest index) and count
+  __shared__ double sb[2];
+  __shared__ int sk[2], sc[2], sbrk[2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(KW_FULL_MASK, best, off);
+    const int ok = __shfl_xor_sync(KW_FULL_MASK, best_k, off);
+    if (ob < best || (ob == best && ok < best_k)) { best = ob; best_k = ok; }
+    still += __shfl_xor_sync(KW_FULL_MASK, still, off);
+    brk |= __shfl_xor_sync(KW_FULL_MASK, brk, off);
+  }
+  if (lane == 0) { sb[warp] = best; sk[warp] = best_k; sc[warp] = still; sbrk[warp] = brk; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int wi = 1; wi < (int)(blockDim.x >> 5); ++wi) {
+      if (sb[wi] < sb[0] || (sb[wi] == sb[0] && sk[wi] < sk[0])) { sb[0] = sb[wi]; sk[0] = sk[wi]; }
+      sc[0] += sc[wi];
+      sbrk[0] |= sbrk[wi];
+    }
+    a.part[4 * blockIdx.x + 0] = sb[0];
+    a.part[4 * blockIdx.x + 1] = (double)sk[0];
+    a.part[4 * blockIdx.x + 2] = (double)sc[0];
+    a.part[4 * blockIdx.x + 3] = (double)sbrk[0];
+  }
+  if (!arrive_last(&st->cnt_shift)) return;
+
+  if (threadIdx.x == 0) {
+    st->cnt_shift = 0;
+    double gb = INFINITY;
+    int gk = 0x7fffffff;
+    long long n_still = 0;
+    int any_brk = 0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      const double vb = __ldcg(a.part + 4 * b);
+      const int vk = (int)__ldcg(a.part + 4 * b + 1);
+      if (vb < gb || (vb == gb && vk < gk)) { gb = vb; gk = vk; }
+      n_still += (long long)__ldcg(a.part + 4 * b + 2);
+      any_brk |= (int)__ldcg(a.part + 4 * b + 3);
+    }
+    st->pi_rescale_pending = 0;
+    if (rec) st->n_rec += 1;
+    const int nl = *((volatile int*)&st->n_list);
+    st->updates += nl;
+    st->xp_pending = (a.full && nl > 0 && !any_brk) ? 1 : 0;
+    st->n_active = (int)n_still;
+    double2 rho1 = st->rho1;
+    double2 boa = cdiv(st->beta, st->alpha);          // beta_n / alpha_n
+    if (any_brk) {                                      // pi_{n+1} = 0 (Eq. 20)
+      set_fail(st, KW_ERR_BREAKDOWN);
+      return;
+    }
+    if (st->seed_switch && n_still > 0 && gb < 1.0) {  // Sec. 2.2.4
+      const double2 pj1 = __ldcg(a.pi1 + gk), pj0 = __ldcg(a.pi0 + gk);
+      const double2 i1 = crecip(pj1), i0 = crecip(pj0);
+      st->scale_rn = i1;                 // r_{n+1} <- r_{n+1} / pi^j_{n+1}
+      st->scale_rnm1 = i0;               // r_n     <- r_n / pi^j_n
+      st->vec_scale_pending = 1;
+      rho1 = cmul(rho1, cmul(i1, i1));   // rho_{n+1} of the rescaled residual
+      boa = cmul(boa, cmul(pj0, i1));    // beta^j_n / alpha^j_n
+      st->inv_pj1 = i1;
+      st->inv_pj0 = i0;
+      st->pi_rescale_pending = 1;
+      st->new_seed = gk;
+      st->seed = gk;
+      st->zs = a.z[gk];
+      st->n_seed_switch += 1;
+    }
+    st->rho = rho1;
+    st->boa = boa;
+    st->iter = st->iter + 1;
+    if (n_still == 0) {
+      st->status = KW_OK;
+      st->done = 1;
+    } else if (st->iter >= st->maxiter) {
+      st->status = KW_NOT_CONVERGED;
+      st->done = 1;
+    }
+  }
+}
+
+// ================================================================ K4: fused x/p update
+template <int P, int TS>
+__global__ void __launch_bounds__(256)
+k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coef,
+            typename PT<P>::V* __restrict__ X, typename PT<P>::V* __restrict__ Pv,
+            const typename PT<P>::V* __restrict__ r1, State* st) {
+  typedef typename PT<P>::V V;
+  if (!st->xp_pending) return;
+  const int nl = st->n_list;
+  const int ntile = (nl + TS - 1) / TS;
+  const int nchunk = (m + blockDim.x - 1) / blockDim.x;
+  __shared__ V cs[TS][3];
+  __shared__ int ks[TS];
+  const long long nitem = (long long)ntile * nchunk;
+  for (long long item = blockIdx.x; item < nitem; item += gridDim.x) {
+    const int tile = (int)(item % ntile), chunk = (int)(item / ntile);
+    const int t0 = tile * TS, nts = min(TS, nl - t0);
+    __syncthreads();
+    if (threadIdx.x < nts) {
+      const int k = list[t0 + threadIdx.x];
+      ks[threadIdx.x] = k;
+      cs[threadIdx.x][0] = vmake<V>(coef[3 * k + 0]);
+      cs[threadIdx.x][1] = vmake<V>(coef[3 * k + 1]);
+      cs[threadIdx.x][2] = vmake<V>(coef[3 * k + 2]);
+    }
+    __syncthreads();
+    const int i = chunk * blockDim.x + threadIdx.x;
+    if (i < m) {
+      const V ri = r1[i];
+#pragma unroll 4
+      for (int s = 0; s < nts; ++s) {
+        const size_t o = (size_t)ks[s] * m + i;
+        V x = X[o], p = Pv[o];
+        x = cadd(x, cmul(cs[s][0], p));                        // Eq. 23
+        p = cadd(cmul(ri, cs[s][2]), cmul(cs[s][1], p));       // Eq. 24
+        X[o] = x;
+        Pv[o] = p;
+      }
+    }
+  }
+  if (!arrive_last(&st->cnt_xp)) return;
+  if (threadIdx.x == 0) {
+    st->cnt_xp = 0;
+    st->xp_pending = 0;
+  }
+}
+
+// ================================================================ initialisation
+template <int P>
+__global__ void k_init_vectors(int m, int np, const double* __restrict__ b, const double* __restrict__ left,
+                               typename PT<P>::V* rn, typename PT<P>::V* rm,
+                               typename PT<P>::R* proj) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    rn[i] = vmake<V>(make_double2(bi, 0.0));
+    rm[i] = vzero<V>();
+    if (np > 0) {
+      proj[i] = (R)bi;
+      for (int l = 1; l < np; ++l) proj[(size_t)l * m + i] = (R)left[(size_t)(l - 1) * m + i];
+    }
+  }
+}
+
+// x_k = 0, p_k = b for every shift (full mode, Eq. 23-24 initialisation).
+template <int P>
+__global__ void k_init_xp(int m, int K, const double* __restrict__ b, typename PT<P>::V* X,
+                          typename PT<P>::V* Pv) {
+  typedef typename PT<P>::V V;
+  const long long total = (long long)K * m;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+       o += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(o % m);
+    X[o] = vzero<V>();
+    Pv[o] = vmake<V>(make_double2(b[i], 0.0));
+  }
+}
+
+// FP64 dots of b with b and with each projection row (from the caller's FP64 arrays):
+// out = [b^T b, a_1^T b, ...]; last block writes rho_0, ||b||, threshold and w0.
+template <int NPM>
+__global__ void __launch_bounds__(256)
+k_init_dots(int m, int np, const double* __restrict__ b, const double* __restrict__ left, double tol,
+            State* st, double* part, double2* w0) {
+  double acc[NPM + 1];
+#pragma unroll
+  for (int l = 0; l <= NPM; ++l) acc[l] = 0.0;
+  const int n = 1 + (np > 1 ? np - 1 : 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double bi = b[i];
+    acc[0] += bi * bi;
+#pragma unroll
+    for (int l = 1; l <= NPM; ++l)
+      if (l < n) acc[l] += left[(size_t)(l - 1) * m + i] * bi;
+  }
+  __shared__ double red[NPM + 1];
+  block_sum<NPM + 1, double>(acc, n, red);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) part[(size_t)blockIdx.x * n + k] = red[k];
+  if (!arrive_last(&st->cnt_init)) return;
+  __shared__ double all[NPM + 1];
+  reduce_partials<NPM + 1>(part, gridDim.x, n, n, all);
+  if (threadIdx.x == 0) {
+    st->cnt_init = 0;
+    st->rho = make_double2(all[0], 0.0);
+    st->norm_b = sqrt(all[0]);
+    st->thresh = tol * st->norm_b;
+    if (np > 0) w0[0] = make_double2(all[0], 0.0);
+    for (int l = 1; l < np; ++l) w0[l] = make_double2(all[l], 0.0);
+    if (!(all[0] > 0.0) || !isfinite(all[0])) set_fail(st, KW_ERR_ARG);
+  }
+}
+
+static __global__ void k_init_shifts(int K, int np, double2* pi1, double2* pi0, int* active, long long* conv_iter,
+                              double* final_res, double2* Y, double2* U, const double2* w0) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  pi1[k] = pi0[k] = make_double2(1.0, 0.0);
+  active[k] = 1;
+  conv_iter[k] = -1;
+  final_res[k] = INFINITY;
+  for (int l = 0; l < np; ++l) {
+    Y[(size_t)k * np + l] = make_double2(0.0, 0.0);
+    U[(size_t)k * np + l] = w0[l];
+  }
+}
+
+// out[k][l] = a_l^T x_k (a_0 = b), FP64 from the caller's FP64 vectors; one block per shift.
+template <int P, int NPM>
+__global__ void __launch_bounds__(256)
+k_project_x(int m, int np, const double* __restrict__ b, const double* __restrict__ left,
+            const typename PT<P>::V* __restrict__ X, double2* out) {
+  typedef typename PT<P>::V V;
+  const int k = blockIdx.x;
+  double acc[2 * NPM];
+#pragma unroll
+  for (int l = 0; l < 2 * NPM; ++l) acc[l] = 0.0;
+  const V* xk = X + (size_t)k * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const V x = xk[i];
+#pragma unroll
+    for (int l = 0; l < NPM; ++l) {
+      if (l < np) {
+        const double a = (l == 0) ? b[i] : left[(size_t)(l - 1) * m + i];
+        acc[2 * l] += a * (double)x.x;
+        acc[2 * l + 1] += a * (double)x.y;
+      }
+    }
+  }
+  __shared__ double red[2 * NPM];
+  block_sum<2 * NPM, double>(acc, 2 * np, red);
+  for (int l = threadIdx.x; l < np; l += blockDim.x) out[(size_t)k * np + l] = make_double2(red[2 * l], red[2 * l + 1]);
+}
+
+static __global__ void k_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// ================================================================ launchers
+template <int P, int G>
+static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  k_spmv_dot<P, G><<<w.nblk_spmv, 256, 0, w.stream>>>((int)w.m, w.rowptr, w.col, (const R*)w.val,
+                                                      (const V*)r, (V*)q, w.st, w.part, mode);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
+  switch (w.spmv_lanes) {
+    case 2: return spmv_launch<P, 2>(w, r, q, mode);
+    case 4: return spmv_launch<P, 4>(w, r, q, mode);
+    case 8: return spmv_launch<P, 8>(w, r, q, mode);
+    case 16: return spmv_launch<P, 16>(w, r, q, mode);
+    default: return spmv_launch<P, 32>(w, r, q, mode);
+  }
+}
+
+template <int P, int NP>
+static cudaError_t seed_launch(Work& w, void* rn, void* rm) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  k_seed_update<P, NP><<<w.nblk_seed, 256, 0, w.stream>>>((int)w.m, (V*)rn, (const V*)w.q, (V*)rm,
+                                                          (const R*)w.proj_rows, w.nproj, w.st, w.part, w.w);
+  return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t seed_dispatch(Work& w, void* rn, void* rm) {
+  const int np = w.nproj;
+  if (np == 0) return seed_launch<P, 0>(w, rn, rm);
+  if (np <= 2) return seed_launch<P, 2>(w, rn, rm);
+  if (np <= 5) return seed_launch<P, 5>(w, rn, rm);
+  if (np <= 9) return seed_launch<P, 9>(w, rn, rm);
+  if (np <= 17) return seed_launch<P, 17>(w, rn, rm);
+  return seed_launch<P, KW_MAX_PROJ>(w, rn, rm);
+}
+
+template <int P>
+cudaError_t launch_iteration(Work& w, int parity) {
+  typedef typename PT<P>::V V;
+  // parity 0: r_n in rA, r_{n-1} in rB; parity 1: swapped.  K2 writes r_{n+1} over r_{n-1}.
+  void* rn = parity ? w.rB : w.rA;
+  void* rm = parity ? w.rA : w.rB;
+  SpmvMode mode;
+  mode.solver = 1;
+  mode.zs = make_double2(0.0, 0.0);
+  mode.t_out = nullptr;
+  cudaError_t e = spmv_dispatch<P>(w, rn, w.q, mode);
+  if (e != cudaSuccess) return e;
+  if ((e = seed_dispatch<P>(w, rn, rm)) != cudaSuccess) return e;
+  ShiftArgs a;
+  a.K = w.K;
+  a.np = w.nproj;
+  a.full = w.full ? 1 : 0;
+  a.z = w.z;
+  a.pi1 = w.pi1;
+  a.pi0 = w.pi0;
+  a.active = w.active;
+  a.conv_iter = w.conv_iter;
+  a.final_res = w.final_res;
+  a.coef = w.coef;
+  a.Y = w.Y;
+  a.U = w.U;
+  a.w = w.w;
+  a.hist = w.hist;
+  a.list = w.list;
+  a.part = w.part;
+  k_shift<<<w.nblk_shift, 64, 0, w.stream>>>(a, w.st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (w.full) {
+    k_update_xp<P, 8><<<w.nblk_xp, 256, 0, w.stream>>>((int)w.m, w.list, w.coef, (V*)w.X, (V*)w.P,
+                                                       (const V*)rm, w.st);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int P>
+cudaError_t launch_init(Work& w) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  const int nb = 4 * w.num_sms;
+  k_init_vectors<P><<<nb, 256, 0, w.stream>>>((int)w.m, w.nproj, w.b, w.left, (V*)w.rA, (V*)w.rB,
+                                              (R*)w.proj_rows);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (w.full) {
+    k_init_xp<P><<<8 * w.num_sms, 256, 0, w.stream>>>((int)w.m, w.K, w.b, (V*)w.X, (V*)w.P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (w.nproj <= 8)
+    k_init_dots<8><<<nb, 256, 0, w.stream>>>((int)w.m, w.nproj, w.b, w.left, w.tol, w.st, w.part, w.w0);
+  else
+    k_init_dots<KW_MAX_PROJ><<<nb, 256, 0, w.stream>>>((int)w.m, w.nproj, w.b, w.left, w.tol, w.st, w.part, w.w0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_init_shifts<<<(w.K + 127) / 128, 128, 0, w.stream>>>(w.K, w.nproj, w.pi1, w.pi0, w.active, w.conv_iter,
+                                                        w.final_res, w.Y, w.U, w.w0);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_project_x(Work& w, double2* out) {
+  typedef typename PT<P>::V V;
+  const int np = w.nout;
+  if (np <= 8)
+    k_project_x<P, 8><<<w.K, 256, 0, w.stream>>>((int)w.m, np, w.b, w.left, (const V*)w.X, out);
+  else
+    k_project_x<P, KW_MAX_PROJ><<<w.K, 256, 0, w.stream>>>((int)w.m, np, w.b, w.left, (const V*)w.X, out);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, double2* t_dev) {
+  SpmvMode mode;
+  mode.solver = 0;
+  mode.zs = zs;
+  mode.t_out = t_dev;
+  return spmv_dispatch<P>(w, r, q, mode);
+}
+
+}  // namespace kw

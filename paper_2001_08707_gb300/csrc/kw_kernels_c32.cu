@@ -1,0 +1,10 @@
+// Complex-FP32-vector instantiation of the iteration kernels (FP32 vectors and
+// matrix values; FP64 scalars, FP64 accumulation across FP32 chunk partials).
+#include "kw_kernels.cuh"
+
+namespace kw {
+template cudaError_t launch_init<PREC_C32>(Work&);
+template cudaError_t launch_iteration<PREC_C32>(Work&, int);
+template cudaError_t launch_project_x<PREC_C32>(Work&, double2*);
+template cudaError_t launch_spmv_dot<PREC_C32>(Work&, const void*, void*, double2, double2*);
+}  // namespace kw

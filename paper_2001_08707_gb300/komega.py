@@ -1,0 +1,244 @@
+"""Python binding of libkomega_gb300.so (ctypes; argument marshalling only).
+
+Every step of the solve runs in the library's CUDA kernels.  PyTorch provides
+device memory and the current CUDA stream.  The names mirror the C ABI in
+include/komega_gb300.h.  There is no CPU fallback: if the library is missing
+or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkomega_gb300.so")
+
+KW_F64 = 0
+KW_C32V_F64S = 1
+PRECISIONS = {"f64": KW_F64, "c32v_f64s": KW_C32V_F64S, "c32": KW_C32V_F64S}
+
+STATUS = {0: "KW_OK", 1: "KW_ERR_ARG", 2: "KW_ERR_CUDA", 3: "KW_ERR_OOM", 4: "KW_ERR_BREAKDOWN",
+          5: "KW_ERR_NONFINITE", 6: "KW_ERR_CALLBACK", 7: "KW_ERR_TIMEOUT", 8: "KW_NOT_CONVERGED"}
+KW_OK, KW_ERR_ARG, KW_NOT_CONVERGED = 0, 1, 8
+MAX_PROJ = 32
+
+
+class kw_options(C.Structure):
+    _fields_ = [("prec", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int64), ("seed_switch", C.c_int),
+                ("hist_stride", C.c_int64), ("hist_max", C.c_int64)]
+
+
+class kw_c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class kw_solve_info(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("n_converged", C.c_int64), ("max_res", C.c_double),
+                ("n_seed_switch", C.c_int64), ("updates", C.c_int64), ("seed", C.c_int64), ("status", C.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2001_08707_gb300.build` "
+                           "(or __graft_entry__.build()); there is no CPU fallback")
+    lib = C.CDLL(path)
+    P, I64, D = C.c_void_p, C.c_int64, C.c_double
+    sig = {
+        "kw_abi_version": (C.c_int, []),
+        "kw_default_options": (None, [C.POINTER(kw_options)]),
+        "kw_status_string": (C.c_char_p, [C.c_int]),
+        "kw_create": (C.c_int, [C.POINTER(P), C.POINTER(kw_options), P]),
+        "kw_destroy": (None, [P]),
+        "kw_last_error": (C.c_int, [P, C.c_char_p, C.c_size_t]),
+        "kw_set_csr": (C.c_int, [P, I64, I64, P, P, P]),
+        "kw_solve": (C.c_int, [P, P, I64, P, I64, P, P, P, C.POINTER(kw_solve_info)]),
+        "kw_solve_host": (C.c_int, [P, I64, I64, P, P, P, P, I64, P, I64, P, P, P, C.POINTER(kw_solve_info)]),
+        "kw_get_shift_status": (C.c_int, [P, P, P]),
+        "kw_get_residual_history": (C.c_int, [P, P, C.POINTER(I64)]),
+        "kw_spmv_dot": (C.c_int, [P, kw_c128, P, P, C.POINTER(kw_c128)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class KomegaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+@dataclass
+class SolveResult:
+    proj: np.ndarray          # [K, nleft+1] complex128; column 0 = b^T x_k
+    x: object                 # torch tensor [K, m] (complex128 / complex64) in full mode, else None
+    iters: int
+    n_converged: int
+    max_res: float
+    n_seed_switch: int
+    updates: int
+    seed: int
+    status: str
+
+
+def _z_array(z):
+    z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
+    return z, z.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """A solver context (kw_ctx) on the current CUDA device and stream."""
+
+    def __init__(self, prec: str = "f64", tol: float = 1e-10, maxiter: int = 100000, seed_switch: bool = True,
+                 hist_stride: int = 0, hist_max: int = 0, stream=None):
+        import torch
+
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("komega: no CUDA device (the solver has no CPU path)")
+        lib = load_library()
+        self._lib = lib
+        self.prec = PRECISIONS[prec]
+        opt = kw_options(self.prec, tol, maxiter, 1 if seed_switch else 0, hist_stride, hist_max)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        ctx = C.c_void_p()
+        st = lib.kw_create(C.byref(ctx), C.byref(opt), C.c_void_p(s.cuda_stream))
+        if st != KW_OK:
+            raise KomegaError(st, "kw_create failed")
+        self._ctx = ctx
+        self._keep = []
+        self.m = None
+        self.vec_dtype = torch.complex128 if self.prec == KW_F64 else torch.complex64
+
+    # ------------------------------------------------------------------ helpers
+    def _err(self, st, what):
+        buf = C.create_string_buffer(512)
+        self._lib.kw_last_error(self._ctx, buf, 512)
+        return KomegaError(st, f"{what}: {buf.value.decode()}")
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.kw_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, a, dtype):
+        t = self._torch
+        if isinstance(a, t.Tensor):
+            a = a.to(device="cuda", dtype=dtype)
+        else:
+            a = t.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+        return a.contiguous()
+
+    # ------------------------------------------------------------------ ABI calls
+    def set_csr(self, rowptr, col, val):
+        t = self._torch
+        rp = self._dev(rowptr, t.int64)
+        cl = self._dev(col, t.int32)
+        vl = self._dev(val, t.float64)
+        m = rp.numel() - 1
+        nnz = cl.numel()
+        st = self._lib.kw_set_csr(self._ctx, m, nnz, C.c_void_p(rp.data_ptr()), C.c_void_p(cl.data_ptr()),
+                                  C.c_void_p(vl.data_ptr()))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_csr")
+        self._keep = [rp, cl, vl]     # borrowed by the context in FP64 mode
+        self.m = m
+
+    def solve(self, b, z, left=None, full: bool = False, x_out=None, check: bool = True) -> SolveResult:
+        t = self._torch
+        bd = self._dev(b, t.float64)
+        zz, zp = _z_array(z)
+        K = zz.size
+        if left is not None:
+            ld = self._dev(left, t.float64)
+            nleft = ld.shape[0] if ld.dim() == 2 else 1
+            lp = C.c_void_p(ld.data_ptr())
+        else:
+            ld, nleft, lp = None, 0, None
+        x = None
+        xp = None
+        if full:
+            x = x_out if x_out is not None else t.empty((K, bd.numel()), dtype=self.vec_dtype, device="cuda")
+            xp = C.c_void_p(x.data_ptr())
+        proj = np.zeros((K, nleft + 1), dtype=np.complex128)
+        info = kw_solve_info()
+        st = self._lib.kw_solve(self._ctx, C.c_void_p(bd.data_ptr()), K, zp, nleft, lp, xp,
+                                proj.ctypes.data_as(C.c_void_p), C.byref(info))
+        if check and st not in (KW_OK, KW_NOT_CONVERGED):
+            raise self._err(st, "kw_solve")
+        return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
+                           info.seed, STATUS.get(st, str(st)))
+
+    def solve_host(self, rowptr, col, val, b, z, left=None, full: bool = False, check: bool = True):
+        """kw_solve_host: all inputs and outputs in host (numpy) memory."""
+        rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+        cl = np.ascontiguousarray(col, dtype=np.int32)
+        vl = np.ascontiguousarray(val, dtype=np.float64)
+        bb = np.ascontiguousarray(b, dtype=np.float64)
+        zz, zp = _z_array(z)
+        K = zz.size
+        m = rp.size - 1
+        ll = None if left is None else np.ascontiguousarray(np.atleast_2d(left), dtype=np.float64)
+        nleft = 0 if ll is None else ll.shape[0]
+        x = None
+        if full:
+            x = np.zeros((K, m), dtype=np.complex128 if self.prec == KW_F64 else np.complex64)
+        proj = np.zeros((K, nleft + 1), dtype=np.complex128)
+        info = kw_solve_info()
+        vp = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
+        st = self._lib.kw_solve_host(self._ctx, m, cl.size, vp(rp), vp(cl), vp(vl), vp(bb), K, zp, nleft, vp(ll),
+                                     vp(x), proj.ctypes.data_as(C.c_void_p), C.byref(info))
+        if check and st not in (KW_OK, KW_NOT_CONVERGED):
+            raise self._err(st, "kw_solve_host")
+        self.m = m
+        return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
+                           info.seed, STATUS.get(st, str(st)))
+
+    def shift_status(self, K: int):
+        ci = np.zeros(K, dtype=np.int64)
+        fr = np.zeros(K, dtype=np.float64)
+        st = self._lib.kw_get_shift_status(self._ctx, ci.ctypes.data_as(C.c_void_p), fr.ctypes.data_as(C.c_void_p))
+        if st != KW_OK:
+            raise self._err(st, "kw_get_shift_status")
+        return ci, fr
+
+    def residual_history(self, K: int):
+        n = C.c_int64()
+        st = self._lib.kw_get_residual_history(self._ctx, None, C.byref(n))
+        if st != KW_OK:
+            raise self._err(st, "kw_get_residual_history")
+        h = np.zeros((max(n.value, 0), K), dtype=np.float64)
+        if n.value > 0:
+            st = self._lib.kw_get_residual_history(self._ctx, h.ctypes.data_as(C.c_void_p), C.byref(n))
+            if st != KW_OK:
+                raise self._err(st, "kw_get_residual_history")
+        return h
+
+    def spmv_dot(self, zs: complex, r, q):
+        """q = zs r - H r and t = r^T q on the device (r, q: device complex tensors)."""
+        t = kw_c128()
+        st = self._lib.kw_spmv_dot(self._ctx, kw_c128(zs.real, zs.imag), C.c_void_p(r.data_ptr()),
+                                   C.c_void_p(q.data_ptr()), C.byref(t))
+        if st != KW_OK:
+            raise self._err(st, "kw_spmv_dot")
+        return complex(t.re, t.im)
