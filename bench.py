@@ -1,0 +1,447 @@
+"""Benchmark: shift-row updates/s of the shifted COCG solver on one GB300.
+
+One step = one complete projected-mode solve of the spin-1/2 Heisenberg chain
+N=24 (S^z=0, M=2,704,156, nnz=36,564,892) for K=1024 shifts w_k + 0.01i,
+w_k on [-12, 12), with 4 left vectors (b and 3 seeded Gaussians) to
+tolerance 1e-10.  Inputs are resident in HBM when the timed region starts
+(the CSR alone is larger than L2, so no L2 flush is needed).
+
+Headline: the FP64 form, the one that reaches the 1e-10 tolerance here.  The
+complex-FP32-vector form (FP64 scalars) is reported beside it, run on the same
+workload with an iteration cap, with its spectrum error against the headline;
+both are credited the headline run's work sum_n K_active(n) * M.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica (the solve does not
+shard across GPUs); value = total work of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "shift·row updates/s and HBM GB/s (% peak), FP32-vector vs FP64 at stated tol"
+UNIT = "shift-row updates/s"
+WORKLOAD = "heisenberg_chain_N24_Sz0_K1024_projected4_delta0.01_tol1e-10"
+KERNEL_SRC = os.path.join(ROOT, "paper_2001_08707_gb300", "csrc", "kw_kernels.cuh")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+
+
+HEADLINE = "f64"
+HEADLINE_DTYPE = "f64"
+PREC_NAMES = {"f64": "complex FP64 vectors, FP64 scalars",
+              "c32": "complex FP32 vectors, FP64 scalars"}
+PREC_BYTES = {"f64": (16, 8), "c32": (8, 4)}   # complex vector element, real element
+FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (a register-only FMA loop measured 1.20)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    h = kernel_source_hash()
+    with open(TRAFFIC_FILE) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel_key and parts[2] == h:
+                return float(parts[1])
+    return None
+
+
+def make_problem():
+    from paper_2001_08707_gb300 import workloads as w
+
+    return w.heisenberg_projected(N=24, K=1024, delta=0.01, tol=1e-10)
+
+
+def spmv_bytes(m, nnz, vec_bytes, val_bytes):
+    """Algorithmic bytes of one K1 launch: CSR (col + val + int64 rowptr), r read once, q written once."""
+    return nnz * (4 + val_bytes) + 8 * (m + 1) + 2 * vec_bytes * m
+
+
+def seed_bytes(m, vec_bytes, real_bytes, nproj):
+    """Algorithmic bytes of one K2 launch: read r_n, q, r_{n-1}; write r_{n+1}; read the projection rows."""
+    return 4 * vec_bytes * m + nproj * real_bytes * m
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int, device) -> float:
+    """Max over ranks (identity for one rank)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) timing
+ORACLE_SCRIPT = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import shifted_cocg as oc
+import scipy.sparse as sp
+d = np.load(sys.argv[2])
+n_iter = int(sys.argv[3]); reps = int(sys.argv[4])
+H = sp.csr_matrix((d["val"], d["col"], d["rowptr"]), shape=(d["rowptr"].size - 1,) * 2)
+out = []
+for _ in range(reps):
+    t0 = time.perf_counter()
+    r = oc.shifted_cocg(H, d["b"], d["z"], left=d["left"], tol=float(d["tol"]), maxiter=n_iter, full=False)
+    out.append({"seconds": time.perf_counter() - t0, "updates": int(r.updates), "iters": int(r.iters)})
+print(json.dumps(out))
+"""
+
+
+def oracle_timing(p, n_iter: int, reps: int):
+    """Run the oracle, as it stands, on n_iter iterations of the workload in a
+    single-threaded subprocess (BLAS threads pinned to 1)."""
+    with tempfile.TemporaryDirectory() as td:
+        f = os.path.join(td, "problem.npz")
+        np.savez(f, rowptr=p.H.rowptr, col=p.H.col, val=p.H.val, b=p.b, z=p.z, left=p.left, tol=p.tol)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", ORACLE_SCRIPT, ROOT, f, str(n_iter), str(reps)],
+                           capture_output=True, text=True, env=env)
+        if r.returncode != 0:
+            raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+ORACLE_ITERS = 12          # oracle iterations per step of the reference arm
+BASELINE_ITERS = 30        # oracle iterations in the cpu_baseline sample (about 10-30 s)
+
+
+def cpu_baseline(p):
+    runs = oracle_timing(p, BASELINE_ITERS, 1)
+    r = runs[0]
+    value = r["updates"] * p.H.m / r["seconds"]
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {r['iters']} iterations of the same workload (all {p.z.size} shifts active), "
+                      f"{r['seconds']:.1f} s, numpy/scipy FP64, BLAS threads 1"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    p = make_problem()
+    runs = oracle_timing(p, ORACLE_ITERS, args.warmup + args.steps)
+    timed = runs[args.warmup:]
+    secs = sum(r["seconds"] for r in timed)
+    upd = sum(r["updates"] for r in timed)
+    value = upd * p.H.m / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": p.H.m, "nnz": p.H.nnz, "K": int(p.z.size), "nleft": 4,
+                       "mode": "projected", "parallelism": "replicas",
+                       "step": f"{ORACLE_ITERS} oracle iterations (bounded sample of one solve)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{ORACLE_ITERS} iterations per step, numpy/scipy FP64, BLAS threads 1"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(device)
+    from paper_2001_08707_gb300 import build as kwbuild
+    from paper_2001_08707_gb300 import komega as kw
+
+    kwbuild.build()
+    p = make_problem()
+    m, nnz = p.H.m, p.H.nnz
+    nleft = p.left.shape[0]
+    nproj = nleft + 1
+    stream = torch.cuda.current_stream()
+    bd = torch.as_tensor(p.b, device=device)
+    ld = torch.as_tensor(p.left, device=device)
+
+    def solver(prec, maxiter):
+        s = kw.Solver(prec, tol=p.tol, maxiter=maxiter)
+        s.set_csr(p.H.rowptr, p.H.col, p.H.val)
+        return s
+
+    if args.profile_iters:
+        # profiling mode: the headline kernels on the same workload, one solve capped at N iterations
+        prec = args.profile_prec or HEADLINE
+        s = solver(prec, args.profile_iters)
+        r = s.solve(bd, p.z, left=ld)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": prec, "iters": r.iters, "status": r.status,
+                          "spmv_config": s.spmv_config()}))
+        return 0
+
+    def device_leg(prec, warmup, steps, maxiter, sampler=None):
+        s = solver(prec, maxiter)
+        s.set_kernel_timing(1)
+        for _ in range(warmup):
+            s.solve(bd, p.z, left=ld)
+        torch.cuda.synchronize()
+        times, stats, res = [], [], None
+        if sampler:
+            sampler.__enter__()
+        for _ in range(steps):
+            barrier(ws)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = s.solve(bd, p.z, left=ld)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            stats.append(s.stats())
+        if sampler:
+            sampler.__exit__(None, None, None)
+        cfg = s.spmv_config()
+        s.close()
+        return times, stats, res, cfg
+
+    # Headline leg first, with the SM clocks sampled during its timed steps.
+    idx = device.index if device.index is not None else 0
+    clk = ClockSampler(idx)
+    h_times, h_stats, h_res, h_cfg = device_leg(HEADLINE, args.warmup, args.steps, 200000, clk)
+    clocks = clk.summary()
+    work = h_res.updates * m                 # sum_n K_active(n) * M of one solve
+    t_ms = statistics.mean(h_times)
+    t_max = reduce_max(t_ms, ws, device)
+    value = ws * work / (t_max / 1e3)
+
+    # FP32-vector comparison leg: same workload, capped at 1.5x the headline's iterations.
+    cap = int(1.5 * h_res.iters) + 16
+    c_times, c_stats, c_res, c_cfg = device_leg("c32", 1, 1, cap)
+    c_ms = reduce_max(statistics.mean(c_times), ws, device)
+    A_h = -np.imag(h_res.proj[:, 0]) / np.pi
+    A_c = -np.imag(c_res.proj[:, 0]) / np.pi
+    spec_err = float(np.abs(A_c - A_h).max() / np.abs(A_h).max())
+    proj_err = float((np.abs(c_res.proj - h_res.proj).max(axis=0) / np.abs(h_res.proj).max(axis=0)).max())
+
+    def kstats(stats):
+        ti = sum(s["timed_iters"] for s in stats)
+        return ti, [sum(s["kernel_ms"][i] for s in stats) / max(ti, 1) for i in range(4)]
+
+    ti_h, k_h = kstats(h_stats)
+    ti_c, k_c = kstats(c_stats)
+    peak, peak_kind = load_peaks()
+    fp64_peak = FP64_PEAK_TFLOPS
+    vb_h, valb_h = PREC_BYTES[HEADLINE][0], (4 if h_cfg[1] else PREC_BYTES[HEADLINE][1])
+    b_spmv_h = spmv_bytes(m, nnz, vb_h, valb_h)
+    b_seed_h = seed_bytes(m, vb_h, PREC_BYTES[HEADLINE][1], nproj)
+    b_spmv_c = spmv_bytes(m, nnz, 8, 4)
+    b_seed_c = seed_bytes(m, 8, 4, nproj)
+    launches = sum(s["launches"] for s in h_stats)
+
+    if HEADLINE == "f64":
+        # FP64 arithmetic of one SpMV launch: 2 FMA per non-zero (real value x complex r)
+        # plus the row epilogue q = z_s r - acc and the r^T q term (about 8 FMA per row).
+        flops = 2.0 * (2 * nnz + 8 * m)
+        achieved = flops / (k_h[0] * 1e-3) / 1e12
+        roofline = {"kernel": "k_spmv_dot (seed SpMV + r^T q), f64", "bound": "alu", "achieved": achieved,
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                    "peak_kind": "nominal FP64 1.25 TFLOP/s (a register-only FMA probe measured 1.20)",
+                    "traffic": recorded_traffic("k_spmv_dot<f64>:heisenberg_N24"),
+                    "algorithmic_flops": flops, "algorithmic_bytes": b_spmv_h,
+                    "hbm_gbs_at_this_time": b_spmv_h / (k_h[0] * 1e-3) / 1e9,
+                    "avg_launch_us": 1e3 * k_h[0], "sampled_launches": ti_h}
+    else:
+        achieved = b_spmv_h / (k_h[0] * 1e-3) / 1e9
+        roofline = {"kernel": f"k_spmv_dot (seed SpMV + r^T q), {HEADLINE}", "bound": "hbm", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                    "traffic": recorded_traffic(f"k_spmv_dot<{HEADLINE}>:heisenberg_N24"),
+                    "algorithmic_bytes": b_spmv_h, "avg_launch_us": 1e3 * k_h[0], "sampled_launches": ti_h}
+
+    # e2e: the public host-buffer entry point, inputs copied from pinned host memory every step
+    rp = torch.from_numpy(p.H.rowptr).pin_memory()
+    cl = torch.from_numpy(p.H.col).pin_memory()
+    vl = torch.from_numpy(p.H.val).pin_memory()
+    bh = torch.from_numpy(p.b).pin_memory()
+    lh = torch.from_numpy(np.ascontiguousarray(p.left)).pin_memory()
+    se = kw.Solver(HEADLINE, tol=p.tol, maxiter=200000)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = se.solve_host(rp.numpy(), cl.numpy(), vl.numpy(), bh.numpy(), p.z, left=lh.numpy())
+        _ = float(np.abs(r.proj).max())          # the step's result is on the host
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    se.close()
+    e2e_s = reduce_max(statistics.mean(e2e_times), ws, device)
+    h2d = 8 * (m + 1) + 4 * nnz + 8 * nnz + 8 * m + 8 * nleft * m
+    d2h = 16 * p.z.size * nproj
+
+    cpu = cpu_baseline(p) if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
+
+    def kern(k, bs, bseed, iters, t):
+        return {"spmv_us": 1e3 * k[0], "spmv_gbs": bs / (k[0] * 1e-3) / 1e9, "seed_update_us": 1e3 * k[1],
+                "seed_update_gbs": bseed / (k[1] * 1e-3) / 1e9, "shift_us": 1e3 * k[2],
+                "iteration_us": t * 1e3 / max(iters, 1)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": HEADLINE_DTYPE, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": m, "nnz": nnz, "K": int(p.z.size), "nleft": nleft,
+                       "mode": "projected", "precision": PREC_NAMES[HEADLINE],
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (CSR %.0f MB)" % ((12 * nnz + 8 * m) / 1e6),
+                       "iters": h_res.iters, "status": h_res.status, "spmv_config": list(h_cfg)},
+            "roofline": roofline,
+            "kernels": {HEADLINE: kern(k_h, b_spmv_h, b_seed_h, h_res.iters, t_max),
+                        "c32": kern(k_c, b_spmv_c, b_seed_c, c_res.iters, c_ms)},
+            "c32_vectors": {"value": ws * work / (c_ms / 1e3), "ms_per_step": c_ms, "iters": c_res.iters,
+                            "iter_cap": cap, "status": c_res.status,
+                            "spectrum_rel_err_vs_headline": spec_err, "projection_rel_err_vs_headline": proj_err,
+                            "work_credit": "headline run's sum_n K_active(n) * M"},
+            "e2e": {"value": ws * work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": 1e3 * e2e_s, "api": "kw_solve_host (pinned host buffers)"},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="profiling mode: one solve capped at N iterations, no timing")
+    ap.add_argument("--profile-prec", choices=["f64", "c32"], default=None,
+                    help="precision form of the profiling-mode solve (default: the headline form)")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

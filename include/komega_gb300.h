@@ -108,7 +108,9 @@ kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
  * col_dev int32 [nnz] in [0, m), val_dev float64 [nnz].  The pointers are
  * borrowed in KW_F64 mode (they must stay valid until the next kw_set_csr or
  * kw_destroy); in KW_C32V_F64S mode the context keeps its own FP32 copy of the
- * values.  Symmetry is the caller's promise and is not checked.  Errors:
+ * values (and, in KW_F64 mode, uses an FP32 copy only if every value is
+ * exactly representable in FP32).  Symmetry is the caller's promise and is
+ * not checked.  Errors:
  * KW_ERR_ARG (m < 1, nnz < 0, nnz >= 2^31, NULL pointer), KW_ERR_OOM. */
 kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev,
                      const int32_t* col_dev, const double* val_dev);
@@ -151,6 +153,36 @@ kw_status kw_get_shift_status(kw_ctx* ctx, int64_t* conv_iter_host, double* fina
  * record i taken after iteration (i+1)*hist_stride.  hist_host may be NULL to
  * query *n_rec; otherwise it must hold hist_max * nshift doubles. */
 kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec);
+
+/* Per-solve statistics for measurement.  kernel_ms[i] sums the device time
+ * of kernel i (0: SpMV + r^T q, 1: three-term update + dots, 2: shift
+ * scalars, 3: x/p update) over timed_iters iterations sampled by
+ * kw_set_kernel_timing; launches counts every kernel the last solve enqueued
+ * (including iterations enqueued after the device stop flag, which return at
+ * once). */
+typedef struct {
+    int64_t launches;
+    int64_t timed_iters;
+    double kernel_ms[4];
+} kw_stats;
+
+/* Bracket the kernels of one iteration in every `every` with CUDA events on
+ * the context stream (0 turns it off; the default).  Errors: KW_ERR_ARG. */
+kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
+
+/* Configuration of the sparse product kernel.  lanes = threads per matrix
+ * row (1, 2, 4, 8 or 16; 0 = choose by timing every candidate on the current
+ * operator at the next solve, the default).  val_f32 (KW_F64 mode only): 1 =
+ * read the matrix values from an FP32 copy, allowed only when every value is
+ * exactly representable in FP32 (checked by kw_set_csr; otherwise FP64 is
+ * used); 0 = FP64 values; -1 = choose by timing.  Errors: KW_ERR_ARG. */
+kw_status kw_set_spmv_config(kw_ctx* ctx, int lanes, int val_f32);
+
+/* The configuration the next solve will use (tunes first if needed). */
+kw_status kw_get_spmv_config(kw_ctx* ctx, int* lanes, int* val_f32);
+
+/* Statistics of the last kw_solve / kw_solve_host. */
+kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out);
 
 /* One seed matrix-vector step (Alg. 1 "q = H r" combined with the seed shift,
  * and the first dot of Eq. 17): q = zs r - H r and t = r^T q (unconjugated),

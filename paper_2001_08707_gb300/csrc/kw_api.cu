@@ -53,6 +53,11 @@ struct kw_ctx {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   DBuf val32;
+  DBuf inexact;
+  bool val32_exact = false;   // every value representable in FP32
+  int spmv_lanes = 0;         // tuned or forced lanes per row (0 = tune at first use)
+  int spmv_val_f32 = 0;       // tuned or forced: FP32 value array in FP64 mode
+  int force_lanes = 0, force_val = -1;
   // host-solve copies
   DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
   // workspace
@@ -61,6 +66,10 @@ struct kw_ctx {
   kw::State* st_host = nullptr;   // pinned
   int* flags_host = nullptr;      // pinned, two slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
+  // kernel timing: one sampled iteration per chunk, two chunks in flight
+  int64_t timing_every = 0;
+  cudaEvent_t kev[2][5] = {};
+  kw_stats stats = {};
   // last solve
   int64_t last_K = 0;
   int64_t last_nrec = 0;
@@ -86,13 +95,6 @@ static kw_status cuda_fail(kw_ctx* c, cudaError_t e, const char* where) {
     cudaError_t e_ = (call);                          \
     if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
   } while (0)
-
-static int pick_lanes(int64_t m, int64_t nnz) {
-  const double avg = m > 0 ? (double)nnz / (double)m : 1.0;
-  int g = 2;
-  while (g < 32 && g * 2 <= avg) g *= 2;   // about two non-zeros per lane
-  return g;
-}
 
 extern "C" {
 
@@ -150,15 +152,18 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
 void kw_destroy(kw_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
-  DBuf* bufs[] = {&ctx->val32, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
+  DBuf* bufs[] = {&ctx->val32, &ctx->inexact, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot};
   for (DBuf* b : bufs) b->release();
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   if (ctx->flags_host) cudaFreeHost(ctx->flags_host);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 2; ++i) {
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (int j = 0; j < 5; ++j)
+      if (ctx->kev[i][j]) cudaEventDestroy(ctx->kev[i][j]);
+  }
   delete ctx;
 }
 
@@ -179,14 +184,104 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   ctx->rowptr = rowptr_dev;
   ctx->col = col_dev;
   ctx->val = val_dev;
-  if (ctx->opt.prec == KW_C32V_F64S && nnz > 0) {
+  ctx->val32_exact = false;
+  ctx->spmv_lanes = 0;   // re-tune for the new operator
+  if (nnz > 0) {
     KW_CUDA(ctx->val32.ensure((size_t)nnz * sizeof(float)), "kw_set_csr: FP32 value copy");
-    KW_CUDA(kw::launch_convert_f64_to_f32(val_dev, (float*)ctx->val32.p, nnz, ctx->stream), "kw_set_csr: convert");
+    KW_CUDA(ctx->inexact.ensure(sizeof(unsigned long long)), "kw_set_csr: counter");
+    KW_CUDA(cudaMemsetAsync(ctx->inexact.p, 0, sizeof(unsigned long long), ctx->stream), "kw_set_csr: memset");
+    KW_CUDA(kw::launch_convert_f64_to_f32(val_dev, (float*)ctx->val32.p, nnz, (unsigned long long*)ctx->inexact.p,
+                                          ctx->stream), "kw_set_csr: convert");
+    unsigned long long bad = 0;
+    KW_CUDA(cudaMemcpyAsync(&bad, ctx->inexact.p, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream), "kw_set_csr: read");
+    KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_set_csr: sync");
+    ctx->val32_exact = bad == 0;
   }
   return KW_OK;
 }
 
 }  // extern "C"
+
+static size_t part_doubles(const kw_ctx* ctx, int64_t K) {
+  return std::max<size_t>({(size_t)kw::kMaxBlocksPerSM * ctx->num_sms * (3 + 2 * KW_MAX_PROJ),
+                           (size_t)K * 4, (size_t)4 * ctx->num_sms * (KW_MAX_PROJ + 1)});
+}
+
+// Work descriptor holding only what the SpMV kernel needs.
+static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
+  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
+  memset(&w, 0, sizeof(w));
+  w.prec = c32 ? kw::PREC_C32 : kw::PREC_F64;
+  w.m = ctx->m;
+  w.rowptr = ctx->rowptr;
+  w.col = ctx->col;
+  w.val_f32 = c32 ? 1 : val_f32;
+  w.val = w.val_f32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
+  w.spmv_lanes = lanes;
+  w.stream = ctx->stream;
+  w.num_sms = ctx->num_sms;
+  w.part = (double*)ctx->part.p;
+  w.st = (kw::State*)ctx->st.p;
+}
+
+// Autotuner for K1: time every (lanes per row, value type) candidate on the
+// current operator with CUDA events and keep the fastest.
+static kw_status tune_spmv(kw_ctx* ctx) {
+  if (ctx->spmv_lanes > 0) return KW_OK;
+  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
+  const size_t vs = c32 ? 8 : 16;
+  KW_CUDA(ctx->rA.ensure(ctx->m * vs), "tune alloc");
+  KW_CUDA(ctx->q.ensure(ctx->m * vs), "tune alloc");
+  KW_CUDA(ctx->part.ensure(part_doubles(ctx, 1) * 8), "tune alloc");
+  KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "tune alloc");
+  KW_CUDA(ctx->tdot.ensure(16), "tune alloc");
+  KW_CUDA(cudaMemsetAsync(ctx->rA.p, 0, ctx->m * vs, ctx->stream), "tune memset");
+  KW_CUDA(cudaMemsetAsync(ctx->st.p, 0, sizeof(kw::State), ctx->stream), "tune memset");
+  const int lane_opts[] = {1, 2, 4, 8, 16};
+  int vals[2] = {0, 1}, nvals = 1;
+  if (c32) vals[0] = 1;
+  else if (ctx->val32_exact) nvals = 2;
+  if (ctx->force_val >= 0 && !c32) {
+    vals[0] = (ctx->force_val && ctx->val32_exact) ? 1 : 0;
+    nvals = 1;
+  }
+  cudaEvent_t e0, e1;
+  KW_CUDA(cudaEventCreate(&e0), "tune event");
+  KW_CUDA(cudaEventCreate(&e1), "tune event");
+  float best = 1e30f;
+  int best_l = 4, best_v = vals[0];
+  for (int vi = 0; vi < nvals; ++vi) {
+    for (int l : lane_opts) {
+      if (ctx->force_lanes > 0 && l != ctx->force_lanes) continue;
+      kw::Work w;
+      spmv_work(ctx, w, l, vals[vi]);
+      const double2 zs = make_double2(0.5, 0.5);
+      cudaError_t e = c32 ? kw::launch_spmv_dot<kw::PREC_C32>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p)
+                          : kw::launch_spmv_dot<kw::PREC_F64>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
+      if (e != cudaSuccess) break;
+      cudaEventRecord(e0, ctx->stream);
+      for (int rep = 0; rep < 3; ++rep) {
+        if (c32) kw::launch_spmv_dot<kw::PREC_C32>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
+        else kw::launch_spmv_dot<kw::PREC_F64>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
+      }
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_l = l;
+        best_v = vals[vi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  KW_CUDA(cudaGetLastError(), "tune launches");
+  ctx->spmv_lanes = best_l;
+  ctx->spmv_val_f32 = best_v;
+  return KW_OK;
+}
 
 // Allocate the workspace of one solve and fill the Work descriptor.
 static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t K, const kw_c128* z_host,
@@ -204,21 +299,16 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.tol = ctx->opt.tol;
   w.rowptr = ctx->rowptr;
   w.col = ctx->col;
-  w.val = c32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
-  w.spmv_lanes = pick_lanes(m, ctx->nnz);
+  w.val_f32 = c32 ? 1 : ctx->spmv_val_f32;
+  w.val = w.val_f32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
+  w.spmv_lanes = ctx->spmv_lanes;
   w.b = b_dev;
   w.left = left_dev;
   w.stream = ctx->stream;
   w.num_sms = ctx->num_sms;
-  w.nblk_spmv = 8 * ctx->num_sms;
-  w.nblk_seed = 2 * ctx->num_sms;
-  w.nblk_shift = (int)((K + 63) / 64);
-  w.nblk_xp = 8 * ctx->num_sms;
-
   const int npw = std::max(w.nproj, 1);
   const int64_t nrecmax = ctx->opt.hist_stride > 0 ? ctx->opt.hist_max : 0;
-  const size_t part_d = std::max<size_t>({(size_t)w.nblk_spmv * 2, (size_t)w.nblk_seed * (3 + 2 * KW_MAX_PROJ),
-                                          (size_t)w.nblk_shift * 4, (size_t)4 * ctx->num_sms * (KW_MAX_PROJ + 1)});
+  const size_t part_d = part_doubles(ctx, K);
   const size_t Ks = (size_t)K, Ms = (size_t)m;
   struct {
     DBuf* b;
@@ -286,16 +376,36 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   return KW_OK;
 }
 
+// Accumulate the sampled kernel times of one chunk (its events are complete).
+static void collect_times(kw_ctx* ctx, int slot, bool full) {
+  float ms[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i) {
+    if (i == 3 && !full) break;
+    if (cudaEventElapsedTime(&ms[i], ctx->kev[slot][i], ctx->kev[slot][i + 1]) != cudaSuccess) return;
+  }
+  for (int i = 0; i < 4; ++i) ctx->stats.kernel_ms[i] += ms[i];
+  ctx->stats.timed_iters += 1;
+}
+
 template <int P>
 static kw_status run(kw_ctx* ctx, kw::Work& w) {
   KW_CUDA(kw::launch_init<P>(w), "init kernels");
+  ctx->stats.launches += w.full ? 5 : 4;
   const int CH = 16;
+  const bool timing = ctx->timing_every > 0;
   int64_t launched = 0;
   int slot = 0;
   bool have_prev = false;
+  int64_t sampled_at[2] = {-1, -1};
   for (;;) {
+    sampled_at[slot] = -1;
     for (int i = 0; i < CH; ++i) {
-      KW_CUDA(kw::launch_iteration<P>(w, (int)(launched & 1)), "iteration launch");
+      cudaEvent_t* ev = nullptr;
+      if (timing && i == 0 && (launched / CH) % ctx->timing_every == 0) {
+        ev = ctx->kev[slot];
+        sampled_at[slot] = launched;
+      }
+      KW_CUDA(kw::launch_iteration<P>(w, (int)(launched & 1), ev, &ctx->stats.launches), "iteration launch");
       ++launched;
     }
     KW_CUDA(cudaMemcpyAsync(ctx->flags_host + slot, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
@@ -304,6 +414,8 @@ static kw_status run(kw_ctx* ctx, kw::Work& w) {
     if (have_prev) {
       KW_CUDA(cudaEventSynchronize(ctx->ev[slot ^ 1]), "event sync");
       if (ctx->flags_host[slot ^ 1]) break;
+      // the previous chunk ran entirely before the stop flag: its sample is a real iteration
+      if (sampled_at[slot ^ 1] >= 0) collect_times(ctx, slot ^ 1, w.full);
     }
     have_prev = true;
     slot ^= 1;
@@ -327,7 +439,10 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
     if (!isfinite(z_host[k].re) || !isfinite(z_host[k].im))
       return fail(ctx, KW_ERR_ARG, "kw_solve: shift %lld is not finite", (long long)k);
   kw::Work w;
-  kw_status s = prepare(ctx, w, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
+  memset(&ctx->stats, 0, sizeof(ctx->stats));
+  kw_status s = tune_spmv(ctx);
+  if (s != KW_OK) return s;
+  s = prepare(ctx, w, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
   if (s != KW_OK) return s;
   s = (w.prec == kw::PREC_C32) ? run<kw::PREC_C32>(ctx, w) : run<kw::PREC_F64>(ctx, w);
   if (s != KW_OK) return s;
@@ -426,27 +541,51 @@ kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec
   return KW_OK;
 }
 
+kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every) {
+  if (!ctx || every < 0) return KW_ERR_ARG;
+  if (every > 0 && !ctx->kev[0][0]) {
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 5; ++j) KW_CUDA(cudaEventCreate(&ctx->kev[i][j]), "kernel timing events");
+  }
+  ctx->timing_every = every;
+  return KW_OK;
+}
+
+kw_status kw_set_spmv_config(kw_ctx* ctx, int lanes, int val_f32) {
+  if (!ctx || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16) || val_f32 < -1 ||
+      val_f32 > 1)
+    return KW_ERR_ARG;
+  ctx->force_lanes = lanes;
+  ctx->force_val = val_f32;
+  ctx->spmv_lanes = 0;
+  return KW_OK;
+}
+
+kw_status kw_get_spmv_config(kw_ctx* ctx, int* lanes, int* val_f32) {
+  if (!ctx || !lanes || !val_f32) return KW_ERR_ARG;
+  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_get_spmv_config: kw_set_csr has not been called");
+  kw_status s = tune_spmv(ctx);
+  if (s != KW_OK) return s;
+  *lanes = ctx->spmv_lanes;
+  *val_f32 = ctx->opt.prec == KW_C32V_F64S ? 1 : ctx->spmv_val_f32;
+  return KW_OK;
+}
+
+kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out) {
+  if (!ctx || !out) return KW_ERR_ARG;
+  *out = ctx->stats;
+  return KW_OK;
+}
+
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host) {
   if (!ctx) return KW_ERR_ARG;
   if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: kw_set_csr has not been called");
   if (!r_dev || !q_dev || !t_host) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: NULL pointer");
   const bool c32 = ctx->opt.prec == KW_C32V_F64S;
+  kw_status ts = tune_spmv(ctx);
+  if (ts != KW_OK) return ts;
   kw::Work w;
-  memset(&w, 0, sizeof(w));
-  w.prec = c32 ? kw::PREC_C32 : kw::PREC_F64;
-  w.m = ctx->m;
-  w.rowptr = ctx->rowptr;
-  w.col = ctx->col;
-  w.val = c32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
-  w.spmv_lanes = pick_lanes(ctx->m, ctx->nnz);
-  w.stream = ctx->stream;
-  w.num_sms = ctx->num_sms;
-  w.nblk_spmv = 8 * ctx->num_sms;
-  KW_CUDA(ctx->part.ensure(std::max<size_t>(ctx->part.cap, (size_t)w.nblk_spmv * 2 * 8)), "alloc partials");
-  KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "alloc state");
-  KW_CUDA(ctx->tdot.ensure(16), "alloc dot");
-  w.part = (double*)ctx->part.p;
-  w.st = (kw::State*)ctx->st.p;
+  spmv_work(ctx, w, ctx->spmv_lanes, ctx->spmv_val_f32);
   KW_CUDA(cudaMemsetAsync(&w.st->cnt_spmv, 0, sizeof(unsigned int), ctx->stream), "reset counter");
   const double2 z2 = make_double2(zs.re, zs.im);
   cudaError_t e = c32 ? kw::launch_spmv_dot<kw::PREC_C32>(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p)

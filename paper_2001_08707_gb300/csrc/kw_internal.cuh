@@ -61,7 +61,8 @@ struct Work {
   const int64_t* rowptr;
   const int32_t* col;
   const void* val;   // double* (F64) or float* (C32)
-  int spmv_lanes;    // lanes per row in K1
+  int spmv_lanes;    // lanes per row in K1 (1 = one thread per row)
+  int val_f32;       // matrix values stored as FP32 (always in C32 mode; in F64 mode when lossless)
   // seed vectors
   void* rA;          // two rotating residual buffers and q
   void* rB;
@@ -87,7 +88,6 @@ struct Work {
   void* P;           // full mode [K][m]
   // reduction scratch
   double* part;
-  int nblk_spmv, nblk_seed, nblk_shift, nblk_xp;
   State* st;
   cudaStream_t stream;
   int num_sms;
@@ -95,10 +95,14 @@ struct Work {
 
 // Launchers implemented per precision (kw_kernels_f64.cu / kw_kernels_c32.cu).
 template <int P> cudaError_t launch_init(Work& w);
-template <int P> cudaError_t launch_iteration(Work& w, int parity);
+template <int P> cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* launches);
 template <int P> cudaError_t launch_project_x(Work& w, double2* out);
 template <int P> cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, double2* t_dev);
-cudaError_t launch_convert_f64_to_f32(const double* in, float* out, int64_t n, cudaStream_t s);
+cudaError_t launch_convert_f64_to_f32(const double* in, float* out, int64_t n, unsigned long long* inexact,
+                                      cudaStream_t s);
+
+// Upper bound on resident 256-thread blocks per SM (2048 threads per SM).
+constexpr int kMaxBlocksPerSM = 8;
 
 // Scratch needed by the reduction kernels (doubles).
 int64_t part_doubles(const Work& w);

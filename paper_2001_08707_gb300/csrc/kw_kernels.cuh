@@ -21,6 +21,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "kw_internal.cuh"
 
 namespace kw {
@@ -146,19 +148,23 @@ struct SpmvMode {
   double2* t_out;    // standalone: result
 };
 
-template <int P, int G>
+template <int P, class RV, int G>
 __global__ void __launch_bounds__(256)
 k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
-           const typename PT<P>::R* __restrict__ val, const typename PT<P>::V* __restrict__ r,
+           const RV* __restrict__ val, const typename PT<P>::V* __restrict__ r,
            typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  typedef typename PT<P>::R R;
+  typedef typename PT<P>::R R;   // arithmetic type of the products
   typedef typename PT<P>::A A;
   double2 zs, sc = make_double2(1.0, 0.0);
+  bool scaled = false;
   if (mode.solver) {
     if (st->done) return;
     zs = st->zs;
-    if (st->vec_scale_pending) sc = st->scale_rn;
+    if (st->vec_scale_pending) {
+      sc = st->scale_rn;
+      scaled = true;
+    }
   } else {
     zs = mode.zs;
   }
@@ -169,18 +175,36 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
 
   A c_re = 0, c_im = 0;      // FP32 (or FP64) partial over <= CHUNK rows
-  double t_re = 0, t_im = 0; // FP64 total, only lane 0 of each warp uses it
+  double t_re = 0, t_im = 0; // FP64 total
   int in_chunk = 0;
   for (int base = warp_global * RPW; base < m; base += nwarps * RPW) {
     const int row = base + gw;
     V acc = vzero<V>();
     if (row < m) {
       const int beg = (int)rowptr[row], end = (int)rowptr[row + 1];
-      for (int j = beg + sub; j < end; j += G) {
-        const R v = val[j];
-        const V x = r[col[j]];
-        acc.x += v * x.x;
-        acc.y += v * x.y;
+      if (G == 1) {
+        int j = beg;
+        for (; j + 1 < end; j += 2) {        // two independent gathers in flight
+          const R v0 = (R)val[j], v1 = (R)val[j + 1];
+          const V x0 = r[col[j]], x1 = r[col[j + 1]];
+          acc.x += v0 * x0.x;
+          acc.y += v0 * x0.y;
+          acc.x += v1 * x1.x;
+          acc.y += v1 * x1.y;
+        }
+        if (j < end) {
+          const R v = (R)val[j];
+          const V x = r[col[j]];
+          acc.x += v * x.x;
+          acc.y += v * x.y;
+        }
+      } else {
+        for (int j = beg + sub; j < end; j += G) {
+          const R v = (R)val[j];
+          const V x = r[col[j]];
+          acc.x += v * x.x;
+          acc.y += v * x.y;
+        }
       }
     }
 #pragma unroll
@@ -189,10 +213,14 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       acc.y += __shfl_xor_sync(KW_FULL_MASK, acc.y, off);
     }
     if (sub == 0 && row < m) {
-      const V ri = r[row];
-      const V qi = cmul(scv, csub(cmul(zsv, ri), acc));   // s (z_s r - H r)
+      V ri = r[row];
+      V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
+      if (scaled) {                           // lazy seed switch: r <- s r, q <- s q
+        qi = cmul(scv, qi);
+        ri = cmul(scv, ri);
+      }
       q[row] = qi;
-      const V pr = cmul(cmul(scv, ri), qi);               // (s r)^T q, unconjugated
+      const V pr = cmul(ri, qi);              // r^T q, unconjugated
       c_re += pr.x;
       c_im += pr.y;
     }
@@ -270,29 +298,49 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
   for (int i = 0; i < N; ++i) chunk[i] = tot[i] = 0;
   int in_chunk = 0;
   const int stride = gridDim.x * blockDim.x;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-    V rn = rn_buf[i];
-    V rm = rm_buf[i];
-    const V qi = q[i];
-    if (pend) {               // lazy seed switch: bring r_n, r_{n-1} to the new seed
-      rn = cmul(s1, rn);
-      rm = cmul(s0, rm);
-      rn_buf[i] = rn;
+  // Two elements per trip, all loads issued before any store.
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += 2 * stride) {
+    const int i1 = i0 + stride;
+    const bool has1 = i1 < m;
+    V rn0 = rn_buf[i0], rm0 = rm_buf[i0];
+    const V q0 = q[i0];
+    V rn1 = vzero<V>(), rm1 = vzero<V>(), q1 = vzero<V>();
+    if (has1) {
+      rn1 = rn_buf[i1];
+      rm1 = rm_buf[i1];
+      q1 = q[i1];
     }
-    const V r1 = csub(csub(cmul(opc, rn), cmul(av, qi)), cmul(cv, rm));
-    rm_buf[i] = r1;
-    chunk[0] += r1.x * r1.x - r1.y * r1.y;   // r^T r (unconjugated)
-    chunk[1] += 2 * r1.x * r1.y;
-    chunk[2] += r1.x * r1.x + r1.y * r1.y;   // r^dagger r
+    R a0[NP > 0 ? NP : 1], a1[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int l = 0; l < NP; ++l) {
+      a0[l] = (l < np) ? proj[(size_t)l * m + i0] : (R)0;
+      a1[l] = (l < np && has1) ? proj[(size_t)l * m + i1] : (R)0;
+    }
+    if (pend) {               // lazy seed switch: bring r_n, r_{n-1} to the new seed
+      rn0 = cmul(s1, rn0);
+      rm0 = cmul(s0, rm0);
+      rn_buf[i0] = rn0;
+      if (has1) {
+        rn1 = cmul(s1, rn1);
+        rm1 = cmul(s0, rm1);
+        rn_buf[i1] = rn1;
+      }
+    }
+    const V r10 = csub(csub(cmul(opc, rn0), cmul(av, q0)), cmul(cv, rm0));
+    const V r11 = csub(csub(cmul(opc, rn1), cmul(av, q1)), cmul(cv, rm1));   // zero when !has1
+    rm_buf[i0] = r10;
+    if (has1) rm_buf[i1] = r11;
+    chunk[0] += (r10.x * r10.x - r10.y * r10.y) + (r11.x * r11.x - r11.y * r11.y);   // r^T r
+    chunk[1] += 2 * (r10.x * r10.y + r11.x * r11.y);
+    chunk[2] += (r10.x * r10.x + r10.y * r10.y) + (r11.x * r11.x + r11.y * r11.y);   // r^dagger r
 #pragma unroll
     for (int l = 0; l < NP; ++l) {
       if (l < np) {
-        const R a = proj[(size_t)l * m + i];
-        chunk[3 + 2 * l] += a * r1.x;
-        chunk[4 + 2 * l] += a * r1.y;
+        chunk[3 + 2 * l] += a0[l] * r10.x + a1[l] * r11.x;
+        chunk[4 + 2 * l] += a0[l] * r10.y + a1[l] * r11.y;
       }
     }
-    if (CHUNKED && ++in_chunk == PT<P>::CHUNK) {
+    if (CHUNKED && (in_chunk += 2) >= PT<P>::CHUNK) {
 #pragma unroll
       for (int k = 0; k < N; ++k) { tot[k] += chunk[k]; chunk[k] = 0; }
       in_chunk = 0;
@@ -339,78 +387,94 @@ struct ShiftArgs {
   double* part;      // per block: [best |pi|^2, best index, n still active]
 };
 
-static __global__ void __launch_bounds__(64) k_shift(ShiftArgs a, State* st) {
+// One warp per block, LPS lanes per shift (LPS = 1 in full mode, else the
+// projection count rounded up to a power of two, at most 32): the lanes of a
+// shift compute its scalars redundantly and update one projection row each, so
+// the FP64 work spreads over many SMs.
+template <int LPS>
+__global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   if (st->done) return;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int SPW = 32 / LPS;   // shifts per warp
+  const int lane = threadIdx.x, sub = lane % LPS;
+  const int k = blockIdx.x * SPW + lane / LPS;
   const double2 alpha = st->alpha, c = st->c, beta = st->beta, zs = st->zs;
-  const double sqrt_nu = sqrt(st->nu);
+  const double nu = st->nu, thresh = st->thresh;
   const int pend = st->pi_rescale_pending, jnew = st->new_seed;
+  const double2 i1 = st->inv_pj1, i0 = st->inv_pj0;
   const long long iter = st->iter;
   const bool rec = st->hist_stride > 0 && ((iter + 1) % st->hist_stride) == 0 && st->n_rec < st->hist_max;
+  const long long rec_row = st->n_rec;
+  const bool inK = k < a.K;
+  const bool act = inK && a.active[k];
 
   double best = INFINITY;
-  int best_k = 0x7fffffff, still = 0, brk = 0;
-  if (k < a.K && a.active[k]) {
-    // warp-aggregated slot in the compacted list of shifts updated this iteration
-    const unsigned act = __activemask();
-    const int leader = __ffs(act) - 1, rank = __popc(act & ((1u << (threadIdx.x & 31)) - 1));
-    int basepos = 0;
-    if ((int)(threadIdx.x & 31) == leader) basepos = atomicAdd(&st->n_list, __popc(act));
-    basepos = __shfl_sync(act, basepos, leader);
-    a.list[basepos + rank] = k;
-
+  int best_k = 0x7fffffff, still = 0, brk = 0, in_list = 0;
+  if (act) {
     double2 p1 = a.pi1[k], p0 = a.pi0[k];
+    const double2 zk = a.z[k];
     if (pend) {                       // lazy rescale after a seed switch
       if (k == jnew) {
         p1 = p0 = make_double2(1.0, 0.0);
       } else {
-        p1 = cmul(p1, st->inv_pj1);
-        p0 = cmul(p0, st->inv_pj0);
+        p1 = cmul(p1, i1);
+        p0 = cmul(p0, i0);
       }
     }
-    const double2 sigma = csub(a.z[k], zs);
+    const double2 sigma = csub(zk, zs);
     // pi_{n+1} = (1 + c_n + alpha_n sigma) pi_n - c_n pi_{n-1}          (Eq. 20)
     const double2 f = cadd(make_double2(1.0 + c.x, c.y), cmul(alpha, sigma));
     const double2 pn = csub(cmul(f, p1), cmul(c, p0));
+    in_list = (sub == 0);
     if (pn.x == 0.0 && pn.y == 0.0) {
       brk = 1;
     } else {
-      const double2 ratio = cdiv(p1, pn);             // pi_n / pi_{n+1}
+      const double2 ipn = crecip(pn);                 // 1 / pi_{n+1}
+      const double2 ratio = cmul(p1, ipn);            // pi_n / pi_{n+1}
       const double2 ak = cmul(ratio, alpha);          // Eq. 21
       const double2 bk = cmul(cmul(ratio, ratio), beta);  // Eq. 22
-      const double2 ipn = crecip(pn);
       if (a.full) {
-        a.coef[3 * k + 0] = ak;
-        a.coef[3 * k + 1] = bk;
-        a.coef[3 * k + 2] = ipn;
+        if (sub == 0) {
+          a.coef[3 * k + 0] = ak;
+          a.coef[3 * k + 1] = bk;
+          a.coef[3 * k + 2] = ipn;
+        }
       } else {
-        for (int l = 0; l < a.np; ++l) {              // Eq. 25-26
+        for (int l = sub; l < a.np; l += LPS) {       // Eq. 25-26
           const size_t o = (size_t)k * a.np + l;
-          const double2 u = a.U[o];
-          a.Y[o] = cadd(a.Y[o], cmul(ak, u));
-          a.U[o] = cadd(cmul(a.w[l], ipn), cmul(bk, u));
+          const double2 u = a.U[o], y = a.Y[o], wl = a.w[l];
+          a.Y[o] = cadd(y, cmul(ak, u));
+          a.U[o] = cadd(cmul(wl, ipn), cmul(bk, u));
         }
       }
-      a.pi0[k] = p1;
-      a.pi1[k] = pn;
-      const double res = sqrt_nu / hypot(pn.x, pn.y);
-      a.final_res[k] = res;
-      if (res <= st->thresh) {
-        a.active[k] = 0;
-        a.conv_iter[k] = iter + 1;
-      } else {
-        still = 1;
-        best = __dadd_rn(__dmul_rn(pn.x, pn.x), __dmul_rn(pn.y, pn.y));
-        best_k = k;
+      const double res = sqrt(nu * (ipn.x * ipn.x + ipn.y * ipn.y));   // ||r|| / |pi_{n+1}|
+      if (sub == 0) {
+        a.pi0[k] = p1;
+        a.pi1[k] = pn;
+        a.final_res[k] = res;
+        if (rec) a.hist[(size_t)rec_row * a.K + k] = res;
+        if (res <= thresh) {
+          a.active[k] = 0;
+          a.conv_iter[k] = iter + 1;
+        } else {
+          still = 1;
+          best = __dadd_rn(__dmul_rn(pn.x, pn.x), __dmul_rn(pn.y, pn.y));
+          best_k = k;
+        }
       }
     }
+  } else if (rec && inK && sub == 0) {
+    a.hist[(size_t)rec_row * a.K + k] = a.final_res[k];
   }
-  if (rec && k < a.K) a.hist[(size_t)st->n_rec * a.K + k] = a.final_res[k];
+  // compacted list of the shifts updated this iteration (one slot per shift)
+  {
+    const unsigned bal = __ballot_sync(KW_FULL_MASK, in_list);
+    int basepos = 0;
+    if (lane == 0 && bal) basepos = atomicAdd(&st->n_list, __popc(bal));
+    basepos = __shfl_sync(KW_FULL_MASK, basepos, 0);
+    if (in_list) a.list[basepos + __popc(bal & ((1u << lane) - 1))] = k;
+  }
 
-  // block argmin of |pi_{n+1}|^2 over still-active shifts (ties: lowest index) and count
-  __shared__ double sb[2];
-  __shared__ int sk[2], sc[2], sbrk[2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // warp argmin of |pi_{n+1}|^2 over still-active shifts (ties: lowest index), count, breakdown
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const double ob = __shfl_xor_sync(KW_FULL_MASK, best, off);
@@ -419,72 +483,81 @@ static __global__ void __launch_bounds__(64) k_shift(ShiftArgs a, State* st) {
     still += __shfl_xor_sync(KW_FULL_MASK, still, off);
     brk |= __shfl_xor_sync(KW_FULL_MASK, brk, off);
   }
-  if (lane == 0) { sb[warp] = best; sk[warp] = best_k; sc[warp] = still; sbrk[warp] = brk; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int wi = 1; wi < (int)(blockDim.x >> 5); ++wi) {
-      if (sb[wi] < sb[0] || (sb[wi] == sb[0] && sk[wi] < sk[0])) { sb[0] = sb[wi]; sk[0] = sk[wi]; }
-      sc[0] += sc[wi];
-      sbrk[0] |= sbrk[wi];
-    }
-    a.part[4 * blockIdx.x + 0] = sb[0];
-    a.part[4 * blockIdx.x + 1] = (double)sk[0];
-    a.part[4 * blockIdx.x + 2] = (double)sc[0];
-    a.part[4 * blockIdx.x + 3] = (double)sbrk[0];
+  if (lane == 0) {
+    a.part[4 * blockIdx.x + 0] = best;
+    a.part[4 * blockIdx.x + 1] = (double)best_k;
+    a.part[4 * blockIdx.x + 2] = (double)still;
+    a.part[4 * blockIdx.x + 3] = (double)brk;
   }
   if (!arrive_last(&st->cnt_shift)) return;
 
-  if (threadIdx.x == 0) {
-    st->cnt_shift = 0;
-    double gb = INFINITY;
-    int gk = 0x7fffffff;
-    long long n_still = 0;
-    int any_brk = 0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      const double vb = __ldcg(a.part + 4 * b);
-      const int vk = (int)__ldcg(a.part + 4 * b + 1);
-      if (vb < gb || (vb == gb && vk < gk)) { gb = vb; gk = vk; }
-      n_still += (long long)__ldcg(a.part + 4 * b + 2);
-      any_brk |= (int)__ldcg(a.part + 4 * b + 3);
-    }
-    st->pi_rescale_pending = 0;
-    if (rec) st->n_rec += 1;
-    const int nl = *((volatile int*)&st->n_list);
-    st->updates += nl;
-    st->xp_pending = (a.full && nl > 0 && !any_brk) ? 1 : 0;
-    st->n_active = (int)n_still;
-    double2 rho1 = st->rho1;
-    double2 boa = cdiv(st->beta, st->alpha);          // beta_n / alpha_n
-    if (any_brk) {                                      // pi_{n+1} = 0 (Eq. 20)
-      set_fail(st, KW_ERR_BREAKDOWN);
-      return;
-    }
-    if (st->seed_switch && n_still > 0 && gb < 1.0) {  // Sec. 2.2.4
-      const double2 pj1 = __ldcg(a.pi1 + gk), pj0 = __ldcg(a.pi0 + gk);
-      const double2 i1 = crecip(pj1), i0 = crecip(pj0);
-      st->scale_rn = i1;                 // r_{n+1} <- r_{n+1} / pi^j_{n+1}
-      st->scale_rnm1 = i0;               // r_n     <- r_n / pi^j_n
-      st->vec_scale_pending = 1;
-      rho1 = cmul(rho1, cmul(i1, i1));   // rho_{n+1} of the rescaled residual
-      boa = cmul(boa, cmul(pj0, i1));    // beta^j_n / alpha^j_n
-      st->inv_pj1 = i1;
-      st->inv_pj0 = i0;
-      st->pi_rescale_pending = 1;
-      st->new_seed = gk;
-      st->seed = gk;
-      st->zs = a.z[gk];
-      st->n_seed_switch += 1;
-    }
-    st->rho = rho1;
-    st->boa = boa;
-    st->iter = st->iter + 1;
-    if (n_still == 0) {
-      st->status = KW_OK;
-      st->done = 1;
-    } else if (st->iter >= st->maxiter) {
-      st->status = KW_NOT_CONVERGED;
-      st->done = 1;
-    }
+  // last block: the lanes reduce the block partials in parallel
+  double gb = INFINITY;
+  int gk = 0x7fffffff, any_brk = 0;
+  long long n_still = 0;
+  for (int b = lane; b < (int)gridDim.x; b += 32) {
+    const double vb = __ldcg(a.part + 4 * b);
+    const int vk = (int)__ldcg(a.part + 4 * b + 1);
+    if (vb < gb || (vb == gb && vk < gk)) { gb = vb; gk = vk; }
+    n_still += (long long)__ldcg(a.part + 4 * b + 2);
+    any_brk |= (int)__ldcg(a.part + 4 * b + 3);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(KW_FULL_MASK, gb, off);
+    const int ok = __shfl_xor_sync(KW_FULL_MASK, gk, off);
+    if (ob < gb || (ob == gb && ok < gk)) { gb = ob; gk = ok; }
+    n_still += __shfl_xor_sync(KW_FULL_MASK, n_still, off);
+    any_brk |= __shfl_xor_sync(KW_FULL_MASK, any_brk, off);
+  }
+  if (lane != 0) return;
+  const int nl = *((volatile int*)&st->n_list);
+  const bool do_switch = st->seed_switch && n_still > 0 && gb < 1.0;
+  const double2 rho1_in = st->rho1;
+  const long long upd = st->updates, maxiter = st->maxiter;
+  const int nsw = st->n_seed_switch;
+  double2 pj1 = make_double2(1.0, 0.0), pj0 = pj1, zj = pj1;
+  if (do_switch) {
+    pj1 = __ldcg(a.pi1 + gk);
+    pj0 = __ldcg(a.pi0 + gk);
+    zj = a.z[gk];
+  }
+  st->cnt_shift = 0;
+  st->pi_rescale_pending = 0;
+  if (rec) st->n_rec = rec_row + 1;
+  st->updates = upd + nl;
+  st->xp_pending = (a.full && nl > 0 && !any_brk) ? 1 : 0;
+  st->n_active = (int)n_still;
+  if (any_brk) {                                        // pi_{n+1} = 0 (Eq. 20)
+    set_fail(st, KW_ERR_BREAKDOWN);
+    return;
+  }
+  double2 rho1 = rho1_in;
+  double2 boa = cdiv(beta, alpha);                      // beta_n / alpha_n
+  if (do_switch) {                                      // Sec. 2.2.4
+    const double2 ii1 = crecip(pj1), ii0 = crecip(pj0);
+    st->scale_rn = ii1;                  // r_{n+1} <- r_{n+1} / pi^j_{n+1}
+    st->scale_rnm1 = ii0;                // r_n     <- r_n / pi^j_n
+    st->vec_scale_pending = 1;
+    rho1 = cmul(rho1, cmul(ii1, ii1));   // rho_{n+1} of the rescaled residual
+    boa = cmul(boa, cmul(pj0, ii1));     // beta^j_n / alpha^j_n
+    st->inv_pj1 = ii1;
+    st->inv_pj0 = ii0;
+    st->pi_rescale_pending = 1;
+    st->new_seed = gk;
+    st->seed = gk;
+    st->zs = zj;
+    st->n_seed_switch = nsw + 1;
+  }
+  st->rho = rho1;
+  st->boa = boa;
+  st->iter = iter + 1;
+  if (n_still == 0) {
+    st->status = KW_OK;
+    st->done = 1;
+  } else if (iter + 1 >= maxiter) {
+    st->status = KW_NOT_CONVERGED;
+    st->done = 1;
   }
 }
 
@@ -642,37 +715,67 @@ k_project_x(int m, int np, const double* __restrict__ b, const double* __restric
   for (int l = threadIdx.x; l < np; l += blockDim.x) out[(size_t)k * np + l] = make_double2(red[2 * l], red[2 * l + 1]);
 }
 
-static __global__ void k_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
+// out = (float)in; *inexact counts the values that FP32 does not represent exactly.
+static __global__ void k_f64_to_f32(const double* __restrict__ in, float* __restrict__ out, int64_t n,
+                                    unsigned long long* inexact) {
+  unsigned long long bad = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float f = (float)in[i];
+    out[i] = f;
+    bad += ((double)f != in[i]);
+  }
+  bad = warp_sum(bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(inexact, bad);
 }
 
 // ================================================================ launchers
-template <int P, int G>
+// Blocks that fit on the device at once for a kernel with the given block size.
+template <class F>
+static int resident_blocks(F kernel, int threads, int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return per_sm * num_sms;
+}
+
+template <int P, class RV, int G>
 static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  typedef typename PT<P>::R R;
-  k_spmv_dot<P, G><<<w.nblk_spmv, 256, 0, w.stream>>>((int)w.m, w.rowptr, w.col, (const R*)w.val,
-                                                      (const V*)r, (V*)q, w.st, w.part, mode);
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_spmv_dot<P, RV, G>, 256, w.num_sms);
+  const int need = (int)((w.m * G + 255) / 256);   // no more blocks than rows need
+  const int grid = std::max(1, std::min(nblk, need));
+  k_spmv_dot<P, RV, G><<<grid, 256, 0, w.stream>>>((int)w.m, w.rowptr, w.col, (const RV*)w.val,
+                                                   (const V*)r, (V*)q, w.st, w.part, mode);
   return cudaGetLastError();
+}
+
+template <int P, class RV>
+static cudaError_t spmv_dispatch_v(Work& w, const void* r, void* q, SpmvMode mode) {
+  switch (w.spmv_lanes) {
+    case 1: return spmv_launch<P, RV, 1>(w, r, q, mode);
+    case 2: return spmv_launch<P, RV, 2>(w, r, q, mode);
+    case 4: return spmv_launch<P, RV, 4>(w, r, q, mode);
+    case 8: return spmv_launch<P, RV, 8>(w, r, q, mode);
+    case 16: return spmv_launch<P, RV, 16>(w, r, q, mode);
+    default: return spmv_launch<P, RV, 32>(w, r, q, mode);
+  }
 }
 
 template <int P>
 static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
-  switch (w.spmv_lanes) {
-    case 2: return spmv_launch<P, 2>(w, r, q, mode);
-    case 4: return spmv_launch<P, 4>(w, r, q, mode);
-    case 8: return spmv_launch<P, 8>(w, r, q, mode);
-    case 16: return spmv_launch<P, 16>(w, r, q, mode);
-    default: return spmv_launch<P, 32>(w, r, q, mode);
-  }
+  if (P == PREC_C32 || w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);
+  return spmv_dispatch_v<P, double>(w, r, q, mode);
 }
 
 template <int P, int NP>
 static cudaError_t seed_launch(Work& w, void* rn, void* rm) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
-  k_seed_update<P, NP><<<w.nblk_seed, 256, 0, w.stream>>>((int)w.m, (V*)rn, (const V*)w.q, (V*)rm,
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_seed_update<P, NP>, 256, w.num_sms);
+  const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
+  k_seed_update<P, NP><<<grid, 256, 0, w.stream>>>((int)w.m, (V*)rn, (const V*)w.q, (V*)rm,
                                                           (const R*)w.proj_rows, w.nproj, w.st, w.part, w.w);
   return cudaGetLastError();
 }
@@ -688,19 +791,26 @@ static cudaError_t seed_dispatch(Work& w, void* rn, void* rm) {
   return seed_launch<P, KW_MAX_PROJ>(w, rn, rm);
 }
 
+// One iteration: K1..K4 on the work stream.  If ev is not NULL, ev[0..4] are
+// recorded before K1 and after each kernel (ev[4] after K3 in projected mode).
 template <int P>
-cudaError_t launch_iteration(Work& w, int parity) {
+cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* launches) {
   typedef typename PT<P>::V V;
   // parity 0: r_n in rA, r_{n-1} in rB; parity 1: swapped.  K2 writes r_{n+1} over r_{n-1}.
   void* rn = parity ? w.rB : w.rA;
   void* rm = parity ? w.rA : w.rB;
+  cudaError_t e;
+#define KW_MARK(i) \
+  if (ev && (e = cudaEventRecord(ev[i], w.stream)) != cudaSuccess) return e;
+  KW_MARK(0);
   SpmvMode mode;
   mode.solver = 1;
   mode.zs = make_double2(0.0, 0.0);
   mode.t_out = nullptr;
-  cudaError_t e = spmv_dispatch<P>(w, rn, w.q, mode);
-  if (e != cudaSuccess) return e;
+  if ((e = spmv_dispatch<P>(w, rn, w.q, mode)) != cudaSuccess) return e;
+  KW_MARK(1);
   if ((e = seed_dispatch<P>(w, rn, rm)) != cudaSuccess) return e;
+  KW_MARK(2);
   ShiftArgs a;
   a.K = w.K;
   a.np = w.nproj;
@@ -718,13 +828,31 @@ cudaError_t launch_iteration(Work& w, int parity) {
   a.hist = w.hist;
   a.list = w.list;
   a.part = w.part;
-  k_shift<<<w.nblk_shift, 64, 0, w.stream>>>(a, w.st);
+  const int lps = w.full ? 1 : (w.nproj <= 1 ? 1 : w.nproj <= 2 ? 2 : w.nproj <= 4 ? 4 : w.nproj <= 8 ? 8
+                                                                     : w.nproj <= 16 ? 16 : 32);
+  const int spw = 32 / lps;
+  const int nb3 = (w.K + spw - 1) / spw;
+  switch (lps) {
+    case 1: k_shift<1><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+    case 2: k_shift<2><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+    case 4: k_shift<4><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+    case 8: k_shift<8><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+    case 16: k_shift<16><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+    default: k_shift<32><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  KW_MARK(3);
+  *launches += 3;
   if (w.full) {
-    k_update_xp<P, 8><<<w.nblk_xp, 256, 0, w.stream>>>((int)w.m, w.list, w.coef, (V*)w.X, (V*)w.P,
+    static int nblk_xp = 0;
+    if (nblk_xp == 0) nblk_xp = resident_blocks(k_update_xp<P, 8>, 256, w.num_sms);
+    k_update_xp<P, 8><<<nblk_xp, 256, 0, w.stream>>>((int)w.m, w.list, w.coef, (V*)w.X, (V*)w.P,
                                                        (const V*)rm, w.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *launches += 1;
   }
+  KW_MARK(4);
+#undef KW_MARK
   return cudaSuccess;
 }
 

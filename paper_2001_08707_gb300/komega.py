@@ -40,6 +40,10 @@ class kw_solve_info(C.Structure):
                 ("n_seed_switch", C.c_int64), ("updates", C.c_int64), ("seed", C.c_int64), ("status", C.c_int)]
 
 
+class kw_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("timed_iters", C.c_int64), ("kernel_ms", C.c_double * 4)]
+
+
 _lib = None
 
 
@@ -66,6 +70,10 @@ def load_library(path: str = LIB_PATH):
         "kw_get_shift_status": (C.c_int, [P, P, P]),
         "kw_get_residual_history": (C.c_int, [P, P, C.POINTER(I64)]),
         "kw_spmv_dot": (C.c_int, [P, kw_c128, P, P, C.POINTER(kw_c128)]),
+        "kw_set_kernel_timing": (C.c_int, [P, I64]),
+        "kw_get_stats": (C.c_int, [P, C.POINTER(kw_stats)]),
+        "kw_set_spmv_config": (C.c_int, [P, C.c_int, C.c_int]),
+        "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +241,30 @@ class Solver:
             if st != KW_OK:
                 raise self._err(st, "kw_get_residual_history")
         return h
+
+    def set_kernel_timing(self, every: int):
+        st = self._lib.kw_set_kernel_timing(self._ctx, every)
+        if st != KW_OK:
+            raise self._err(st, "kw_set_kernel_timing")
+
+    def set_spmv_config(self, lanes: int = 0, val_f32: int = -1):
+        st = self._lib.kw_set_spmv_config(self._ctx, lanes, val_f32)
+        if st != KW_OK:
+            raise self._err(st, "kw_set_spmv_config")
+
+    def spmv_config(self):
+        l, v = C.c_int(), C.c_int()
+        st = self._lib.kw_get_spmv_config(self._ctx, C.byref(l), C.byref(v))
+        if st != KW_OK:
+            raise self._err(st, "kw_get_spmv_config")
+        return l.value, v.value
+
+    def stats(self) -> dict:
+        s = kw_stats()
+        st = self._lib.kw_get_stats(self._ctx, C.byref(s))
+        if st != KW_OK:
+            raise self._err(st, "kw_get_stats")
+        return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms)}
 
     def spmv_dot(self, zs: complex, r, q):
         """q = zs r - H r and t = r^T q on the device (r, q: device complex tensors)."""
