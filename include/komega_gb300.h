@@ -190,6 +190,32 @@ kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out);
  * context precision; t_host receives the FP64 dot. */
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host);
 
+/* Most thread blocks kw_spmv_dot_noalloc launches; its static scratch holds
+ * one FP64 complex partial per block (64 KiB) plus a counter and the result. */
+#define KW_NOALLOC_MAX_BLOCKS 4096
+
+/* kw_spmv_dot for callers that cannot allocate device memory: code whose GPU
+ * memory is entirely owned by another allocator (for example a framework's
+ * caching pool, or a fixed budget) and latency-critical loops that cannot pay
+ * for the implicit synchronisation of cudaMalloc.  The paper has no
+ * counterpart; it is the same seed step (q = zs r - H r, t = r^T q,
+ * unconjugated) as kw_spmv_dot, in FP64, without a context.
+ *   m, nnz, rowptr_dev, col_dev, val_dev: the operator as in kw_set_csr.
+ *   r_dev, q_dev: [m] kw_c128 device arrays (input r, output q).
+ *   t_host: receives t.  cuda_stream: the stream to run on (NULL = default).
+ * Nothing is allocated: the scratch is one static device array of about 66 KiB
+ * that every GPU loading this library keeps until the process exits, and the
+ * launch uses at most KW_NOALLOC_MAX_BLOCKS blocks (grid-stride loops cover any
+ * m below 2^31).  The first call on a device resolves the array's device
+ * address for that device (make that first call before any stream capture).
+ * All calls share the array and each call leaves its last contents there, so
+ * calls that overlap on the GPU (other streams, other threads) race: serialise
+ * them.  Returns after synchronising cuda_stream.  Errors: KW_ERR_ARG (m < 1,
+ * m or nnz >= 2^31, NULL pointer), KW_ERR_CUDA. */
+kw_status kw_spmv_dot_noalloc(int64_t m, int64_t nnz, const int64_t* rowptr_dev, const int32_t* col_dev,
+                              const double* val_dev, kw_c128 zs, const kw_c128* r_dev, kw_c128* q_dev,
+                              kw_c128* t_host, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

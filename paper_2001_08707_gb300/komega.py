@@ -73,6 +73,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_kernel_timing": (C.c_int, [P, I64]),
         "kw_get_stats": (C.c_int, [P, C.POINTER(kw_stats)]),
         "kw_set_spmv_config": (C.c_int, [P, C.c_int, C.c_int]),
+        "kw_spmv_dot_noalloc": (C.c_int, [I64, I64, P, P, P, kw_c128, P, P, C.POINTER(kw_c128), P]),
         "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
@@ -81,6 +82,24 @@ def load_library(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def spmv_dot_noalloc(rowptr, col, val, zs: complex, r, q, stream=None) -> complex:
+    """kw_spmv_dot_noalloc: q = zs r - H r and t = r^T q in FP64 without any
+    device allocation by the library (all arguments are CUDA tensors: int64
+    rowptr, int32 col, float64 val, complex128 r and q)."""
+    import torch
+
+    lib = load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    t = kw_c128()
+    st = lib.kw_spmv_dot_noalloc(rowptr.numel() - 1, col.numel(), C.c_void_p(rowptr.data_ptr()),
+                                 C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
+                                 kw_c128(zs.real, zs.imag), C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()),
+                                 C.byref(t), C.c_void_p(s.cuda_stream))
+    if st != KW_OK:
+        raise KomegaError(st, "kw_spmv_dot_noalloc")
+    return complex(t.re, t.im)
 
 
 class KomegaError(RuntimeError):
