@@ -53,10 +53,18 @@ typedef enum {
 
 typedef enum {
     KW_F64 = 0,         /* complex FP64 vectors, FP64 matrix values, FP64 scalars */
-    KW_C32V_F64S = 1    /* complex FP32 vectors and FP32 matrix values; dots
+    KW_C32V_F64S = 1,   /* complex FP32 vectors and FP32 matrix values; dots
                            accumulated in FP64 over FP32 chunk partials; every
                            seed and shift scalar (alpha, beta, rho, pi) and the
                            convergence test in FP64 */
+    KW_DF64 = 2         /* complex vectors as FP32 pairs (hi, lo): a 48-bit
+                           significand computed with error-free FP32 operations
+                           (TwoSum, TwoProd) on the FP32 pipes; matrix values
+                           FP32 when exact, else FP32 pairs; FP64 scalars and
+                           convergence test.  Element layout in device memory:
+                           4 floats (re.hi, re.lo, im.hi, im.lo), 16 bytes.
+                           Values below about 1e-30 lose precision (FP32
+                           exponent range). */
 } kw_precision;
 
 typedef struct { double re, im; } kw_c128;
@@ -121,7 +129,8 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
  *   nleft       number of left vectors a_l (0 .. KW_MAX_PROJ-1).
  *   left_dev    float64 [nleft][m] row-major, or NULL when nleft = 0.
  *   x_out_dev   full mode: [nshift][m] complex in the context precision
- *               (kw_c128 for KW_F64, float2 for KW_C32V_F64S), receives x_k.
+ *               (kw_c128 for KW_F64 and KW_DF64, float2 for KW_C32V_F64S),
+ *               receives x_k.
  *               NULL selects projected mode (Eq. 25-26): no x_k is formed.
  *   proj_out_host kw_c128 [nshift][nleft+1] or NULL; column 0 = b^T x_k,
  *               column l = a_{l-1}^T x_k (a real, so a^dagger = a^T).
@@ -172,7 +181,8 @@ kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
 
 /* Configuration of the sparse product kernel.  lanes = threads per matrix
  * row (1, 2, 4, 8 or 16; 0 = choose by timing every candidate on the current
- * operator at the next solve, the default).  val_f32 (KW_F64 mode only): 1 =
+ * operator at the next solve, the default; operators with fewer than 2^20
+ * non-zeros are not timed and use 1).  val_f32 (KW_F64 mode only): 1 =
  * read the matrix values from an FP32 copy, allowed only when every value is
  * exactly representable in FP32 (checked by kw_set_csr; otherwise FP64 is
  * used); 0 = FP64 values; -1 = choose by timing.  Errors: KW_ERR_ARG. */
@@ -187,7 +197,8 @@ kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out);
 /* One seed matrix-vector step (Alg. 1 "q = H r" combined with the seed shift,
  * and the first dot of Eq. 17): q = zs r - H r and t = r^T q (unconjugated),
  * with the context's operator and precision.  r_dev, q_dev: [m] complex in the
- * context precision; t_host receives the FP64 dot. */
+ * context precision (KW_DF64: the 4-float pair layout); t_host receives the
+ * FP64 dot. */
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host);
 
 /* Most thread blocks kw_spmv_dot_noalloc launches; its static scratch holds

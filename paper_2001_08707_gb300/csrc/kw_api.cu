@@ -19,6 +19,17 @@
 
 namespace {
 
+// Bytes of a complex vector element and of a real projection-row element.
+size_t vec_bytes(kw_precision p) { return p == KW_C32V_F64S ? 8 : 16; }
+size_t real_bytes(kw_precision p) { return p == KW_C32V_F64S ? 4 : 8; }
+int prec_id(kw_precision p) { return p == KW_C32V_F64S ? kw::PREC_C32 : p == KW_DF64 ? kw::PREC_DF : kw::PREC_F64; }
+
+// FP32-pair image of a complex FP64 scalar, computed on the host.
+float4 host_pair(double re, double im) {
+  const float rh = (float)re, ih = (float)im;
+  return make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+}
+
 // Device buffer that only grows.
 struct DBuf {
   void* p = nullptr;
@@ -53,6 +64,7 @@ struct kw_ctx {
   const int32_t* col = nullptr;
   const double* val = nullptr;
   DBuf val32;
+  DBuf valpair;               // FP32-pair copy of the values (KW_DF64, values not exact in FP32)
   DBuf inexact;
   bool val32_exact = false;   // every value representable in FP32
   int spmv_lanes = 0;         // tuned or forced lanes per row (0 = tune at first use)
@@ -61,8 +73,8 @@ struct kw_ctx {
   // host-solve copies
   DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
   // workspace
-  DBuf rA, rB, q, proj_rows, z, pi1, pi0, active, conv_iter, final_res, coef, Y, U, w, w0, hist, list, X, P,
-      part, st, projx, tdot;
+  DBuf rA, rB, q, proj_rows, z, pi1, pi0, active, conv_iter, final_res, coef, coef_pair, Y, U, w, w0, hist, list,
+      X, P, part, st, projx, tdot;
   kw::State* st_host = nullptr;   // pinned
   int* flags_host = nullptr;      // pinned, two slots
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -129,7 +141,7 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
   if (!out || !opt) return KW_ERR_ARG;
   *out = nullptr;
   if (!(opt->tol >= 0.0) || opt->maxiter < 1 || opt->hist_stride < 0 || opt->hist_max < 0 ||
-      (opt->prec != KW_F64 && opt->prec != KW_C32V_F64S))
+      (opt->prec != KW_F64 && opt->prec != KW_C32V_F64S && opt->prec != KW_DF64))
     return KW_ERR_ARG;
   kw_ctx* ctx = new kw_ctx();
   ctx->opt = *opt;
@@ -152,7 +164,7 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
 void kw_destroy(kw_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
-  DBuf* bufs[] = {&ctx->val32, &ctx->inexact, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
+  DBuf* bufs[] = {&ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot};
@@ -196,6 +208,10 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
     KW_CUDA(cudaMemcpyAsync(&bad, ctx->inexact.p, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream), "kw_set_csr: read");
     KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_set_csr: sync");
     ctx->val32_exact = bad == 0;
+    if (ctx->opt.prec == KW_DF64 && !ctx->val32_exact) {
+      KW_CUDA(ctx->valpair.ensure((size_t)nnz * 8), "kw_set_csr: FP32-pair value copy");
+      KW_CUDA(kw::launch_convert_f64_to_pair(val_dev, ctx->valpair.p, nnz, ctx->stream), "kw_set_csr: convert");
+    }
   }
   return KW_OK;
 }
@@ -209,14 +225,17 @@ static size_t part_doubles(const kw_ctx* ctx, int64_t K) {
 
 // Work descriptor holding only what the SpMV kernel needs.
 static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
-  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
+  const kw_precision p = ctx->opt.prec;
   memset(&w, 0, sizeof(w));
-  w.prec = c32 ? kw::PREC_C32 : kw::PREC_F64;
+  w.prec = prec_id(p);
   w.m = ctx->m;
   w.rowptr = ctx->rowptr;
   w.col = ctx->col;
-  w.val_f32 = c32 ? 1 : val_f32;
-  w.val = w.val_f32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
+  if (p == KW_C32V_F64S) w.val_f32 = 1;
+  else if (p == KW_DF64) w.val_f32 = ctx->val32_exact ? 1 : 0;
+  else w.val_f32 = val_f32;
+  w.val = w.val_f32 ? (const void*)ctx->val32.p
+                    : (p == KW_DF64 ? (const void*)ctx->valpair.p : (const void*)ctx->val);
   w.spmv_lanes = lanes;
   w.stream = ctx->stream;
   w.num_sms = ctx->num_sms;
@@ -224,12 +243,31 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.st = (kw::State*)ctx->st.p;
 }
 
+static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 zs, double2* t) {
+  if (!w.st || !w.part || !t || !w.rowptr) return cudaErrorInvalidValue;   // workspace must exist
+  const float4 zp = host_pair(zs.x, zs.y);
+  switch (w.prec) {
+    case kw::PREC_C32: return kw::launch_spmv_dot<kw::PREC_C32>(w, r, q, zs, zp, t);
+    case kw::PREC_DF: return kw::launch_spmv_dot<kw::PREC_DF>(w, r, q, zs, zp, t);
+    default: return kw::launch_spmv_dot<kw::PREC_F64>(w, r, q, zs, zp, t);
+  }
+}
+
 // Autotuner for K1: time every (lanes per row, value type) candidate on the
 // current operator with CUDA events and keep the fastest.
+// Operators below this many non-zeros are not timed (launch overhead dominates
+// and the pick would be noise); they use one thread per row and FP64 values.
+static const int64_t kTuneMinNnz = 1 << 20;
+
 static kw_status tune_spmv(kw_ctx* ctx) {
   if (ctx->spmv_lanes > 0) return KW_OK;
-  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
-  const size_t vs = c32 ? 8 : 16;
+  const kw_precision p = ctx->opt.prec;
+  if (ctx->nnz < kTuneMinNnz) {
+    ctx->spmv_lanes = ctx->force_lanes > 0 ? ctx->force_lanes : 1;
+    ctx->spmv_val_f32 = (p == KW_F64 && ctx->force_val == 1 && ctx->val32_exact) ? 1 : 0;
+    return KW_OK;
+  }
+  const size_t vs = vec_bytes(p);
   KW_CUDA(ctx->rA.ensure(ctx->m * vs), "tune alloc");
   KW_CUDA(ctx->q.ensure(ctx->m * vs), "tune alloc");
   KW_CUDA(ctx->part.ensure(part_doubles(ctx, 1) * 8), "tune alloc");
@@ -238,10 +276,10 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   KW_CUDA(cudaMemsetAsync(ctx->rA.p, 0, ctx->m * vs, ctx->stream), "tune memset");
   KW_CUDA(cudaMemsetAsync(ctx->st.p, 0, sizeof(kw::State), ctx->stream), "tune memset");
   const int lane_opts[] = {1, 2, 4, 8, 16};
+  // value storage candidates: only the FP64 form has a choice (FP64 or exact FP32 values)
   int vals[2] = {0, 1}, nvals = 1;
-  if (c32) vals[0] = 1;
-  else if (ctx->val32_exact) nvals = 2;
-  if (ctx->force_val >= 0 && !c32) {
+  if (p == KW_F64 && ctx->val32_exact) nvals = 2;
+  if (p == KW_F64 && ctx->force_val >= 0) {
     vals[0] = (ctx->force_val && ctx->val32_exact) ? 1 : 0;
     nvals = 1;
   }
@@ -250,25 +288,22 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   KW_CUDA(cudaEventCreate(&e1), "tune event");
   float best = 1e30f;
   int best_l = 4, best_v = vals[0];
+  // Candidates are visited in a fixed order; a later one replaces the current
+  // pick only if it is more than 5% faster, so near-ties resolve the same way.
   for (int vi = 0; vi < nvals; ++vi) {
     for (int l : lane_opts) {
       if (ctx->force_lanes > 0 && l != ctx->force_lanes) continue;
       kw::Work w;
       spmv_work(ctx, w, l, vals[vi]);
       const double2 zs = make_double2(0.5, 0.5);
-      cudaError_t e = c32 ? kw::launch_spmv_dot<kw::PREC_C32>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p)
-                          : kw::launch_spmv_dot<kw::PREC_F64>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
-      if (e != cudaSuccess) break;
+      if (spmv_dot_launch(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p) != cudaSuccess) break;
       cudaEventRecord(e0, ctx->stream);
-      for (int rep = 0; rep < 3; ++rep) {
-        if (c32) kw::launch_spmv_dot<kw::PREC_C32>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
-        else kw::launch_spmv_dot<kw::PREC_F64>(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
-      }
+      for (int rep = 0; rep < 3; ++rep) spmv_dot_launch(w, ctx->rA.p, ctx->q.p, zs, (double2*)ctx->tdot.p);
       cudaEventRecord(e1, ctx->stream);
       cudaEventSynchronize(e1);
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
+      if (ms < 0.95f * best) {
         best = ms;
         best_l = l;
         best_v = vals[vi];
@@ -286,22 +321,15 @@ static kw_status tune_spmv(kw_ctx* ctx) {
 // Allocate the workspace of one solve and fill the Work descriptor.
 static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t K, const kw_c128* z_host,
                          int64_t nleft, const double* left_dev, void* x_out_dev) {
-  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
-  const size_t vs = c32 ? 8 : 16, rs = c32 ? 4 : 8;
+  const size_t vs = vec_bytes(ctx->opt.prec), rs = real_bytes(ctx->opt.prec);
   const int64_t m = ctx->m;
-  memset(&w, 0, sizeof(w));
-  w.prec = c32 ? kw::PREC_C32 : kw::PREC_F64;
+  spmv_work(ctx, w, ctx->spmv_lanes, ctx->spmv_val_f32);
   w.m = m;
   w.K = (int)K;
   w.full = x_out_dev != nullptr;
   w.nout = (int)nleft + 1;
   w.nproj = w.full ? 0 : (int)nleft + 1;
   w.tol = ctx->opt.tol;
-  w.rowptr = ctx->rowptr;
-  w.col = ctx->col;
-  w.val_f32 = c32 ? 1 : ctx->spmv_val_f32;
-  w.val = w.val_f32 ? (const void*)ctx->val32.p : (const void*)ctx->val;
-  w.spmv_lanes = ctx->spmv_lanes;
   w.b = b_dev;
   w.left = left_dev;
   w.stream = ctx->stream;
@@ -325,6 +353,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->conv_iter, Ks * 8},
       {&ctx->final_res, Ks * 8},
       {&ctx->coef, Ks * 48},
+      {&ctx->coef_pair, Ks * 48},
       {&ctx->Y, Ks * npw * 16},
       {&ctx->U, Ks * npw * 16},
       {&ctx->w, (size_t)KW_MAX_PROJ * 16},
@@ -348,6 +377,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.conv_iter = (long long*)ctx->conv_iter.p;
   w.final_res = (double*)ctx->final_res.p;
   w.coef = (double2*)ctx->coef.p;
+  w.coef_pair = (float4*)ctx->coef_pair.p;
   w.Y = (double2*)ctx->Y.p;
   w.U = (double2*)ctx->U.p;
   w.w = (double2*)ctx->w.p;
@@ -365,6 +395,8 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   s.zs = make_double2(z_host[0].re, z_host[0].im);
   s.boa = make_double2(0.0, 0.0);
   s.scale_rn = s.scale_rnm1 = make_double2(1.0, 0.0);
+  s.p_zs = host_pair(z_host[0].re, z_host[0].im);
+  s.p_s1 = s.p_s0 = host_pair(1.0, 0.0);
   s.seed = 0;
   s.seed_switch = ctx->opt.seed_switch ? 1 : 0;
   s.status = KW_NOT_CONVERGED;
@@ -444,7 +476,14 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
   if (s != KW_OK) return s;
   s = prepare(ctx, w, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
   if (s != KW_OK) return s;
-  s = (w.prec == kw::PREC_C32) ? run<kw::PREC_C32>(ctx, w) : run<kw::PREC_F64>(ctx, w);
+  s = w.prec == kw::PREC_C32 ? run<kw::PREC_C32>(ctx, w)
+      : w.prec == kw::PREC_DF ? run<kw::PREC_DF>(ctx, w)
+                              : run<kw::PREC_F64>(ctx, w);
+  if (s != KW_OK) return s;
+  if (w.full) {   // FP32-pair x is converted to FP64 in place (the caller's buffer holds kw_c128)
+    cudaError_t e = w.prec == kw::PREC_DF ? kw::launch_finish_x<kw::PREC_DF>(w) : cudaSuccess;
+    KW_CUDA(e, "finish x");
+  }
   if (s != KW_OK) return s;
   KW_CUDA(cudaMemcpy(ctx->st_host, w.st, sizeof(kw::State), cudaMemcpyDeviceToHost), "read state");
   const kw::State& st = *ctx->st_host;
@@ -452,8 +491,9 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
   ctx->last_nrec = st.n_rec;
   if (proj_out_host) {
     if (w.full) {
-      cudaError_t e = (w.prec == kw::PREC_C32) ? kw::launch_project_x<kw::PREC_C32>(w, (double2*)ctx->projx.p)
-                                                : kw::launch_project_x<kw::PREC_F64>(w, (double2*)ctx->projx.p);
+      cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_project_x<kw::PREC_C32>(w, (double2*)ctx->projx.p)
+                      : w.prec == kw::PREC_DF ? kw::launch_project_x<kw::PREC_DF>(w, (double2*)ctx->projx.p)
+                                              : kw::launch_project_x<kw::PREC_F64>(w, (double2*)ctx->projx.p);
       KW_CUDA(e, "projection of x");
       KW_CUDA(cudaMemcpyAsync(proj_out_host, ctx->projx.p, (size_t)nshift * w.nout * 16, cudaMemcpyDeviceToHost,
                               ctx->stream), "copy projections");
@@ -497,7 +537,7 @@ kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowp
   if (m < 1 || nnz < 0 || !rowptr_host || (nnz > 0 && (!col_host || !val_host)) || !b_host || nshift < 1 ||
       nleft < 0 || (nleft > 0 && !left_host))
     return fail(ctx, KW_ERR_ARG, "kw_solve_host: invalid sizes or NULL host arrays");
-  const size_t vs = ctx->opt.prec == KW_C32V_F64S ? 8 : 16;
+  const size_t vs = vec_bytes(ctx->opt.prec);
   KW_CUDA(ctx->h_rowptr.ensure((m + 1) * 8), "alloc rowptr");
   KW_CUDA(ctx->h_col.ensure(std::max<int64_t>(nnz, 1) * 4), "alloc col");
   KW_CUDA(ctx->h_val.ensure(std::max<int64_t>(nnz, 1) * 8), "alloc val");
@@ -567,7 +607,7 @@ kw_status kw_get_spmv_config(kw_ctx* ctx, int* lanes, int* val_f32) {
   kw_status s = tune_spmv(ctx);
   if (s != KW_OK) return s;
   *lanes = ctx->spmv_lanes;
-  *val_f32 = ctx->opt.prec == KW_C32V_F64S ? 1 : ctx->spmv_val_f32;
+  *val_f32 = ctx->opt.prec == KW_F64 ? ctx->spmv_val_f32 : (ctx->opt.prec == KW_C32V_F64S ? 1 : (ctx->val32_exact ? 1 : 0));
   return KW_OK;
 }
 
@@ -581,15 +621,16 @@ kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, k
   if (!ctx) return KW_ERR_ARG;
   if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: kw_set_csr has not been called");
   if (!r_dev || !q_dev || !t_host) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: NULL pointer");
-  const bool c32 = ctx->opt.prec == KW_C32V_F64S;
   kw_status ts = tune_spmv(ctx);
   if (ts != KW_OK) return ts;
+  KW_CUDA(ctx->part.ensure(part_doubles(ctx, 1) * 8), "alloc partials");
+  KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "alloc state");
+  KW_CUDA(ctx->tdot.ensure(16), "alloc dot");
   kw::Work w;
   spmv_work(ctx, w, ctx->spmv_lanes, ctx->spmv_val_f32);
   KW_CUDA(cudaMemsetAsync(&w.st->cnt_spmv, 0, sizeof(unsigned int), ctx->stream), "reset counter");
   const double2 z2 = make_double2(zs.re, zs.im);
-  cudaError_t e = c32 ? kw::launch_spmv_dot<kw::PREC_C32>(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p)
-                      : kw::launch_spmv_dot<kw::PREC_F64>(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p);
+  cudaError_t e = spmv_dot_launch(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p);
   KW_CUDA(e, "kw_spmv_dot launch");
   KW_CUDA(cudaMemcpyAsync(t_host, ctx->tdot.p, 16, cudaMemcpyDeviceToHost, ctx->stream), "read dot");
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_spmv_dot sync");

@@ -1,0 +1,265 @@
+// Arithmetic layer of the kernels: complex operations for the three vector
+// forms (double2: FP64; float2: FP32; dfc: FP32 pairs) and the accumulators of
+// the dot products.
+//
+// FP32-pair ("double-float") numbers represent x = hi + lo with |lo| <= ulp(hi)/2,
+// a 48-bit significand (relative rounding about 2^-48 = 3.6e-15) with FP32's
+// exponent range, computed entirely on the FP32 pipes.  The building blocks are
+// the error-free transformations of Knuth (TwoSum: a + b = s + e exactly) and
+// of Dekker/Ogita-Rump-Oishi with FMA (TwoProd: a * b = p + e exactly).  Each
+// operation uses explicitly rounded intrinsics so that no contraction or
+// reassociation can change it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace kw {
+
+struct __align__(8) df {
+  float hi, lo;
+};
+struct __align__(16) dfc {
+  df re, im;
+};
+
+// ------------------------------------------------------------- error-free transformations
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df fast_two_sum(float a, float b) {   // requires |a| >= |b| (or a == 0)
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+
+// ------------------------------------------------------------- FP32-pair real arithmetic
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+  p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+__device__ __forceinline__ df df_mul_f(df a, float b) {   // b an exact FP32 number
+  df p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+// a*b - c*d with one rounding of the leading parts
+__device__ __forceinline__ df df_fms(df a, df b, df c, df d) {
+  const df p = two_prod(a.hi, b.hi);
+  const df q = two_prod(c.hi, d.hi);
+  const df s = two_sum(p.hi, -q.hi);
+  float lo = __fadd_rn(s.lo, __fsub_rn(p.lo, q.lo));
+  lo = __fmaf_rn(a.hi, b.lo, lo);
+  lo = __fmaf_rn(a.lo, b.hi, lo);
+  lo = __fmaf_rn(-c.hi, d.lo, lo);
+  lo = __fmaf_rn(-c.lo, d.hi, lo);
+  return fast_two_sum(s.hi, lo);
+}
+// a*b + c*d
+__device__ __forceinline__ df df_fma2(df a, df b, df c, df d) { return df_fms(a, b, df_neg(c), d); }
+
+__device__ __forceinline__ df df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+// ------------------------------------------------------------- complex operations
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ dfc cmul(dfc a, dfc b) {
+  return {df_fms(a.re, b.re, a.im, b.im), df_fma2(a.re, b.im, a.im, b.re)};
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ dfc cadd(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ dfc csub(dfc a, dfc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+
+template <class V> __device__ __forceinline__ V vzero();
+template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ dfc vzero<dfc>() { return {{0.f, 0.f}, {0.f, 0.f}}; }
+
+// A complex FP64 scalar in the vector form.  `pair` is its FP32-pair form
+// (x = re.hi, y = re.lo, z = im.hi, w = im.lo), precomputed by whoever wrote
+// the scalar so that the kernels do no FP64 conversions per thread.
+template <class V> __device__ __forceinline__ V vscalar(double2 d, float4 pair);
+template <> __device__ __forceinline__ double2 vscalar<double2>(double2 d, float4) { return d; }
+template <> __device__ __forceinline__ float2 vscalar<float2>(double2, float4 p) { return make_float2(p.x, p.z); }
+template <> __device__ __forceinline__ dfc vscalar<dfc>(double2, float4 p) { return {{p.x, p.y}, {p.z, p.w}}; }
+
+// A complex vector element from a real FP64 value (initialisation only).
+template <class V> __device__ __forceinline__ V vreal(double x);
+template <> __device__ __forceinline__ double2 vreal<double2>(double x) { return make_double2(x, 0.0); }
+template <> __device__ __forceinline__ float2 vreal<float2>(double x) { return make_float2((float)x, 0.f); }
+template <> __device__ __forceinline__ dfc vreal<dfc>(double x) { return {df_from_double(x), {0.f, 0.f}}; }
+
+template <class V> __device__ __forceinline__ double2 vto_double(V v);
+template <> __device__ __forceinline__ double2 vto_double<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ double2 vto_double<float2>(float2 v) { return make_double2(v.x, v.y); }
+template <> __device__ __forceinline__ double2 vto_double<dfc>(dfc v) {
+  return make_double2(df_to_double(v.re), df_to_double(v.im));
+}
+
+// Real element types of matrix values and projection rows.
+template <class R> __device__ __forceinline__ R rfrom_double(double x);
+template <> __device__ __forceinline__ double rfrom_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ float rfrom_double<float>(double x) { return (float)x; }
+template <> __device__ __forceinline__ df rfrom_double<df>(double x) { return df_from_double(x); }
+
+// ------------------------------------------------------------- acc += v * x (real v, complex x)
+__device__ __forceinline__ void mac(double2& acc, double v, double2 x) {
+  acc.x = fma(v, x.x, acc.x);
+  acc.y = fma(v, x.y, acc.y);
+}
+__device__ __forceinline__ void mac(double2& acc, float v, double2 x) { mac(acc, (double)v, x); }
+__device__ __forceinline__ void mac(float2& acc, float v, float2 x) {
+  acc.x = fmaf(v, x.x, acc.x);
+  acc.y = fmaf(v, x.y, acc.y);
+}
+// FP32-pair accumulation with deferred normalisation: acc.hi collects the
+// rounded leading terms exactly through TwoSum, acc.lo the errors.
+__device__ __forceinline__ void mac_pair(df& acc, float v, df x) {
+  const df p = two_prod(v, x.hi);
+  const df s = two_sum(acc.hi, p.hi);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, __fmaf_rn(v, x.lo, p.lo)));
+}
+__device__ __forceinline__ void mac_pair(df& acc, df v, df x) {
+  const df p = two_prod(v.hi, x.hi);
+  const df s = two_sum(acc.hi, p.hi);
+  float e = __fmaf_rn(v.hi, x.lo, p.lo);
+  e = __fmaf_rn(v.lo, x.hi, e);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
+__device__ __forceinline__ void mac(dfc& acc, float v, dfc x) {
+  mac_pair(acc.re, v, x.re);
+  mac_pair(acc.im, v, x.im);
+}
+__device__ __forceinline__ void mac(dfc& acc, df v, dfc x) {
+  mac_pair(acc.re, v, x.re);
+  mac_pair(acc.im, v, x.im);
+}
+__device__ __forceinline__ dfc normalize(dfc a) {
+  return {fast_two_sum(a.re.hi, a.re.lo), fast_two_sum(a.im.hi, a.im.lo)};
+}
+__device__ __forceinline__ double2 normalize(double2 a) { return a; }
+__device__ __forceinline__ float2 normalize(float2 a) { return a; }
+
+// ------------------------------------------------------------- dot-product accumulators
+// Accumulator type A: double (FP64 form), float (FP32 form, FP64 across chunks),
+// df (FP32-pair form).
+__device__ __forceinline__ void aadd(double& a, double v) { a += v; }
+__device__ __forceinline__ void aadd(float& a, float v) { a += v; }
+__device__ __forceinline__ void aadd(df& a, df v) { a = df_add(a, v); }
+
+// rho += r^T r (unconjugated): re += x^2 - y^2, im += 2 x y;  nrm += x^2 + y^2
+__device__ __forceinline__ void acc_rho_nrm(double& re, double& im, double& n, double2 r) {
+  re += r.x * r.x - r.y * r.y;
+  im += 2.0 * r.x * r.y;
+  n += r.x * r.x + r.y * r.y;
+}
+__device__ __forceinline__ void acc_rho_nrm(float& re, float& im, float& n, float2 r) {
+  re += r.x * r.x - r.y * r.y;
+  im += 2.f * r.x * r.y;
+  n += r.x * r.x + r.y * r.y;
+}
+__device__ __forceinline__ void acc_rho_nrm(df& re, df& im, df& n, dfc r) {
+  re = df_add(re, df_fms(r.re, r.re, r.im, r.im));
+  const df xy = df_mul(r.re, r.im);
+  im = df_add(im, {2.f * xy.hi, 2.f * xy.lo});
+  n = df_add(n, df_fma2(r.re, r.re, r.im, r.im));
+}
+// (re, im) += a * r  (real a)
+__device__ __forceinline__ void acc_proj(double& re, double& im, double a, double2 r) {
+  re = fma(a, r.x, re);
+  im = fma(a, r.y, im);
+}
+__device__ __forceinline__ void acc_proj(float& re, float& im, float a, float2 r) {
+  re = fmaf(a, r.x, re);
+  im = fmaf(a, r.y, im);
+}
+__device__ __forceinline__ void acc_proj(df& re, df& im, df a, dfc r) {
+  re = df_add(re, df_mul(a, r.re));
+  im = df_add(im, df_mul(a, r.im));
+}
+// (re, im) += p
+__device__ __forceinline__ void acc_cplx(double& re, double& im, double2 p) {
+  re += p.x;
+  im += p.y;
+}
+__device__ __forceinline__ void acc_cplx(float& re, float& im, float2 p) {
+  re += p.x;
+  im += p.y;
+}
+__device__ __forceinline__ void acc_cplx(df& re, df& im, dfc p) {
+  re = df_add(re, p.re);
+  im = df_add(im, p.im);
+}
+
+__device__ __forceinline__ double ato_double(double a) { return a; }
+__device__ __forceinline__ double ato_double(float a) { return (double)a; }
+__device__ __forceinline__ double ato_double(df a) { return df_to_double(a); }
+
+template <class A> __device__ __forceinline__ A azero();
+template <> __device__ __forceinline__ double azero<double>() { return 0.0; }
+template <> __device__ __forceinline__ float azero<float>() { return 0.f; }
+template <> __device__ __forceinline__ df azero<df>() { return {0.f, 0.f}; }
+
+#define KW_FULL_MASK 0xffffffffu
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(KW_FULL_MASK, v, o); }
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(KW_FULL_MASK, v, o); }
+__device__ __forceinline__ df shfl_xor(df v, int o) {
+  return {__shfl_xor_sync(KW_FULL_MASK, v.hi, o), __shfl_xor_sync(KW_FULL_MASK, v.lo, o)};
+}
+__device__ __forceinline__ void vshfl_add(double2& a, int o) {
+  a.x += shfl_xor(a.x, o);
+  a.y += shfl_xor(a.y, o);
+}
+__device__ __forceinline__ void vshfl_add(float2& a, int o) {
+  a.x += shfl_xor(a.x, o);
+  a.y += shfl_xor(a.y, o);
+}
+__device__ __forceinline__ void vshfl_add(dfc& a, int o) {
+  a.re = df_add(a.re, shfl_xor(a.re, o));
+  a.im = df_add(a.im, shfl_xor(a.im, o));
+}
+
+// Warp sum of an accumulator (every lane gets the result).
+template <class A> __device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) aadd(v, shfl_xor(v, off));
+  return v;
+}
+template <> __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(KW_FULL_MASK, v, off);
+  return v;
+}
+
+}  // namespace kw

@@ -28,6 +28,9 @@ struct State {
   // the rescaled r_n back.
   double2 scale_rn, scale_rnm1;
   double2 inv_pj1, inv_pj0;  // 1/pi^j_{n+1}, 1/pi^j_n for the lazy pi rescale in K3
+  // FP32-pair images (re.hi, re.lo, im.hi, im.lo) of the scalars the vector
+  // kernels use, written next to their FP64 values; the FP32 form uses the .hi parts.
+  float4 p_zs, p_alpha, p_c, p_opc, p_s1, p_s0;
   int vec_scale_pending;
   int pi_rescale_pending;
   int new_seed;
@@ -46,7 +49,7 @@ struct State {
   unsigned int pad1;
 };
 
-enum Prec { PREC_F64 = 0, PREC_C32 = 1 };
+enum Prec { PREC_F64 = 0, PREC_C32 = 1, PREC_DF = 2 };
 
 // Device buffers of one solve.  Vector buffers are void* and typed by precision.
 struct Work {
@@ -78,6 +81,7 @@ struct Work {
   long long* conv_iter;
   double* final_res;
   double2* coef;     // full mode: [K][3] = alpha^k, beta^k, 1/pi^k_{n+1}
+  float4* coef_pair; // the same as FP32 pairs
   double2* Y;        // projected: [K][nproj]
   double2* U;
   double2* w;        // [nproj] = P r_{n+1}
@@ -96,10 +100,13 @@ struct Work {
 // Launchers implemented per precision (kw_kernels_f64.cu / kw_kernels_c32.cu).
 template <int P> cudaError_t launch_init(Work& w);
 template <int P> cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* launches);
+template <int P> cudaError_t launch_finish_x(Work& w);
 template <int P> cudaError_t launch_project_x(Work& w, double2* out);
-template <int P> cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, double2* t_dev);
+template <int P>
+cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, float4 zs_pair, double2* t_dev);
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, int64_t n, unsigned long long* inexact,
                                       cudaStream_t s);
+cudaError_t launch_convert_f64_to_pair(const double* in, void* out, int64_t n, cudaStream_t s);
 
 // Upper bound on resident 256-thread blocks per SM (2048 threads per SM).
 constexpr int kMaxBlocksPerSM = 8;

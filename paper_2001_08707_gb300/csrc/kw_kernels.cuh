@@ -11,6 +11,13 @@
 //   K4 k_update_xp    full mode: x^k += alpha^k p^k; p^k = r_{n+1}/pi^k + beta^k p^k
 //                     (Eq. 23-24) for the compacted active shifts.
 //
+// Three vector forms share these kernels through kw_arith.cuh: FP64 (double2),
+// FP32 (float2; FP32 partials over at most 16 terms per lane, FP64 across
+// chunks, warps and blocks) and FP32 pairs (dfc, 48-bit significand on the FP32
+// pipes).  Every seed and shift scalar is FP64 in all three; kernels read the
+// FP32 / FP32-pair images of the scalars they need from the State, written by
+// the reduction tails, so no kernel converts FP64 scalars per thread.
+//
 // Every kernel reads the iteration state from device memory, so the host only
 // enqueues launches; no host synchronisation happens inside the loop.
 // Reductions are deterministic: fixed per-block partials summed in a fixed
@@ -22,19 +29,19 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
+#include "kw_arith.cuh"
 #include "kw_internal.cuh"
 
 namespace kw {
 
-#define KW_FULL_MASK 0xffffffffu
-
 template <int P> struct PT;
 template <> struct PT<PREC_F64> {
   typedef double2 V;   // complex vector element
-  typedef double R;    // matrix value / projection row element
+  typedef double R;    // projection-row element
   typedef double A;    // in-block accumulator
-  static const int CHUNK = 1 << 30;  // no chunking needed in FP64
+  static const int CHUNK = 1 << 30;  // no chunking in FP64
 };
 template <> struct PT<PREC_C32> {
   typedef float2 V;
@@ -42,28 +49,14 @@ template <> struct PT<PREC_C32> {
   typedef float A;
   static const int CHUNK = 16;       // FP32 partial over at most 16 terms per lane
 };
+template <> struct PT<PREC_DF> {
+  typedef dfc V;
+  typedef df R;
+  typedef df A;
+  static const int CHUNK = 1 << 30;
+};
 
-// ---------------------------------------------------------------- complex helpers
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-
-template <class V> __device__ __forceinline__ V vmake(double2 a);
-template <> __device__ __forceinline__ double2 vmake<double2>(double2 a) { return a; }
-template <> __device__ __forceinline__ float2 vmake<float2>(double2 a) {
-  return make_float2((float)a.x, (float)a.y);
-}
-template <class V> __device__ __forceinline__ V vzero();
-template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
-template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
-
+// ---------------------------------------------------------------- FP64 scalar helpers
 // Complex division a/b in FP64 (Smith's algorithm).
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
   if (fabs(b.x) >= fabs(b.y)) {
@@ -76,16 +69,15 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 crecip(double2 b) { return cdiv(make_double2(1.0, 0.0), b); }
 __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
-
-// ---------------------------------------------------------------- reductions
-template <class T> __device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(KW_FULL_MASK, v, off);
-  return v;
+// FP32-pair image of a complex FP64 scalar (x = re.hi, y = re.lo, z = im.hi, w = im.lo).
+__device__ __forceinline__ float4 pair_of(double2 a) {
+  const df r = df_from_double(a.x), i = df_from_double(a.y);
+  return make_float4(r.hi, r.lo, i.hi, i.lo);
 }
 
-// Sum N per-thread values over the block (FP32 or FP64 warp tree, then the
-// warps combined in FP64 in a fixed order).  Result valid in threads < N of
+// ---------------------------------------------------------------- reductions
+// Sum N per-thread accumulators over the block: warp trees in the accumulator
+// type, then the warps combined in FP64 in a fixed order.  Result valid in
 // `out` (shared).  Requires blockDim.x a multiple of 32, <= 1024.
 template <int N, class T>
 __device__ __forceinline__ void block_sum(const T (&v)[N], int n, double* out) {
@@ -94,8 +86,8 @@ __device__ __forceinline__ void block_sum(const T (&v)[N], int n, double* out) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (i < n) {
-      T s = warp_sum(v[i]);
-      if (lane == 0) sh[warp][i] = (double)s;
+      const T s = warp_sum(v[i]);
+      if (lane == 0) sh[warp][i] = ato_double(s);
     }
   }
   __syncthreads();
@@ -145,6 +137,7 @@ __device__ __forceinline__ void set_fail(State* st, int status) {
 struct SpmvMode {
   int solver;        // 1: inside the solve (reads z_s, pending scale, computes alpha)
   double2 zs;        // standalone: seed shift
+  float4 zs_pair;    // standalone: its FP32-pair image
   double2* t_out;    // standalone: result
 };
 
@@ -154,28 +147,26 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
            const RV* __restrict__ val, const typename PT<P>::V* __restrict__ r,
            typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  typedef typename PT<P>::R R;   // arithmetic type of the products
   typedef typename PT<P>::A A;
-  double2 zs, sc = make_double2(1.0, 0.0);
+  V zsv, scv = vzero<V>();
   bool scaled = false;
   if (mode.solver) {
     if (st->done) return;
-    zs = st->zs;
+    zsv = vscalar<V>(st->zs, st->p_zs);
     if (st->vec_scale_pending) {
-      sc = st->scale_rn;
+      scv = vscalar<V>(st->scale_rn, st->p_s1);
       scaled = true;
     }
   } else {
-    zs = mode.zs;
+    zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
-  const V zsv = vmake<V>(zs), scv = vmake<V>(sc);
   const int lane = threadIdx.x & 31, sub = lane % G, gw = lane / G;
   const int RPW = 32 / G;
   const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
 
-  A c_re = 0, c_im = 0;      // FP32 (or FP64) partial over <= CHUNK rows
-  double t_re = 0, t_im = 0; // FP64 total
+  A c_re = azero<A>(), c_im = azero<A>();  // partial over <= CHUNK rows
+  double t_re = 0, t_im = 0;               // FP64 total
   int in_chunk = 0;
   for (int base = warp_global * RPW; base < m; base += nwarps * RPW) {
     const int row = base + gw;
@@ -185,34 +176,20 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       if (G == 1) {
         int j = beg;
         for (; j + 1 < end; j += 2) {        // two independent gathers in flight
-          const R v0 = (R)val[j], v1 = (R)val[j + 1];
+          const RV v0 = val[j], v1 = val[j + 1];
           const V x0 = r[col[j]], x1 = r[col[j + 1]];
-          acc.x += v0 * x0.x;
-          acc.y += v0 * x0.y;
-          acc.x += v1 * x1.x;
-          acc.y += v1 * x1.y;
+          mac(acc, v0, x0);
+          mac(acc, v1, x1);
         }
-        if (j < end) {
-          const R v = (R)val[j];
-          const V x = r[col[j]];
-          acc.x += v * x.x;
-          acc.y += v * x.y;
-        }
+        if (j < end) mac(acc, val[j], r[col[j]]);
       } else {
-        for (int j = beg + sub; j < end; j += G) {
-          const R v = (R)val[j];
-          const V x = r[col[j]];
-          acc.x += v * x.x;
-          acc.y += v * x.y;
-        }
+        for (int j = beg + sub; j < end; j += G) mac(acc, val[j], r[col[j]]);
       }
     }
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) {
-      acc.x += __shfl_xor_sync(KW_FULL_MASK, acc.x, off);
-      acc.y += __shfl_xor_sync(KW_FULL_MASK, acc.y, off);
-    }
+    for (int off = G / 2; off > 0; off >>= 1) vshfl_add(acc, off);
     if (sub == 0 && row < m) {
+      acc = normalize(acc);
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
       if (scaled) {                           // lazy seed switch: r <- s r, q <- s q
@@ -220,23 +197,17 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
         ri = cmul(scv, ri);
       }
       q[row] = qi;
-      const V pr = cmul(ri, qi);              // r^T q, unconjugated
-      c_re += pr.x;
-      c_im += pr.y;
+      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
     if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
-      A s_re = warp_sum(c_re), s_im = warp_sum(c_im);
-      t_re += (double)s_re;
-      t_im += (double)s_im;
-      c_re = c_im = 0;
+      t_re += ato_double(warp_sum(c_re));
+      t_im += ato_double(warp_sum(c_im));
+      c_re = c_im = azero<A>();
       in_chunk = 0;
     }
   }
-  {
-    A s_re = warp_sum(c_re), s_im = warp_sum(c_im);
-    t_re += (double)s_re;
-    t_im += (double)s_im;
-  }
+  t_re += ato_double(warp_sum(c_re));
+  t_im += ato_double(warp_sum(c_im));
   __shared__ double red[2];
   {
     double v2[2] = {lane == 0 ? t_re : 0.0, lane == 0 ? t_im : 0.0};
@@ -270,6 +241,9 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
     }
     st->alpha = alpha;
     st->c = c;
+    st->p_alpha = pair_of(alpha);
+    st->p_c = pair_of(c);
+    st->p_opc = pair_of(make_double2(1.0 + c.x, c.y));
     st->n_list = 0;
   }
 }
@@ -285,17 +259,18 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
   typedef typename PT<P>::R R;
   typedef typename PT<P>::A A;
   constexpr int N = 3 + 2 * NP;
+  constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
   if (st->done) return;
-  const double2 alpha = st->alpha, c = st->c;
   const int pend = st->vec_scale_pending;
-  const V s1 = vmake<V>(st->scale_rn), s0 = vmake<V>(st->scale_rnm1);
-  const V opc = vmake<V>(make_double2(1.0 + c.x, c.y)), av = vmake<V>(alpha), cv = vmake<V>(c);
+  const V s1 = vscalar<V>(st->scale_rn, st->p_s1), s0 = vscalar<V>(st->scale_rnm1, st->p_s0);
+  const double2 c = st->c;
+  const V opc = vscalar<V>(make_double2(1.0 + c.x, c.y), st->p_opc);
+  const V av = vscalar<V>(st->alpha, st->p_alpha), cv = vscalar<V>(c, st->p_c);
   const int n = 3 + 2 * np;
 
-  constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
   A chunk[N], tot[N];
 #pragma unroll
-  for (int i = 0; i < N; ++i) chunk[i] = tot[i] = 0;
+  for (int i = 0; i < N; ++i) chunk[i] = tot[i] = azero<A>();
   int in_chunk = 0;
   const int stride = gridDim.x * blockDim.x;
   // Two elements per trip, all loads issued before any store.
@@ -313,8 +288,8 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
     R a0[NP > 0 ? NP : 1], a1[NP > 0 ? NP : 1];
 #pragma unroll
     for (int l = 0; l < NP; ++l) {
-      a0[l] = (l < np) ? proj[(size_t)l * m + i0] : (R)0;
-      a1[l] = (l < np && has1) ? proj[(size_t)l * m + i1] : (R)0;
+      a0[l] = (l < np) ? proj[(size_t)l * m + i0] : rfrom_double<R>(0.0);
+      a1[l] = (l < np && has1) ? proj[(size_t)l * m + i1] : rfrom_double<R>(0.0);
     }
     if (pend) {               // lazy seed switch: bring r_n, r_{n-1} to the new seed
       rn0 = cmul(s1, rn0);
@@ -330,24 +305,29 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
     const V r11 = csub(csub(cmul(opc, rn1), cmul(av, q1)), cmul(cv, rm1));   // zero when !has1
     rm_buf[i0] = r10;
     if (has1) rm_buf[i1] = r11;
-    chunk[0] += (r10.x * r10.x - r10.y * r10.y) + (r11.x * r11.x - r11.y * r11.y);   // r^T r
-    chunk[1] += 2 * (r10.x * r10.y + r11.x * r11.y);
-    chunk[2] += (r10.x * r10.x + r10.y * r10.y) + (r11.x * r11.x + r11.y * r11.y);   // r^dagger r
+    acc_rho_nrm(chunk[0], chunk[1], chunk[2], r10);
+    acc_rho_nrm(chunk[0], chunk[1], chunk[2], r11);
 #pragma unroll
     for (int l = 0; l < NP; ++l) {
       if (l < np) {
-        chunk[3 + 2 * l] += a0[l] * r10.x + a1[l] * r11.x;
-        chunk[4 + 2 * l] += a0[l] * r10.y + a1[l] * r11.y;
+        acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a0[l], r10);
+        acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a1[l], r11);
       }
     }
     if (CHUNKED && (in_chunk += 2) >= PT<P>::CHUNK) {
 #pragma unroll
-      for (int k = 0; k < N; ++k) { tot[k] += chunk[k]; chunk[k] = 0; }
+      for (int k = 0; k < N; ++k) {
+        aadd(tot[k], chunk[k]);
+        chunk[k] = azero<A>();
+      }
       in_chunk = 0;
     }
   }
 #pragma unroll
-  for (int k = 0; k < N; ++k) tot[k] = CHUNKED ? tot[k] + chunk[k] : chunk[k];
+  for (int k = 0; k < N; ++k) {
+    if (CHUNKED) aadd(tot[k], chunk[k]);
+    else tot[k] = chunk[k];
+  }
 
   __shared__ double red[N];
   block_sum<N, A>(tot, n, red);
@@ -378,7 +358,8 @@ struct ShiftArgs {
   int* active;
   long long* conv_iter;
   double* final_res;
-  double2* coef;     // full mode [K][3]
+  double2* coef;     // full mode [K][3]: alpha^k, beta^k, 1/pi^k_{n+1}
+  float4* coef_pair; // the same as FP32 pairs (read by K4 in the FP32 and FP32-pair forms)
   double2* Y;
   double2* U;
   const double2* w;  // P r_{n+1}
@@ -437,6 +418,9 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
           a.coef[3 * k + 0] = ak;
           a.coef[3 * k + 1] = bk;
           a.coef[3 * k + 2] = ipn;
+          a.coef_pair[3 * k + 0] = pair_of(ak);
+          a.coef_pair[3 * k + 1] = pair_of(bk);
+          a.coef_pair[3 * k + 2] = pair_of(ipn);
         }
       } else {
         for (int l = sub; l < a.np; l += LPS) {       // Eq. 25-26
@@ -538,6 +522,9 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
     const double2 ii1 = crecip(pj1), ii0 = crecip(pj0);
     st->scale_rn = ii1;                  // r_{n+1} <- r_{n+1} / pi^j_{n+1}
     st->scale_rnm1 = ii0;                // r_n     <- r_n / pi^j_n
+    st->p_s1 = pair_of(ii1);
+    st->p_s0 = pair_of(ii0);
+    st->p_zs = pair_of(zj);
     st->vec_scale_pending = 1;
     rho1 = cmul(rho1, cmul(ii1, ii1));   // rho_{n+1} of the rescaled residual
     boa = cmul(boa, cmul(pj0, ii1));     // beta^j_n / alpha^j_n
@@ -565,8 +552,8 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
 template <int P, int TS>
 __global__ void __launch_bounds__(256)
 k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coef,
-            typename PT<P>::V* __restrict__ X, typename PT<P>::V* __restrict__ Pv,
-            const typename PT<P>::V* __restrict__ r1, State* st) {
+            const float4* __restrict__ coef_pair, typename PT<P>::V* __restrict__ X,
+            typename PT<P>::V* __restrict__ Pv, const typename PT<P>::V* __restrict__ r1, State* st) {
   typedef typename PT<P>::V V;
   if (!st->xp_pending) return;
   const int nl = st->n_list;
@@ -582,9 +569,8 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
     if (threadIdx.x < nts) {
       const int k = list[t0 + threadIdx.x];
       ks[threadIdx.x] = k;
-      cs[threadIdx.x][0] = vmake<V>(coef[3 * k + 0]);
-      cs[threadIdx.x][1] = vmake<V>(coef[3 * k + 1]);
-      cs[threadIdx.x][2] = vmake<V>(coef[3 * k + 2]);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cs[threadIdx.x][j] = vscalar<V>(coef[3 * k + j], coef_pair[3 * k + j]);
     }
     __syncthreads();
     const int i = chunk * blockDim.x + threadIdx.x;
@@ -611,17 +597,16 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
 // ================================================================ initialisation
 template <int P>
 __global__ void k_init_vectors(int m, int np, const double* __restrict__ b, const double* __restrict__ left,
-                               typename PT<P>::V* rn, typename PT<P>::V* rm,
-                               typename PT<P>::R* proj) {
+                               typename PT<P>::V* rn, typename PT<P>::V* rm, typename PT<P>::R* proj) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
     const double bi = b[i];
-    rn[i] = vmake<V>(make_double2(bi, 0.0));
+    rn[i] = vreal<V>(bi);
     rm[i] = vzero<V>();
     if (np > 0) {
-      proj[i] = (R)bi;
-      for (int l = 1; l < np; ++l) proj[(size_t)l * m + i] = (R)left[(size_t)(l - 1) * m + i];
+      proj[i] = rfrom_double<R>(bi);
+      for (int l = 1; l < np; ++l) proj[(size_t)l * m + i] = rfrom_double<R>(left[(size_t)(l - 1) * m + i]);
     }
   }
 }
@@ -636,12 +621,12 @@ __global__ void k_init_xp(int m, int K, const double* __restrict__ b, typename P
        o += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(o % m);
     X[o] = vzero<V>();
-    Pv[o] = vmake<V>(make_double2(b[i], 0.0));
+    Pv[o] = vreal<V>(b[i]);
   }
 }
 
-// FP64 dots of b with b and with each projection row (from the caller's FP64 arrays):
-// out = [b^T b, a_1^T b, ...]; last block writes rho_0, ||b||, threshold and w0.
+// FP64 dots of b with b and with each left vector (from the caller's FP64 arrays):
+// last block writes rho_0 = b^T b, ||b||, the threshold and w0 = P b.
 template <int NPM>
 __global__ void __launch_bounds__(256)
 k_init_dots(int m, int np, const double* __restrict__ b, const double* __restrict__ left, double tol,
@@ -675,7 +660,7 @@ k_init_dots(int m, int np, const double* __restrict__ b, const double* __restric
 }
 
 static __global__ void k_init_shifts(int K, int np, double2* pi1, double2* pi0, int* active, long long* conv_iter,
-                              double* final_res, double2* Y, double2* U, const double2* w0) {
+                                     double* final_res, double2* Y, double2* U, const double2* w0) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= K) return;
   pi1[k] = pi0[k] = make_double2(1.0, 0.0);
@@ -700,19 +685,28 @@ k_project_x(int m, int np, const double* __restrict__ b, const double* __restric
   for (int l = 0; l < 2 * NPM; ++l) acc[l] = 0.0;
   const V* xk = X + (size_t)k * m;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const V x = xk[i];
+    const double2 x = vto_double(xk[i]);
 #pragma unroll
     for (int l = 0; l < NPM; ++l) {
       if (l < np) {
         const double a = (l == 0) ? b[i] : left[(size_t)(l - 1) * m + i];
-        acc[2 * l] += a * (double)x.x;
-        acc[2 * l + 1] += a * (double)x.y;
+        acc[2 * l] = fma(a, x.x, acc[2 * l]);
+        acc[2 * l + 1] = fma(a, x.y, acc[2 * l + 1]);
       }
     }
   }
   __shared__ double red[2 * NPM];
   block_sum<2 * NPM, double>(acc, 2 * np, red);
   for (int l = threadIdx.x; l < np; l += blockDim.x) out[(size_t)k * np + l] = make_double2(red[2 * l], red[2 * l + 1]);
+}
+
+// In-place conversion of FP32-pair complex vectors to FP64 complex (same 16 bytes):
+// hi + lo is exact in FP64.
+static __global__ void k_pairs_to_double(dfc* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const dfc v = x[i];
+    reinterpret_cast<double2*>(x)[i] = vto_double(v);
+  }
 }
 
 // out = (float)in; *inexact counts the values that FP32 does not represent exactly.
@@ -726,6 +720,11 @@ static __global__ void k_f64_to_f32(const double* __restrict__ in, float* __rest
   }
   bad = warp_sum(bad);
   if ((threadIdx.x & 31) == 0 && bad) atomicAdd(inexact, bad);
+}
+
+static __global__ void k_f64_to_pair(const double* __restrict__ in, df* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df_from_double(in[i]);
 }
 
 // ================================================================ launchers
@@ -757,15 +756,21 @@ static cudaError_t spmv_dispatch_v(Work& w, const void* r, void* q, SpmvMode mod
     case 2: return spmv_launch<P, RV, 2>(w, r, q, mode);
     case 4: return spmv_launch<P, RV, 4>(w, r, q, mode);
     case 8: return spmv_launch<P, RV, 8>(w, r, q, mode);
-    case 16: return spmv_launch<P, RV, 16>(w, r, q, mode);
-    default: return spmv_launch<P, RV, 32>(w, r, q, mode);
+    default: return spmv_launch<P, RV, 16>(w, r, q, mode);
   }
 }
 
 template <int P>
 static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
-  if (P == PREC_C32 || w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);
-  return spmv_dispatch_v<P, double>(w, r, q, mode);
+  if constexpr (P == PREC_F64) {
+    if (w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);
+    return spmv_dispatch_v<P, double>(w, r, q, mode);
+  } else if constexpr (P == PREC_C32) {
+    return spmv_dispatch_v<P, float>(w, r, q, mode);
+  } else {
+    if (w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);
+    return spmv_dispatch_v<P, df>(w, r, q, mode);
+  }
 }
 
 template <int P, int NP>
@@ -776,7 +781,7 @@ static cudaError_t seed_launch(Work& w, void* rn, void* rm) {
   if (nblk == 0) nblk = resident_blocks(k_seed_update<P, NP>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   k_seed_update<P, NP><<<grid, 256, 0, w.stream>>>((int)w.m, (V*)rn, (const V*)w.q, (V*)rm,
-                                                          (const R*)w.proj_rows, w.nproj, w.st, w.part, w.w);
+                                                   (const R*)w.proj_rows, w.nproj, w.st, w.part, w.w);
   return cudaGetLastError();
 }
 
@@ -796,6 +801,7 @@ static cudaError_t seed_dispatch(Work& w, void* rn, void* rm) {
 template <int P>
 cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* launches) {
   typedef typename PT<P>::V V;
+  if (!w.st || !w.part || !w.rA || !w.rB || !w.q || !w.z || !w.list) return cudaErrorInvalidValue;
   // parity 0: r_n in rA, r_{n-1} in rB; parity 1: swapped.  K2 writes r_{n+1} over r_{n-1}.
   void* rn = parity ? w.rB : w.rA;
   void* rm = parity ? w.rA : w.rB;
@@ -806,6 +812,7 @@ cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* laun
   SpmvMode mode;
   mode.solver = 1;
   mode.zs = make_double2(0.0, 0.0);
+  mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);
   mode.t_out = nullptr;
   if ((e = spmv_dispatch<P>(w, rn, w.q, mode)) != cudaSuccess) return e;
   KW_MARK(1);
@@ -822,6 +829,7 @@ cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* laun
   a.conv_iter = w.conv_iter;
   a.final_res = w.final_res;
   a.coef = w.coef;
+  a.coef_pair = w.coef_pair;
   a.Y = w.Y;
   a.U = w.U;
   a.w = w.w;
@@ -846,8 +854,8 @@ cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* laun
   if (w.full) {
     static int nblk_xp = 0;
     if (nblk_xp == 0) nblk_xp = resident_blocks(k_update_xp<P, 8>, 256, w.num_sms);
-    k_update_xp<P, 8><<<nblk_xp, 256, 0, w.stream>>>((int)w.m, w.list, w.coef, (V*)w.X, (V*)w.P,
-                                                       (const V*)rm, w.st);
+    k_update_xp<P, 8><<<nblk_xp, 256, 0, w.stream>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
+                                                     (const V*)rm, w.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
   }
@@ -860,6 +868,8 @@ template <int P>
 cudaError_t launch_init(Work& w) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
+  if (!w.st || !w.part || !w.rA || !w.rB || !w.b || !w.pi1 || !w.w0 || (w.full && (!w.X || !w.P)))
+    return cudaErrorInvalidValue;
   const int nb = 4 * w.num_sms;
   k_init_vectors<P><<<nb, 256, 0, w.stream>>>((int)w.m, w.nproj, w.b, w.left, (V*)w.rA, (V*)w.rB,
                                               (R*)w.proj_rows);
@@ -879,22 +889,37 @@ cudaError_t launch_init(Work& w) {
   return cudaGetLastError();
 }
 
+// Full-mode outputs: FP32-pair vectors are first converted to FP64 in place
+// (the caller's x buffer holds kw_c128 in that form), then projected.
+template <int P>
+cudaError_t launch_finish_x(Work& w) {
+  if constexpr (P == PREC_DF) {
+    k_pairs_to_double<<<8 * w.num_sms, 256, 0, w.stream>>>((dfc*)w.X, (long long)w.K * w.m);
+    return cudaGetLastError();
+  } else {
+    return cudaSuccess;
+  }
+}
+
 template <int P>
 cudaError_t launch_project_x(Work& w, double2* out) {
-  typedef typename PT<P>::V V;
+  // after launch_finish_x the FP32-pair form holds FP64 values
+  typedef typename std::conditional<P == PREC_C32, float2, double2>::type XV;
+  constexpr int PX = P == PREC_C32 ? PREC_C32 : PREC_F64;
   const int np = w.nout;
   if (np <= 8)
-    k_project_x<P, 8><<<w.K, 256, 0, w.stream>>>((int)w.m, np, w.b, w.left, (const V*)w.X, out);
+    k_project_x<PX, 8><<<w.K, 256, 0, w.stream>>>((int)w.m, np, w.b, w.left, (const XV*)w.X, out);
   else
-    k_project_x<P, KW_MAX_PROJ><<<w.K, 256, 0, w.stream>>>((int)w.m, np, w.b, w.left, (const V*)w.X, out);
+    k_project_x<PX, KW_MAX_PROJ><<<w.K, 256, 0, w.stream>>>((int)w.m, np, w.b, w.left, (const XV*)w.X, out);
   return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, double2* t_dev) {
+cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, float4 zs_pair, double2* t_dev) {
   SpmvMode mode;
   mode.solver = 0;
   mode.zs = zs;
+  mode.zs_pair = zs_pair;
   mode.t_out = t_dev;
   return spmv_dispatch<P>(w, r, q, mode);
 }

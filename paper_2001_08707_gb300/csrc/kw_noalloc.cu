@@ -83,6 +83,7 @@ extern "C" kw_status kw_spmv_dot_noalloc(int64_t m, int64_t nnz, const int64_t* 
   kw::SpmvMode mode;
   mode.solver = 0;
   mode.zs = make_double2(zs.re, zs.im);
+  mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);   // unused in the FP64 form
   mode.t_out = result;
   kw::k_spmv_dot<kw::PREC_F64, double, 1><<<grid, 256, 0, stream>>>(
       (int)m, rowptr_dev, col_dev, val_dev, (const double2*)r_dev, (double2*)q_dev, st, part, mode);

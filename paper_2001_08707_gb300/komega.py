@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, "libkomega_gb300.so")
 
 KW_F64 = 0
 KW_C32V_F64S = 1
-PRECISIONS = {"f64": KW_F64, "c32v_f64s": KW_C32V_F64S, "c32": KW_C32V_F64S}
+KW_DF64 = 2
+PRECISIONS = {"f64": KW_F64, "c32v_f64s": KW_C32V_F64S, "c32": KW_C32V_F64S, "df64": KW_DF64}
 
 STATUS = {0: "KW_OK", 1: "KW_ERR_ARG", 2: "KW_ERR_CUDA", 3: "KW_ERR_OOM", 4: "KW_ERR_BREAKDOWN",
           5: "KW_ERR_NONFINITE", 6: "KW_ERR_CALLBACK", 7: "KW_ERR_TIMEOUT", 8: "KW_NOT_CONVERGED"}
@@ -149,7 +150,7 @@ class Solver:
         self._ctx = ctx
         self._keep = []
         self.m = None
-        self.vec_dtype = torch.complex128 if self.prec == KW_F64 else torch.complex64
+        self.vec_dtype = torch.complex64 if self.prec == KW_C32V_F64S else torch.complex128
 
     # ------------------------------------------------------------------ helpers
     def _err(self, st, what):
@@ -229,7 +230,7 @@ class Solver:
         nleft = 0 if ll is None else ll.shape[0]
         x = None
         if full:
-            x = np.zeros((K, m), dtype=np.complex128 if self.prec == KW_F64 else np.complex64)
+            x = np.zeros((K, m), dtype=np.complex64 if self.prec == KW_C32V_F64S else np.complex128)
         proj = np.zeros((K, nleft + 1), dtype=np.complex128)
         info = kw_solve_info()
         vp = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
@@ -286,7 +287,9 @@ class Solver:
         return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms)}
 
     def spmv_dot(self, zs: complex, r, q):
-        """q = zs r - H r and t = r^T q on the device (r, q: device complex tensors)."""
+        """q = zs r - H r and t = r^T q on the device.  r, q: device tensors in the
+        context's element layout (complex128 for f64, complex64 for c32, float32
+        [m, 4] pairs (re.hi, re.lo, im.hi, im.lo) for df64)."""
         t = kw_c128()
         st = self._lib.kw_spmv_dot(self._ctx, kw_c128(zs.real, zs.imag), C.c_void_p(r.data_ptr()),
                                    C.c_void_p(q.data_ptr()), C.byref(t))

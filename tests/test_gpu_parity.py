@@ -33,6 +33,18 @@ def _built():
     build.build()
 
 
+def to_pairs(z):
+    """complex128 tensor [m] -> float32 [m, 4] (re.hi, re.lo, im.hi, im.lo)."""
+    d = torch.view_as_real(z.to(torch.complex128))
+    hi = d.float()
+    lo = (d - hi.double()).float()
+    return torch.stack([hi[:, 0], lo[:, 0], hi[:, 1], lo[:, 1]], dim=1).contiguous()
+
+
+def from_pairs(p):
+    return torch.complex(p[:, 0].double() + p[:, 1].double(), p[:, 2].double() + p[:, 3].double())
+
+
 def _solver(H, prec="f64", **opts):
     s = kw.Solver(prec, **opts)
     s.set_csr(H.rowptr, H.col, H.val)
@@ -66,7 +78,7 @@ SPMV_CASES = {
 }
 
 
-@pytest.mark.parametrize("prec", ["f64", "c32"])
+@pytest.mark.parametrize("prec", ["f64", "c32", "df64"])
 @pytest.mark.parametrize("case", sorted(SPMV_CASES))
 def test_spmv_dot(case, prec):
     H = SPMV_CASES[case]()
@@ -74,12 +86,24 @@ def test_spmv_dot(case, prec):
     r = rng.standard_normal(H.m) + 1j * rng.standard_normal(H.m)
     zs = 0.37 - 1.2j
     s = _solver(H, prec)
+    Hs = H.to_scipy()
+    if prec == "df64":
+        # FP32-pair form: 48-bit significand, matrix values FP32 when exact, else FP32 pairs
+        rd = to_pairs(torch.as_tensor(r, device="cuda"))
+        qd = torch.empty_like(rd)
+        t = s.spmv_dot(zs, rd, qd)
+        q = from_pairs(qd).cpu().numpy()
+        r64 = from_pairs(rd).cpu().numpy()
+        q_ref = zs * r64 - Hs @ r64
+        scale = np.abs(zs) * np.abs(r64) + abs(Hs) @ np.abs(r64)
+        assert np.all(np.abs(q - q_ref) <= 1e-13 * scale)
+        assert abs(t - np.dot(r64, q_ref)) <= 1e-12 * np.sum(np.abs(r64 * q_ref))
+        return
     dt = torch.complex128 if prec == "f64" else torch.complex64
     rd = torch.as_tensor(r, device="cuda").to(dt)
     qd = torch.empty_like(rd)
     t = s.spmv_dot(zs, rd, qd)
     q = qd.cpu().numpy().astype(np.complex128)
-    Hs = H.to_scipy()
     if prec == "f64":
         q_ref = zs * r - Hs @ r
         t_ref = np.dot(r, q_ref)
@@ -152,9 +176,10 @@ def _compare_iterates(gpu, orc, full, rtol):
     assert np.all(num <= rtol * den), (num / den).max()
 
 
+@pytest.mark.parametrize("prec,rtol", [("f64", 1e-11), ("df64", 1e-10)])
 @pytest.mark.parametrize("full", [True, False])
 @pytest.mark.parametrize("n", [1, 2, 7, 20, 40])
-def test_fixed_iterations_f64(n, full):
+def test_fixed_iterations(n, full, prec, rtol):
     """Iterates after n steps (no freezing, seed switching on) match the oracle
     element by element.  On the L=12 cube (M=1728) the first 40 iterations are
     well conditioned: two oracle runs that differ only in the summation order of
@@ -162,14 +187,14 @@ def test_fixed_iterations_f64(n, full):
     p = w.anderson_small(L=12, K=24, delta=0.1)
     left = w.gaussian_unit(p.H.m, 5, w.STREAM_LEFT, count=3)
     orc = oc.shifted_cocg(p.H.to_scipy(), p.b, p.z, left=left, tol=0.0, maxiter=n, full=full)
-    s = _solver(p.H, "f64", tol=0.0, maxiter=n)
+    s = _solver(p.H, prec, tol=0.0, maxiter=n)
     g = s.solve(p.b, p.z, left=left, full=full)
     assert g.status == "KW_NOT_CONVERGED" and g.iters == n
     assert g.n_seed_switch == orc.n_seed_switch and g.seed == orc.seeds[-1]
-    _compare_iterates(g, orc, full, 1e-11)
+    _compare_iterates(g, orc, full, rtol)
 
 
-@pytest.mark.parametrize("prec,gap", [("f64", 1e-12), ("c32", 1e-5)])
+@pytest.mark.parametrize("prec,gap", [("f64", 1e-12), ("c32", 1e-5), ("df64", 1e-12)])
 @pytest.mark.parametrize("L,n", [(6, 80), (12, 150), (12, 400)])
 def test_collinear_residuals_long_run(L, n, prec, gap):
     """Past the point where Ritz values converge, intermediate iterates amplify
@@ -214,12 +239,14 @@ def test_residual_history_and_status_f64():
     np.testing.assert_array_equal(h[-1], fr)
 
 
-def test_anderson_L10_K64_full_converged_f64():
-    """The M=1000, K=64 full-x workload (tol 1e-10) against the oracle and the dense solve."""
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_anderson_L10_K64_full_converged(prec):
+    """The M=1000, K=64 full-x workload (tol 1e-10) against the oracle and the dense solve
+    (its random on-site energies are not exact in FP32: the FP32-pair form reads value pairs)."""
     p = w.anderson_small()
     Hs = p.H.to_scipy()
     orc = oc.shifted_cocg(Hs, p.b, p.z, tol=p.tol, full=True)
-    s = _solver(p.H, "f64", tol=p.tol)
+    s = _solver(p.H, prec, tol=p.tol)
     g = s.solve(p.b, p.z, full=True)
     assert g.status == "KW_OK" and g.n_converged == p.z.size
     xg = g.x.cpu().numpy()
@@ -238,12 +265,13 @@ def test_anderson_L10_K64_full_converged_f64():
     assert abs(g.iters - orc.iters) <= max(3, orc.iters // 20)
 
 
+@pytest.mark.parametrize("prec", ["f64", "df64"])
 @pytest.mark.parametrize("N", [12, 14])
-def test_heisenberg_projected_f64(N):
+def test_heisenberg_projected(N, prec):
     p = w.heisenberg_projected(N=N, K=48, delta=0.05, tol=1e-10)
     Hs = p.H.to_scipy()
     orc = oc.shifted_cocg(Hs, p.b, p.z, left=p.left, tol=p.tol, full=False)
-    s = _solver(p.H, "f64", tol=p.tol)
+    s = _solver(p.H, prec, tol=p.tol)
     g = s.solve(p.b, p.z, left=p.left, full=False)
     assert g.status == "KW_OK"
     dist = np.abs(p.z.imag)
@@ -270,12 +298,14 @@ def test_heisenberg_projected_c32_spectrum_error():
     assert np.all(errp <= 1e-5), errp
 
 
-def test_solve_host_equals_device_path():
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_solve_host_equals_device_path(prec):
     p = w.anderson_small(L=6, K=16, delta=0.1, tol=1e-9)
     left = w.gaussian_unit(p.H.m, 8, w.STREAM_LEFT, count=2)
-    s = _solver(p.H, "f64", tol=p.tol)
+    s = _solver(p.H, prec, tol=p.tol)
     g = s.solve(p.b, p.z, left=left, full=True)
-    s2 = kw.Solver("f64", tol=p.tol)
+    s2 = kw.Solver(prec, tol=p.tol)
+    s2.set_spmv_config(*s.spmv_config())
     h = s2.solve_host(p.H.rowptr, p.H.col, p.H.val, p.b, p.z, left=left, full=True)
     assert g.iters == h.iters
     np.testing.assert_array_equal(g.proj, h.proj)
@@ -296,7 +326,7 @@ def test_edge_zero_matrix_one_iteration():
     H = w.CSR(m, np.zeros(m + 1, np.int64), np.zeros(0, np.int32), np.zeros(0))
     b = w.gaussian_unit(m, 2)
     z = np.array([1 + 1j, -2 + 0.5j, 0.5j])
-    for prec, rt in (("f64", 1e-15), ("c32", 1e-6)):
+    for prec, rt in (("f64", 1e-15), ("c32", 1e-6), ("df64", 1e-14)):
         s = _solver(H, prec, tol=1e-12)
         g = s.solve(b, z, full=True)
         assert g.iters == 1 and g.status == "KW_OK"
@@ -322,9 +352,12 @@ def test_ragged_sizes_full_mode_c32_vs_f64():
     orc = oc.shifted_cocg(H.to_scipy(), b, z, tol=1e-9, full=True)
     g64 = _solver(H, "f64", tol=1e-9).solve(b, z, full=True)
     g32 = _solver(H, "c32", tol=1e-9).solve(b, z, full=True)
+    gdf = _solver(H, "df64", tol=1e-9).solve(b, z, full=True)
     x64 = g64.x.cpu().numpy()
     x32 = g32.x.cpu().numpy().astype(np.complex128)
     d = np.linalg.norm(x64 - orc.x, axis=1) / np.linalg.norm(orc.x, axis=1)
     assert d.max() <= 1e-8
+    ddf = np.linalg.norm(gdf.x.cpu().numpy() - orc.x, axis=1) / np.linalg.norm(orc.x, axis=1)
+    assert ddf.max() <= 1e-8
     d32 = np.linalg.norm(x32 - orc.x, axis=1) / np.linalg.norm(orc.x, axis=1)
     assert d32.max() <= 1e-4
