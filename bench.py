@@ -6,10 +6,12 @@ w_k on [-12, 12), with 4 left vectors (b and 3 seeded Gaussians) to
 tolerance 1e-10.  Inputs are resident in HBM when the timed region starts
 (the CSR alone is larger than L2, so no L2 flush is needed).
 
-Headline: the FP64 form, the one that reaches the 1e-10 tolerance here.  The
-complex-FP32-vector form (FP64 scalars) is reported beside it, run on the same
-workload with an iteration cap, with its spectrum error against the headline;
-both are credited the headline run's work sum_n K_active(n) * M.
+Headline: the FP32-pair form (KW_DF64): vectors as (hi, lo) FP32 pairs with
+error-free FP32 arithmetic, FP64 scalars; it reaches the 1e-10 tolerance.  The
+plain FP64 form and the complex-FP32-vector form (FP64 scalars; run with an
+iteration cap, it stalls at this delta) are reported beside it with their
+spectrum errors against the headline.  Every form is credited the headline
+run's work sum_n K_active(n) * M.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own replica (the solve does not
@@ -41,11 +43,12 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2001_08707_gb300", "csrc", "kw_kernels.cu
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
 
 
-HEADLINE = "f64"
-HEADLINE_DTYPE = "f64"
+HEADLINE = "df64"
+HEADLINE_DTYPE = "df64 (FP32 pairs, 48-bit significand; FP64 scalars)"
 PREC_NAMES = {"f64": "complex FP64 vectors, FP64 scalars",
-              "c32": "complex FP32 vectors, FP64 scalars"}
-PREC_BYTES = {"f64": (16, 8), "c32": (8, 4)}   # complex vector element, real element
+              "c32": "complex FP32 vectors, FP64 scalars",
+              "df64": "complex FP32-pair vectors (error-free FP32 arithmetic), FP64 scalars"}
+PREC_BYTES = {"f64": (16, 8), "c32": (8, 4), "df64": (16, 8)}   # complex vector element, real element
 FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (a register-only FMA loop measured 1.20)
 
 
@@ -278,7 +281,9 @@ def run_ours(args):
     if args.profile_iters:
         # profiling mode: the headline kernels on the same workload, one solve capped at N iterations
         prec = args.profile_prec or HEADLINE
-        s = solver(prec, args.profile_iters)
+        s = kw.Solver(prec, tol=p.tol, maxiter=args.profile_iters)
+        s.set_spmv_config(args.profile_lanes, 0)
+        s.set_csr(p.H.rowptr, p.H.col, p.H.val)
         r = s.solve(bd, p.z, left=ld)
         torch.cuda.synchronize()
         print(json.dumps({"profile": prec, "iters": r.iters, "status": r.status,
@@ -321,49 +326,64 @@ def run_ours(args):
     t_max = reduce_max(t_ms, ws, device)
     value = ws * work / (t_max / 1e3)
 
-    # FP32-vector comparison leg: same workload, capped at 1.5x the headline's iterations.
-    cap = int(1.5 * h_res.iters) + 16
-    c_times, c_stats, c_res, c_cfg = device_leg("c32", 1, 1, cap)
-    c_ms = reduce_max(statistics.mean(c_times), ws, device)
-    A_h = -np.imag(h_res.proj[:, 0]) / np.pi
-    A_c = -np.imag(c_res.proj[:, 0]) / np.pi
-    spec_err = float(np.abs(A_c - A_h).max() / np.abs(A_h).max())
-    proj_err = float((np.abs(c_res.proj - h_res.proj).max(axis=0) / np.abs(h_res.proj).max(axis=0)).max())
-
     def kstats(stats):
         ti = sum(s["timed_iters"] for s in stats)
         return ti, [sum(s["kernel_ms"][i] for s in stats) / max(ti, 1) for i in range(4)]
 
-    ti_h, k_h = kstats(h_stats)
-    ti_c, k_c = kstats(c_stats)
-    peak, peak_kind = load_peaks()
-    fp64_peak = FP64_PEAK_TFLOPS
-    vb_h, valb_h = PREC_BYTES[HEADLINE][0], (4 if h_cfg[1] else PREC_BYTES[HEADLINE][1])
-    b_spmv_h = spmv_bytes(m, nnz, vb_h, valb_h)
-    b_seed_h = seed_bytes(m, vb_h, PREC_BYTES[HEADLINE][1], nproj)
-    b_spmv_c = spmv_bytes(m, nnz, 8, 4)
-    b_seed_c = seed_bytes(m, 8, 4, nproj)
-    launches = sum(s["launches"] for s in h_stats)
+    def kern(prec, cfg, stats, iters, t):
+        ti, k = kstats(stats)
+        vb, rb = PREC_BYTES[prec]
+        valb = 4 if (prec == "c32" or cfg[1]) else 8
+        bs, bseed = spmv_bytes(m, nnz, vb, valb), seed_bytes(m, vb, rb, nproj)
+        return {"spmv_us": 1e3 * k[0], "spmv_gbs": bs / (k[0] * 1e-3) / 1e9, "spmv_bytes": bs,
+                "seed_update_us": 1e3 * k[1], "seed_update_gbs": bseed / (k[1] * 1e-3) / 1e9,
+                "shift_us": 1e3 * k[2], "iteration_us": t * 1e3 / max(iters, 1), "sampled_iterations": ti,
+                "spmv_config": list(cfg)}
 
-    if HEADLINE == "f64":
-        # FP64 arithmetic of one SpMV launch: 2 FMA per non-zero (real value x complex r)
-        # plus the row epilogue q = z_s r - acc and the r^T q term (about 8 FMA per row).
-        flops = 2.0 * (2 * nnz + 8 * m)
-        achieved = flops / (k_h[0] * 1e-3) / 1e12
-        roofline = {"kernel": "k_spmv_dot (seed SpMV + r^T q), f64", "bound": "alu", "achieved": achieved,
-                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                    "peak_kind": "nominal FP64 1.25 TFLOP/s (a register-only FMA probe measured 1.20)",
-                    "traffic": recorded_traffic("k_spmv_dot<f64>:heisenberg_N24"),
-                    "algorithmic_flops": flops, "algorithmic_bytes": b_spmv_h,
-                    "hbm_gbs_at_this_time": b_spmv_h / (k_h[0] * 1e-3) / 1e9,
-                    "avg_launch_us": 1e3 * k_h[0], "sampled_launches": ti_h}
-    else:
-        achieved = b_spmv_h / (k_h[0] * 1e-3) / 1e9
-        roofline = {"kernel": f"k_spmv_dot (seed SpMV + r^T q), {HEADLINE}", "bound": "hbm", "achieved": achieved,
-                    "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                    "traffic": recorded_traffic(f"k_spmv_dot<{HEADLINE}>:heisenberg_N24"),
-                    "algorithmic_bytes": b_spmv_h, "avg_launch_us": 1e3 * k_h[0], "sampled_launches": ti_h}
+    kernels = {HEADLINE: kern(HEADLINE, h_cfg, h_stats, h_res.iters, t_max)}
+    A_h = -np.imag(h_res.proj[:, 0]) / np.pi
+
+    def compare(res):
+        A = -np.imag(res.proj[:, 0]) / np.pi
+        return (float(np.abs(A - A_h).max() / np.abs(A_h).max()),
+                float((np.abs(res.proj - h_res.proj).max(axis=0) / np.abs(h_res.proj).max(axis=0)).max()))
+
+    legs = {}
+    # Plain FP64 form (the spec comparison), one warm-up and one timed solve.
+    f_times, f_stats, f_res, f_cfg = device_leg("f64", 1, 1, 200000)
+    f_ms = reduce_max(statistics.mean(f_times), ws, device)
+    kernels["f64"] = kern("f64", f_cfg, f_stats, f_res.iters, f_ms)
+    e_spec, e_proj = compare(f_res)
+    legs["f64"] = {"value": ws * work / (f_ms / 1e3), "ms_per_step": f_ms, "iters": f_res.iters,
+                   "status": f_res.status, "spectrum_rel_err_vs_headline": e_spec,
+                   "projection_rel_err_vs_headline": e_proj}
+    # FP32-vector form, capped at 1.5x the headline's iterations (it stalls at this delta).
+    cap = int(1.5 * h_res.iters) + 16
+    c_times, c_stats, c_res, c_cfg = device_leg("c32", 1, 1, cap)
+    c_ms = reduce_max(statistics.mean(c_times), ws, device)
+    kernels["c32"] = kern("c32", c_cfg, c_stats, c_res.iters, c_ms)
+    e_spec, e_proj = compare(c_res)
+    legs["c32"] = {"value": ws * work / (c_ms / 1e3), "ms_per_step": c_ms, "iters": c_res.iters,
+                   "iter_cap": cap, "status": c_res.status, "spectrum_rel_err_vs_headline": e_spec,
+                   "projection_rel_err_vs_headline": e_proj}
+
+    peak, peak_kind = load_peaks()
+    kh = kernels[HEADLINE]
+    launches = sum(s["launches"] for s in h_stats)
+    roofline = {"kernel": f"k_spmv_dot (seed SpMV + r^T q), {HEADLINE}", "bound": "hbm",
+                "achieved": kh["spmv_gbs"], "peak": peak, "unit": "GB/s", "frac": kh["spmv_gbs"] / peak,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "traffic": recorded_traffic(f"k_spmv_dot<{HEADLINE}>:heisenberg_N24"),
+                "algorithmic_bytes": kh["spmv_bytes"], "avg_launch_us": kh["spmv_us"],
+                "sampled_launches": kh["sampled_iterations"]}
+    kf = kernels["f64"]
+    fp64_flops = 2.0 * (2 * nnz + 8 * m)
+    legs["f64"]["roofline"] = {"kernel": "k_spmv_dot, f64", "bound": "alu",
+                               "achieved": fp64_flops / (kf["spmv_us"] * 1e-6) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                               "unit": "TFLOP/s",
+                               "frac": fp64_flops / (kf["spmv_us"] * 1e-6) / 1e12 / FP64_PEAK_TFLOPS,
+                               "peak_kind": "nominal FP64 1.25 TFLOP/s (a register-only FMA probe measured 1.20)",
+                               "traffic": recorded_traffic("k_spmv_dot<f64>:heisenberg_N24")}
 
     # e2e: the public host-buffer entry point, inputs copied from pinned host memory every step
     rp = torch.from_numpy(p.H.rowptr).pin_memory()
@@ -389,11 +409,6 @@ def run_ours(args):
 
     cpu = cpu_baseline(p) if (rank == 0 and ws == 1 and not args.no_cpu_baseline) else None
 
-    def kern(k, bs, bseed, iters, t):
-        return {"spmv_us": 1e3 * k[0], "spmv_gbs": bs / (k[0] * 1e-3) / 1e9, "seed_update_us": 1e3 * k[1],
-                "seed_update_gbs": bseed / (k[1] * 1e-3) / 1e9, "shift_us": 1e3 * k[2],
-                "iteration_us": t * 1e3 / max(iters, 1)}
-
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -405,12 +420,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (CSR %.0f MB)" % ((12 * nnz + 8 * m) / 1e6),
                        "iters": h_res.iters, "status": h_res.status, "spmv_config": list(h_cfg)},
             "roofline": roofline,
-            "kernels": {HEADLINE: kern(k_h, b_spmv_h, b_seed_h, h_res.iters, t_max),
-                        "c32": kern(k_c, b_spmv_c, b_seed_c, c_res.iters, c_ms)},
-            "c32_vectors": {"value": ws * work / (c_ms / 1e3), "ms_per_step": c_ms, "iters": c_res.iters,
-                            "iter_cap": cap, "status": c_res.status,
-                            "spectrum_rel_err_vs_headline": spec_err, "projection_rel_err_vs_headline": proj_err,
-                            "work_credit": "headline run's sum_n K_active(n) * M"},
+            "kernels": kernels,
+            "legs": legs,
             "e2e": {"value": ws * work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_s, "api": "kw_solve_host (pinned host buffers)"},
             "gpu_launches": launches,
@@ -435,8 +446,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="profiling mode: one solve capped at N iterations, no timing")
-    ap.add_argument("--profile-prec", choices=["f64", "c32"], default=None,
+    ap.add_argument("--profile-prec", choices=["f64", "c32", "df64"], default=None,
                     help="precision form of the profiling-mode solve (default: the headline form)")
+    ap.add_argument("--profile-lanes", type=int, default=1,
+                    help="SpMV lanes per row in profiling mode (the autotuner's timings are not "
+                         "meaningful under a profiler; 1 is its pick on this workload)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

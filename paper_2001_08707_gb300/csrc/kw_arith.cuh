@@ -41,13 +41,12 @@ __device__ __forceinline__ df two_prod(float a, float b) {
 
 // ------------------------------------------------------------- FP32-pair real arithmetic
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+// Pair addition in Dekker's form: the leading parts are added exactly, the
+// trailing parts in plain FP32.  Its error is about 2^-48 (|a| + |b|), the same
+// order as the rounding the operands already carry, at 11 operations.
 __device__ __forceinline__ df df_add(df a, df b) {
-  df s = two_sum(a.hi, b.hi);
-  const df t = two_sum(a.lo, b.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
-  return fast_two_sum(s.hi, s.lo);
+  const df s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ df df_mul(df a, df b) {
@@ -174,6 +173,11 @@ __device__ __forceinline__ float2 normalize(float2 a) { return a; }
 // ------------------------------------------------------------- dot-product accumulators
 // Accumulator type A: double (FP64 form), float (FP32 form, FP64 across chunks),
 // df (FP32-pair form).
+// Bring an accumulator to normalised form (pairs accumulate with deferred
+// normalisation, so hi and lo may overlap).
+__device__ __forceinline__ double anorm(double a) { return a; }
+__device__ __forceinline__ float anorm(float a) { return a; }
+__device__ __forceinline__ df anorm(df a) { return two_sum(a.hi, a.lo); }
 __device__ __forceinline__ void aadd(double& a, double v) { a += v; }
 __device__ __forceinline__ void aadd(float& a, float v) { a += v; }
 __device__ __forceinline__ void aadd(df& a, df v) { a = df_add(a, v); }
@@ -189,11 +193,24 @@ __device__ __forceinline__ void acc_rho_nrm(float& re, float& im, float& n, floa
   im += 2.f * r.x * r.y;
   n += r.x * r.x + r.y * r.y;
 }
+// acc += a*b for pairs, deferring normalisation: the rounded leading product is
+// added exactly (TwoSum), every error term goes to acc.lo.
+__device__ __forceinline__ void acc_prod(df& acc, df a, df b) {
+  const df p = two_prod(a.hi, b.hi);
+  const df s = two_sum(acc.hi, p.hi);
+  float e = __fmaf_rn(a.hi, b.lo, p.lo);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
 __device__ __forceinline__ void acc_rho_nrm(df& re, df& im, df& n, dfc r) {
-  re = df_add(re, df_fms(r.re, r.re, r.im, r.im));
-  const df xy = df_mul(r.re, r.im);
-  im = df_add(im, {2.f * xy.hi, 2.f * xy.lo});
-  n = df_add(n, df_fma2(r.re, r.re, r.im, r.im));
+  const df mim = df_neg(r.im);
+  acc_prod(re, r.re, r.re);
+  acc_prod(re, mim, r.im);
+  const df x2 = {2.f * r.re.hi, 2.f * r.re.lo};
+  acc_prod(im, x2, r.im);
+  acc_prod(n, r.re, r.re);
+  acc_prod(n, r.im, r.im);
 }
 // (re, im) += a * r  (real a)
 __device__ __forceinline__ void acc_proj(double& re, double& im, double a, double2 r) {
@@ -205,8 +222,8 @@ __device__ __forceinline__ void acc_proj(float& re, float& im, float a, float2 r
   im = fmaf(a, r.y, im);
 }
 __device__ __forceinline__ void acc_proj(df& re, df& im, df a, dfc r) {
-  re = df_add(re, df_mul(a, r.re));
-  im = df_add(im, df_mul(a, r.im));
+  acc_prod(re, a, r.re);
+  acc_prod(im, a, r.im);
 }
 // (re, im) += p
 __device__ __forceinline__ void acc_cplx(double& re, double& im, double2 p) {
@@ -224,7 +241,7 @@ __device__ __forceinline__ void acc_cplx(df& re, df& im, dfc p) {
 
 __device__ __forceinline__ double ato_double(double a) { return a; }
 __device__ __forceinline__ double ato_double(float a) { return (double)a; }
-__device__ __forceinline__ double ato_double(df a) { return df_to_double(a); }
+__device__ __forceinline__ double ato_double(df a) { return df_to_double(a); }   // hi + lo, exact in FP64
 
 template <class A> __device__ __forceinline__ A azero();
 template <> __device__ __forceinline__ double azero<double>() { return 0.0; }

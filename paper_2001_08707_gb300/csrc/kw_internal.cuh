@@ -20,6 +20,8 @@ struct State {
   double2 c;         // alpha_n beta_{n-1} / alpha_{n-1}
   double2 beta;      // beta_n = rho_{n+1} / rho_n
   double2 t;         // r_n^T A r_n
+  double2 inv_rho;   // 1 / rho_n
+  double2 inv_rho_alpha;  // 1 / (rho_n alpha_n)
   double nu;         // ||r_{n+1}||_2^2
   double thresh;     // tol * ||b||
   double norm_b;

@@ -67,7 +67,14 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
     return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
   }
 }
-__device__ __forceinline__ double2 crecip(double2 b) { return cdiv(make_double2(1.0, 0.0), b); }
+// 1/b = conj(b) / |b|^2, evaluated on b scaled by a power of two (exact) so that
+// |b|^2 neither overflows nor underflows; one division.  b must be nonzero.
+__device__ __forceinline__ double2 crecip(double2 b) {
+  const int e = ilogb(fmax(fabs(b.x), fabs(b.y)));
+  const double bx = scalbn(b.x, -e), by = scalbn(b.y, -e);
+  const double r = 1.0 / (bx * bx + by * by);
+  return make_double2(scalbn(bx * r, -e), scalbn(-by * r, -e));
+}
 __device__ __forceinline__ bool cfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 // FP32-pair image of a complex FP64 scalar (x = re.hi, y = re.lo, z = im.hi, w = im.lo).
 __device__ __forceinline__ float4 pair_of(double2 a) {
@@ -86,7 +93,7 @@ __device__ __forceinline__ void block_sum(const T (&v)[N], int n, double* out) {
 #pragma unroll
   for (int i = 0; i < N; ++i) {
     if (i < n) {
-      const T s = warp_sum(v[i]);
+      const T s = warp_sum(anorm(v[i]));
       if (lane == 0) sh[warp][i] = ato_double(s);
     }
   }
@@ -175,13 +182,16 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       const int beg = (int)rowptr[row], end = (int)rowptr[row + 1];
       if (G == 1) {
         int j = beg;
-        for (; j + 1 < end; j += 2) {        // two independent gathers in flight
-          const RV v0 = val[j], v1 = val[j + 1];
-          const V x0 = r[col[j]], x1 = r[col[j + 1]];
+        for (; j + 3 < end; j += 4) {        // four independent gathers in flight
+          const int c0 = col[j], c1 = col[j + 1], c2 = col[j + 2], c3 = col[j + 3];
+          const RV v0 = val[j], v1 = val[j + 1], v2 = val[j + 2], v3 = val[j + 3];
+          const V x0 = r[c0], x1 = r[c1], x2 = r[c2], x3 = r[c3];
           mac(acc, v0, x0);
           mac(acc, v1, x1);
+          mac(acc, v2, x2);
+          mac(acc, v3, x3);
         }
-        if (j < end) mac(acc, val[j], r[col[j]]);
+        for (; j < end; ++j) mac(acc, val[j], r[col[j]]);
       } else {
         for (int j = beg + sub; j < end; j += G) mac(acc, val[j], r[col[j]]);
       }
@@ -200,14 +210,14 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
     if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
-      t_re += ato_double(warp_sum(c_re));
-      t_im += ato_double(warp_sum(c_im));
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
       c_re = c_im = azero<A>();
       in_chunk = 0;
     }
   }
-  t_re += ato_double(warp_sum(c_re));
-  t_im += ato_double(warp_sum(c_im));
+  t_re += ato_double(warp_sum(anorm(c_re)));
+  t_im += ato_double(warp_sum(anorm(c_im)));
   __shared__ double red[2];
   {
     double v2[2] = {lane == 0 ? t_re : 0.0, lane == 0 ? t_im : 0.0};
@@ -233,7 +243,8 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       set_fail(st, KW_ERR_BREAKDOWN);
       return;
     }
-    const double2 alpha = cdiv(rho, denom);
+    const double2 inv_denom = crecip(denom), inv_rho = crecip(rho);
+    const double2 alpha = cmul(rho, inv_denom);
     const double2 c = cmul(alpha, boa);
     if (!cfinite(alpha) || !cfinite(c)) {
       set_fail(st, KW_ERR_NONFINITE);
@@ -241,6 +252,8 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
     }
     st->alpha = alpha;
     st->c = c;
+    st->inv_rho = inv_rho;                                    // beta_n = rho_{n+1} / rho_n in K2
+    st->inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));  // 1/(rho_n alpha_n): beta_n/alpha_n in K3
     st->p_alpha = pair_of(alpha);
     st->p_c = pair_of(c);
     st->p_opc = pair_of(make_double2(1.0 + c.x, c.y));
@@ -251,7 +264,7 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
 // ================================================================ K2: three-term update + dots
 // Values per block: [rho.re, rho.im, nu, w_0.re, w_0.im, ..., w_{np-1}.re, w_{np-1}.im]
 template <int P, int NP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5) ? 3 : 1)
 k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
               typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int np,
               State* st, double* __restrict__ part, double2* __restrict__ w_out) {
@@ -273,48 +286,40 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
   for (int i = 0; i < N; ++i) chunk[i] = tot[i] = azero<A>();
   int in_chunk = 0;
   const int stride = gridDim.x * blockDim.x;
-  // Two elements per trip, all loads issued before any store.
-  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += 2 * stride) {
-    const int i1 = i0 + stride;
-    const bool has1 = i1 < m;
-    V rn0 = rn_buf[i0], rm0 = rm_buf[i0];
-    const V q0 = q[i0];
-    V rn1 = vzero<V>(), rm1 = vzero<V>(), q1 = vzero<V>();
-    if (has1) {
-      rn1 = rn_buf[i1];
-      rm1 = rm_buf[i1];
-      q1 = q[i1];
-    }
-    R a0[NP > 0 ? NP : 1], a1[NP > 0 ? NP : 1];
+  // ILP elements per trip, all loads issued before any store: two for the FP64
+  // and FP32 forms; one for FP32 pairs, whose arithmetic already fills the
+  // pipes and whose registers would otherwise limit occupancy.
+  constexpr int ILP = (P == PREC_DF) ? 1 : 2;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += ILP * stride) {
+    V rn[ILP], rm[ILP], qv[ILP];
+    R a[ILP][NP > 0 ? NP : 1];
+    bool has[ILP];
 #pragma unroll
-    for (int l = 0; l < NP; ++l) {
-      a0[l] = (l < np) ? proj[(size_t)l * m + i0] : rfrom_double<R>(0.0);
-      a1[l] = (l < np && has1) ? proj[(size_t)l * m + i1] : rfrom_double<R>(0.0);
-    }
-    if (pend) {               // lazy seed switch: bring r_n, r_{n-1} to the new seed
-      rn0 = cmul(s1, rn0);
-      rm0 = cmul(s0, rm0);
-      rn_buf[i0] = rn0;
-      if (has1) {
-        rn1 = cmul(s1, rn1);
-        rm1 = cmul(s0, rm1);
-        rn_buf[i1] = rn1;
-      }
-    }
-    const V r10 = csub(csub(cmul(opc, rn0), cmul(av, q0)), cmul(cv, rm0));
-    const V r11 = csub(csub(cmul(opc, rn1), cmul(av, q1)), cmul(cv, rm1));   // zero when !has1
-    rm_buf[i0] = r10;
-    if (has1) rm_buf[i1] = r11;
-    acc_rho_nrm(chunk[0], chunk[1], chunk[2], r10);
-    acc_rho_nrm(chunk[0], chunk[1], chunk[2], r11);
+    for (int u = 0; u < ILP; ++u) {
+      const int i = i0 + u * stride;
+      has[u] = i < m;
+      rn[u] = has[u] ? rn_buf[i] : vzero<V>();
+      rm[u] = has[u] ? rm_buf[i] : vzero<V>();
+      qv[u] = has[u] ? q[i] : vzero<V>();
 #pragma unroll
-    for (int l = 0; l < NP; ++l) {
-      if (l < np) {
-        acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a0[l], r10);
-        acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a1[l], r11);
-      }
+      for (int l = 0; l < NP; ++l) a[u][l] = (l < np && has[u]) ? proj[(size_t)l * m + i] : rfrom_double<R>(0.0);
     }
-    if (CHUNKED && (in_chunk += 2) >= PT<P>::CHUNK) {
+#pragma unroll
+    for (int u = 0; u < ILP; ++u) {
+      const int i = i0 + u * stride;
+      if (pend) {             // lazy seed switch: bring r_n, r_{n-1} to the new seed
+        rn[u] = cmul(s1, rn[u]);
+        rm[u] = cmul(s0, rm[u]);
+        if (has[u]) rn_buf[i] = rn[u];
+      }
+      const V r1 = csub(csub(cmul(opc, rn[u]), cmul(av, qv[u])), cmul(cv, rm[u]));   // zero when !has
+      if (has[u]) rm_buf[i] = r1;
+      acc_rho_nrm(chunk[0], chunk[1], chunk[2], r1);
+#pragma unroll
+      for (int l = 0; l < NP; ++l)
+        if (l < np) acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a[u][l], r1);
+    }
+    if (CHUNKED && (in_chunk += ILP) >= PT<P>::CHUNK) {
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         aadd(tot[k], chunk[k]);
@@ -341,7 +346,7 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
     st->cnt_seed = 0;
     st->vec_scale_pending = 0;
     const double2 rho1 = make_double2(all[0], all[1]);
-    const double2 beta = cdiv(rho1, st->rho);          // beta_n = rho_{n+1} / rho_n
+    const double2 beta = cmul(rho1, st->inv_rho);      // beta_n = rho_{n+1} / rho_n
     st->rho1 = rho1;
     st->beta = beta;
     st->nu = all[2];
@@ -413,6 +418,7 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
       const double2 ratio = cmul(p1, ipn);            // pi_n / pi_{n+1}
       const double2 ak = cmul(ratio, alpha);          // Eq. 21
       const double2 bk = cmul(cmul(ratio, ratio), beta);  // Eq. 22
+      if (sub == 0) a.coef[3 * k + 2] = ipn;       // read by the seed switch and by K4
       if (a.full) {
         if (sub == 0) {
           a.coef[3 * k + 0] = ak;
@@ -500,9 +506,9 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   const double2 rho1_in = st->rho1;
   const long long upd = st->updates, maxiter = st->maxiter;
   const int nsw = st->n_seed_switch;
-  double2 pj1 = make_double2(1.0, 0.0), pj0 = pj1, zj = pj1;
+  double2 ipj1 = make_double2(1.0, 0.0), pj0 = ipj1, zj = ipj1;
   if (do_switch) {
-    pj1 = __ldcg(a.pi1 + gk);
+    ipj1 = __ldcg(a.coef + 3 * gk + 2);   // 1/pi^j_{n+1}, computed by the shift's owner lane
     pj0 = __ldcg(a.pi0 + gk);
     zj = a.z[gk];
   }
@@ -517,9 +523,9 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
     return;
   }
   double2 rho1 = rho1_in;
-  double2 boa = cdiv(beta, alpha);                      // beta_n / alpha_n
+  double2 boa = cmul(rho1_in, st->inv_rho_alpha);       // beta_n / alpha_n
   if (do_switch) {                                      // Sec. 2.2.4
-    const double2 ii1 = crecip(pj1), ii0 = crecip(pj0);
+    const double2 ii1 = ipj1, ii0 = crecip(pj0);
     st->scale_rn = ii1;                  // r_{n+1} <- r_{n+1} / pi^j_{n+1}
     st->scale_rnm1 = ii0;                // r_n     <- r_n / pi^j_n
     st->p_s1 = pair_of(ii1);
