@@ -180,9 +180,12 @@ typedef struct {
 kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
 
 /* Configuration of the sparse product kernel.  lanes = threads per matrix
- * row (1, 2, 4, 8 or 16; 0 = choose by timing every candidate on the current
- * operator at the next solve, the default; operators with fewer than 2^20
- * non-zeros are not timed and use 1).  val_f32 (KW_F64 mode only): 1 =
+ * row of the CSR kernel (1, 2, 4, 8 or 16), or 32 = the SELL-32 layout (an
+ * internal sliced-ELLPACK copy: rows sorted by length within windows of 1024
+ * rows, 32 rows per slice, column-major inside a slice, one thread per row);
+ * 0 = choose by timing every candidate on the current operator at the next
+ * solve, the default (operators with fewer than 2^20 non-zeros are not timed
+ * and use 1).  val_f32 (KW_F64 mode only): 1 =
  * read the matrix values from an FP32 copy, allowed only when every value is
  * exactly representable in FP32 (checked by kw_set_csr; otherwise FP64 is
  * used); 0 = FP64 values; -1 = choose by timing.  Errors: KW_ERR_ARG. */

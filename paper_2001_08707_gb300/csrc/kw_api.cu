@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "komega_gb300.h"
+#include "kw_arith.cuh"
 #include "kw_internal.cuh"
 
 namespace {
@@ -70,6 +71,9 @@ struct kw_ctx {
   int spmv_lanes = 0;         // tuned or forced lanes per row (0 = tune at first use)
   int spmv_val_f32 = 0;       // tuned or forced: FP32 value array in FP64 mode
   int force_lanes = 0, force_val = -1;
+  // SELL-32 copy of the operator (built when the tuner tries it or it is forced)
+  DBuf sell_perm, sell_len, sell_slen, sell_ptr, sell_col, sell_val;
+  bool sell_built = false;
   // host-solve copies
   DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
   // workspace
@@ -164,7 +168,8 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
 void kw_destroy(kw_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
-  DBuf* bufs[] = {&ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
+  DBuf* bufs[] = {&ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->sell_perm, &ctx->sell_len,
+                  &ctx->sell_slen, &ctx->sell_ptr, &ctx->sell_col, &ctx->sell_val, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot};
@@ -198,6 +203,7 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   ctx->val = val_dev;
   ctx->val32_exact = false;
   ctx->spmv_lanes = 0;   // re-tune for the new operator
+  ctx->sell_built = false;
   if (nnz > 0) {
     KW_CUDA(ctx->val32.ensure((size_t)nnz * sizeof(float)), "kw_set_csr: FP32 value copy");
     KW_CUDA(ctx->inexact.ensure(sizeof(unsigned long long)), "kw_set_csr: counter");
@@ -237,10 +243,66 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.val = w.val_f32 ? (const void*)ctx->val32.p
                     : (p == KW_DF64 ? (const void*)ctx->valpair.p : (const void*)ctx->val);
   w.spmv_lanes = lanes;
+  if (lanes == kw::KW_SPMV_SELL) {
+    if (p == KW_F64) w.val_f32 = 0;       // the SELL copy keeps FP64 values in the FP64 form
+    w.sell_perm = (const int*)ctx->sell_perm.p;
+    w.sell_len = (const int*)ctx->sell_len.p;
+    w.sell_ptr = (const int64_t*)ctx->sell_ptr.p;
+    w.sell_col = (const int*)ctx->sell_col.p;
+    w.sell_val = ctx->sell_val.p;
+  }
   w.stream = ctx->stream;
   w.num_sms = ctx->num_sms;
   w.part = (double*)ctx->part.p;
   w.st = (kw::State*)ctx->st.p;
+}
+
+// Build the SELL-32 copy of the operator: device sort of each 1024-row window
+// by row length, slice offsets by a host prefix sum, device fill.
+static kw_status build_sell(kw_ctx* ctx) {
+  if (ctx->sell_built) return KW_OK;
+  const kw_precision p = ctx->opt.prec;
+  const int m = (int)ctx->m;
+  const int nslice = (m + 31) / 32;
+  KW_CUDA(ctx->sell_perm.ensure((size_t)m * 4), "sell alloc");
+  KW_CUDA(ctx->sell_len.ensure((size_t)m * 4), "sell alloc");
+  KW_CUDA(ctx->sell_slen.ensure((size_t)nslice * 4), "sell alloc");
+  KW_CUDA(ctx->sell_ptr.ensure((size_t)(nslice + 1) * 8), "sell alloc");
+  KW_CUDA(kw::launch_sell_order(m, ctx->rowptr, (int*)ctx->sell_perm.p, (int*)ctx->sell_len.p,
+                                (int*)ctx->sell_slen.p, ctx->stream), "sell order");
+  std::vector<int> slen(nslice);
+  std::vector<int64_t> sptr(nslice + 1);
+  KW_CUDA(cudaMemcpyAsync(slen.data(), ctx->sell_slen.p, (size_t)nslice * 4, cudaMemcpyDeviceToHost, ctx->stream),
+          "sell read");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "sell sync");
+  sptr[0] = 0;
+  for (int s = 0; s < nslice; ++s) sptr[s + 1] = sptr[s] + 32 * (int64_t)slen[s];
+  KW_CUDA(cudaMemcpyAsync(ctx->sell_ptr.p, sptr.data(), (size_t)(nslice + 1) * 8, cudaMemcpyHostToDevice, ctx->stream),
+          "sell upload");
+  const int64_t padded = std::max<int64_t>(sptr[nslice], 1);
+  // value kind: FP64 form -> double; FP32 form -> float; pair form -> float if exact, else pairs
+  const int kind = p == KW_F64 ? 0 : (p == KW_C32V_F64S || ctx->val32_exact) ? 1 : 2;
+  const size_t vb = kind == 1 ? 4 : 8;
+  KW_CUDA(ctx->sell_col.ensure((size_t)padded * 4), "sell alloc");
+  KW_CUDA(ctx->sell_val.ensure((size_t)padded * vb), "sell alloc");
+  KW_CUDA(cudaMemsetAsync(ctx->sell_col.p, 0, (size_t)padded * 4, ctx->stream), "sell memset");
+  KW_CUDA(cudaMemsetAsync(ctx->sell_val.p, 0, (size_t)padded * vb, ctx->stream), "sell memset");
+  if (ctx->nnz > 0) {
+    const void* src = kind == 0 ? (const void*)ctx->val : kind == 1 ? ctx->val32.p : ctx->valpair.p;
+    cudaError_t e =
+        kind == 0 ? kw::launch_sell_fill<double>(m, (const int*)ctx->sell_perm.p, (const int*)ctx->sell_len.p,
+                                                 (const int64_t*)ctx->sell_ptr.p, ctx->rowptr, ctx->col, src,
+                                                 (int*)ctx->sell_col.p, ctx->sell_val.p, ctx->stream)
+        : kind == 1 ? kw::launch_sell_fill<float>(m, (const int*)ctx->sell_perm.p, (const int*)ctx->sell_len.p,
+                                                  (const int64_t*)ctx->sell_ptr.p, ctx->rowptr, ctx->col, src,
+                                                  (int*)ctx->sell_col.p, ctx->sell_val.p, ctx->stream)
+                    : kw::launch_sell_fill<kw::df>(m, (const int*)ctx->sell_perm.p, (const int*)ctx->sell_len.p,
+                                                   (const int64_t*)ctx->sell_ptr.p, ctx->rowptr, ctx->col, src,
+                                                   (int*)ctx->sell_col.p, ctx->sell_val.p, ctx->stream);
+    KW_CUDA(e, "sell fill");
+  }
+  ctx->sell_built = true;
+  return KW_OK;
 }
 
 static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 zs, double2* t) {
@@ -262,9 +324,13 @@ static const int64_t kTuneMinNnz = 1 << 20;
 static kw_status tune_spmv(kw_ctx* ctx) {
   if (ctx->spmv_lanes > 0) return KW_OK;
   const kw_precision p = ctx->opt.prec;
-  if (ctx->nnz < kTuneMinNnz) {
+  if (ctx->nnz < kTuneMinNnz || ctx->force_lanes == kw::KW_SPMV_SELL) {
     ctx->spmv_lanes = ctx->force_lanes > 0 ? ctx->force_lanes : 1;
     ctx->spmv_val_f32 = (p == KW_F64 && ctx->force_val == 1 && ctx->val32_exact) ? 1 : 0;
+    if (ctx->spmv_lanes == kw::KW_SPMV_SELL) {
+      if (p == KW_F64) ctx->spmv_val_f32 = 0;   // the SELL copy keeps FP64 values in the FP64 form
+      return build_sell(ctx);
+    }
     return KW_OK;
   }
   const size_t vs = vec_bytes(p);
@@ -275,7 +341,7 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   KW_CUDA(ctx->tdot.ensure(16), "tune alloc");
   KW_CUDA(cudaMemsetAsync(ctx->rA.p, 0, ctx->m * vs, ctx->stream), "tune memset");
   KW_CUDA(cudaMemsetAsync(ctx->st.p, 0, sizeof(kw::State), ctx->stream), "tune memset");
-  const int lane_opts[] = {1, 2, 4, 8, 16};
+  const int lane_opts[] = {1, 2, 4, 8, 16, kw::KW_SPMV_SELL};
   // value storage candidates: only the FP64 form has a choice (FP64 or exact FP32 values)
   int vals[2] = {0, 1}, nvals = 1;
   if (p == KW_F64 && ctx->val32_exact) nvals = 2;
@@ -293,6 +359,11 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   for (int vi = 0; vi < nvals; ++vi) {
     for (int l : lane_opts) {
       if (ctx->force_lanes > 0 && l != ctx->force_lanes) continue;
+      if (l == kw::KW_SPMV_SELL) {
+        if (vi > 0) continue;   // the SELL copy has one value type per form
+        kw_status bs = build_sell(ctx);
+        if (bs != KW_OK) return bs;
+      }
       kw::Work w;
       spmv_work(ctx, w, l, vals[vi]);
       const double2 zs = make_double2(0.5, 0.5);
@@ -314,7 +385,12 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   cudaEventDestroy(e1);
   KW_CUDA(cudaGetLastError(), "tune launches");
   ctx->spmv_lanes = best_l;
-  ctx->spmv_val_f32 = best_v;
+  ctx->spmv_val_f32 = best_l == kw::KW_SPMV_SELL ? (p == KW_F64 ? 0 : best_v) : best_v;
+  if (best_l != kw::KW_SPMV_SELL && ctx->sell_built) {   // not chosen: give the memory back
+    ctx->sell_col.release();
+    ctx->sell_val.release();
+    ctx->sell_built = false;
+  }
   return KW_OK;
 }
 
@@ -592,8 +668,10 @@ kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every) {
 }
 
 kw_status kw_set_spmv_config(kw_ctx* ctx, int lanes, int val_f32) {
-  if (!ctx || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16) || val_f32 < -1 ||
-      val_f32 > 1)
+  if (!ctx ||
+      !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
+        lanes == kw::KW_SPMV_SELL) ||
+      val_f32 < -1 || val_f32 > 1)
     return KW_ERR_ARG;
   ctx->force_lanes = lanes;
   ctx->force_val = val_f32;

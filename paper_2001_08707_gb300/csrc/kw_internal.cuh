@@ -66,7 +66,13 @@ struct Work {
   const int64_t* rowptr;
   const int32_t* col;
   const void* val;   // double* (F64) or float* (C32)
-  int spmv_lanes;    // lanes per row in K1 (1 = one thread per row)
+  int spmv_lanes;    // lanes per row in K1 (1 = one thread per row); KW_SPMV_SELL = SELL-32 layout
+  // SELL-32 copy of the operator (used when spmv_lanes == KW_SPMV_SELL)
+  const int* sell_perm;      // [m] sorted position -> row
+  const int* sell_len;       // [m] row length at each sorted position
+  const int64_t* sell_ptr;   // [nslice + 1] start of each slice
+  const int* sell_col;       // [padded nnz]
+  const void* sell_val;      // [padded nnz] in the SpMV value type
   int val_f32;       // matrix values stored as FP32 (always in C32 mode; in F64 mode when lossless)
   // seed vectors
   void* rA;          // two rotating residual buffers and q
@@ -109,6 +115,13 @@ cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, float4 
 cudaError_t launch_convert_f64_to_f32(const double* in, float* out, int64_t n, unsigned long long* inexact,
                                       cudaStream_t s);
 cudaError_t launch_convert_f64_to_pair(const double* in, void* out, int64_t n, cudaStream_t s);
+
+// spmv_lanes value that selects the SELL-32 layout.
+constexpr int KW_SPMV_SELL = 32;
+cudaError_t launch_sell_order(int m, const int64_t* rowptr, int* perm, int* rlen, int* slen, cudaStream_t s);
+template <class RV>
+cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,
+                             const int* col, const void* val, int* scol, void* sval, cudaStream_t s);
 
 // Upper bound on resident 256-thread blocks per SM (2048 threads per SM).
 constexpr int kMaxBlocksPerSM = 8;

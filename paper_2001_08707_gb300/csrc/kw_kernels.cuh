@@ -148,6 +148,56 @@ struct SpmvMode {
   double2* t_out;    // standalone: result
 };
 
+// End of K1 (both layouts): block sum of r^T q, then the last block computes
+// alpha_n and c_n (Eq. 17) or, standalone, returns t.
+template <class A>
+__device__ __forceinline__ void spmv_finish(A c_re, A c_im, double t_re, double t_im, int lane, State* st,
+                                            double* __restrict__ part, const SpmvMode& mode) {
+  t_re += ato_double(warp_sum(anorm(c_re)));
+  t_im += ato_double(warp_sum(anorm(c_im)));
+  __shared__ double red[2];
+  {
+    double v2[2] = {lane == 0 ? t_re : 0.0, lane == 0 ? t_im : 0.0};
+    block_sum<2, double>(v2, 2, red);
+  }
+  if (threadIdx.x < 2) part[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
+  if (!arrive_last(&st->cnt_spmv)) return;
+
+  __shared__ double tot[2];
+  reduce_partials<2>(part, gridDim.x, 2, 2, tot);
+  if (threadIdx.x == 0) {
+    st->cnt_spmv = 0;
+    const double2 t = make_double2(tot[0], tot[1]);
+    if (!mode.solver) {
+      *mode.t_out = t;
+      return;
+    }
+    st->t = t;
+    const double2 rho = st->rho, boa = st->boa;
+    // alpha_n = rho_n / (r_n^T A r_n - (beta_{n-1}/alpha_{n-1}) rho_n)   (Eq. 17)
+    const double2 denom = csub(t, cmul(boa, rho));
+    if ((rho.x == 0.0 && rho.y == 0.0) || (denom.x == 0.0 && denom.y == 0.0)) {
+      set_fail(st, KW_ERR_BREAKDOWN);
+      return;
+    }
+    const double2 inv_denom = crecip(denom), inv_rho = crecip(rho);
+    const double2 alpha = cmul(rho, inv_denom);
+    const double2 c = cmul(alpha, boa);
+    if (!cfinite(alpha) || !cfinite(c)) {
+      set_fail(st, KW_ERR_NONFINITE);
+      return;
+    }
+    st->alpha = alpha;
+    st->c = c;
+    st->inv_rho = inv_rho;                                    // beta_n = rho_{n+1} / rho_n in K2
+    st->inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));  // 1/(rho_n alpha_n): beta_n/alpha_n in K3
+    st->p_alpha = pair_of(alpha);
+    st->p_c = pair_of(c);
+    st->p_opc = pair_of(make_double2(1.0 + c.x, c.y));
+    st->n_list = 0;
+  }
+}
+
 template <int P, class RV, int G>
 __global__ void __launch_bounds__(256)
 k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
@@ -216,48 +266,140 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       in_chunk = 0;
     }
   }
-  t_re += ato_double(warp_sum(anorm(c_re)));
-  t_im += ato_double(warp_sum(anorm(c_im)));
-  __shared__ double red[2];
-  {
-    double v2[2] = {lane == 0 ? t_re : 0.0, lane == 0 ? t_im : 0.0};
-    block_sum<2, double>(v2, 2, red);
-  }
-  if (threadIdx.x < 2) part[blockIdx.x * 2 + threadIdx.x] = red[threadIdx.x];
-  if (!arrive_last(&st->cnt_spmv)) return;
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
 
-  __shared__ double tot[2];
-  reduce_partials<2>(part, gridDim.x, 2, 2, tot);
-  if (threadIdx.x == 0) {
-    st->cnt_spmv = 0;
-    const double2 t = make_double2(tot[0], tot[1]);
-    if (!mode.solver) {
-      *mode.t_out = t;
-      return;
+// K1 on the SELL-32 layout (sliced ELLPACK): rows sorted by length inside
+// 1024-row windows, 32 rows per slice, each slice's entries stored column-major
+// so that one warp reads 32 consecutive indices and values per step.  One warp
+// per slice, one lane per row; perm maps a sorted position to its row.
+template <int P, class RV>
+__global__ void __launch_bounds__(256)
+k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restrict__ rlen,
+            const int64_t* __restrict__ sptr, const int* __restrict__ scol, const RV* __restrict__ sval,
+            const typename PT<P>::V* __restrict__ r, typename PT<P>::V* __restrict__ q, State* st,
+            double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  V zsv, scv = vzero<V>();
+  bool scaled = false;
+  if (mode.solver) {
+    if (st->done) return;
+    zsv = vscalar<V>(st->zs, st->p_zs);
+    if (st->vec_scale_pending) {
+      scv = vscalar<V>(st->scale_rn, st->p_s1);
+      scaled = true;
     }
-    st->t = t;
-    const double2 rho = st->rho, boa = st->boa;
-    // alpha_n = rho_n / (r_n^T A r_n - (beta_{n-1}/alpha_{n-1}) rho_n)   (Eq. 17)
-    const double2 denom = csub(t, cmul(boa, rho));
-    if ((rho.x == 0.0 && rho.y == 0.0) || (denom.x == 0.0 && denom.y == 0.0)) {
-      set_fail(st, KW_ERR_BREAKDOWN);
-      return;
+  } else {
+    zsv = vscalar<V>(mode.zs, mode.zs_pair);
+  }
+  const int lane = threadIdx.x & 31;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  for (int s = warp_global; s < nslice; s += nwarps) {   // uniform across the warp
+    const int p = s * 32 + lane;
+    if (p < m) {
+      const int row = perm[p], len = rlen[p];
+      const int* __restrict__ cp = scol + sptr[s] + lane;
+      const RV* __restrict__ vp = sval + sptr[s] + lane;
+      V acc = vzero<V>();
+      int j = 0;
+      for (; j + 3 < len; j += 4) {
+        const int c0 = cp[32 * j], c1 = cp[32 * (j + 1)], c2 = cp[32 * (j + 2)], c3 = cp[32 * (j + 3)];
+        const RV v0 = vp[32 * j], v1 = vp[32 * (j + 1)], v2 = vp[32 * (j + 2)], v3 = vp[32 * (j + 3)];
+        const V x0 = r[c0], x1 = r[c1], x2 = r[c2], x3 = r[c3];
+        mac(acc, v0, x0);
+        mac(acc, v1, x1);
+        mac(acc, v2, x2);
+        mac(acc, v3, x3);
+      }
+      for (; j < len; ++j) mac(acc, vp[32 * j], r[cp[32 * j]]);
+      acc = normalize(acc);
+      V ri = r[row];
+      V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
+      if (scaled) {
+        qi = cmul(scv, qi);
+        ri = cmul(scv, ri);
+      }
+      q[row] = qi;
+      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
-    const double2 inv_denom = crecip(denom), inv_rho = crecip(rho);
-    const double2 alpha = cmul(rho, inv_denom);
-    const double2 c = cmul(alpha, boa);
-    if (!cfinite(alpha) || !cfinite(c)) {
-      set_fail(st, KW_ERR_NONFINITE);
-      return;
+    if (++in_chunk == PT<P>::CHUNK) {
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
     }
-    st->alpha = alpha;
-    st->c = c;
-    st->inv_rho = inv_rho;                                    // beta_n = rho_{n+1} / rho_n in K2
-    st->inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));  // 1/(rho_n alpha_n): beta_n/alpha_n in K3
-    st->p_alpha = pair_of(alpha);
-    st->p_c = pair_of(c);
-    st->p_opc = pair_of(make_double2(1.0 + c.x, c.y));
-    st->n_list = 0;
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
+// ---------------------------------------------------------------- SELL-32 construction
+// One block of 1024 threads per window of 1024 rows: bitonic sort of
+// (descending length, row) keys; writes the sorted order and lengths.
+static __global__ void __launch_bounds__(1024) k_sell_sort(int m, const int64_t* __restrict__ rowptr, int* perm,
+                                                         int* rlen) {
+  __shared__ unsigned int key[1024];
+  const int i = threadIdx.x, base = blockIdx.x * 1024, row = base + i;
+  const unsigned int LMAX = (1u << 21) - 1;
+  unsigned int kk = 0xffffffffu;
+  if (row < m) {
+    const long long len = rowptr[row + 1] - rowptr[row];
+    const unsigned int l = (unsigned int)(len < (long long)LMAX ? len : (long long)LMAX);
+    kk = ((LMAX - l) << 10) | (unsigned int)i;
+  }
+  key[i] = kk;
+  __syncthreads();
+  for (int size = 2; size <= 1024; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const int j = i ^ stride;
+      if (j > i) {
+        const unsigned int a = key[i], b = key[j];
+        const bool up = (i & size) == 0;
+        if ((a > b) == up) {
+          key[i] = b;
+          key[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (base + i < m) {
+    const int r0 = base + (int)(key[i] & 1023u);
+    perm[base + i] = r0;
+    rlen[base + i] = (int)(rowptr[r0 + 1] - rowptr[r0]);
+  }
+}
+
+// Length of each 32-row slice = its longest row.
+static __global__ void k_sell_slicelen(int m, int nslice, const int* __restrict__ rlen, int* slen) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslice; s += gridDim.x * blockDim.x) {
+    int mx = 0;
+    for (int p = s * 32; p < min(m, s * 32 + 32); ++p) mx = max(mx, rlen[p]);
+    slen[s] = mx;
+  }
+}
+
+// One warp per slice: copy every row's entries into the column-major slice.
+template <class RV>
+__global__ void k_sell_fill(int m, int nslice, const int* __restrict__ perm, const int* __restrict__ rlen,
+                            const int64_t* __restrict__ sptr, const int64_t* __restrict__ rowptr,
+                            const int* __restrict__ col, const RV* __restrict__ val, int* scol, RV* sval) {
+  const int lane = threadIdx.x & 31;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int s = warp_global; s < nslice; s += nwarps) {
+    const int p = s * 32 + lane;
+    if (p >= m) continue;
+    const int row = perm[p], len = rlen[p];
+    const int64_t src = rowptr[row], dst = sptr[s] + lane;
+    for (int j = 0; j < len; ++j) {
+      scol[dst + 32 * (int64_t)j] = col[src + j];
+      sval[dst + 32 * (int64_t)j] = val[src + j];
+    }
   }
 }
 
@@ -756,7 +898,24 @@ static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
 }
 
 template <int P, class RV>
+static cudaError_t sell_launch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_spmv_sell<P, RV>, 256, w.num_sms);
+  const int nslice = (int)((w.m + 31) / 32);
+  const int grid = std::max(1, std::min(nblk, (nslice + 7) / 8));
+  k_spmv_sell<P, RV><<<grid, 256, 0, w.stream>>>((int)w.m, nslice, w.sell_perm, w.sell_len, w.sell_ptr,
+                                                 w.sell_col, (const RV*)w.sell_val, (const V*)r, (V*)q, w.st,
+                                                 w.part, mode);
+  return cudaGetLastError();
+}
+
+template <int P, class RV>
 static cudaError_t spmv_dispatch_v(Work& w, const void* r, void* q, SpmvMode mode) {
+  if (w.spmv_lanes == KW_SPMV_SELL) {
+    if (!w.sell_perm || !w.sell_len || !w.sell_ptr || !w.sell_col || !w.sell_val) return cudaErrorInvalidValue;
+    return sell_launch<P, RV>(w, r, q, mode);
+  }
   switch (w.spmv_lanes) {
     case 1: return spmv_launch<P, RV, 1>(w, r, q, mode);
     case 2: return spmv_launch<P, RV, 2>(w, r, q, mode);

@@ -18,4 +18,31 @@ cudaError_t launch_convert_f64_to_pair(const double* in, void* out, int64_t n, c
   k_f64_to_pair<<<1024, 256, 0, s>>>(in, (df*)out, n);
   return cudaGetLastError();
 }
+// SELL-32 construction, step 1: sorted order, row lengths, slice lengths.
+cudaError_t launch_sell_order(int m, const int64_t* rowptr, int* perm, int* rlen, int* slen,
+                                     cudaStream_t s) {
+  const int nwin = (m + 1023) / 1024, nslice = (m + 31) / 32;
+  k_sell_sort<<<nwin, 1024, 0, s>>>(m, rowptr, perm, rlen);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sell_slicelen<<<(nslice + 255) / 256, 256, 0, s>>>(m, nslice, rlen, slen);
+  return cudaGetLastError();
+}
+
+// Step 2 (after the host has formed the slice offsets): copy the entries.
+template <class RV>
+cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,
+                             const int* col, const void* val, int* scol, void* sval, cudaStream_t s) {
+  const int nslice = (m + 31) / 32;
+  k_sell_fill<RV><<<(nslice + 7) / 8, 256, 0, s>>>(m, nslice, perm, rlen, sptr, rowptr, col, (const RV*)val, scol,
+                                                   (RV*)sval);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sell_fill<double>(int, const int*, const int*, const int64_t*, const int64_t*,
+                                               const int*, const void*, int*, void*, cudaStream_t);
+template cudaError_t launch_sell_fill<float>(int, const int*, const int*, const int64_t*, const int64_t*,
+                                              const int*, const void*, int*, void*, cudaStream_t);
+template cudaError_t launch_sell_fill<df>(int, const int*, const int*, const int64_t*, const int64_t*, const int*,
+                                           const void*, int*, void*, cudaStream_t);
 }  // namespace kw

@@ -120,7 +120,7 @@ def test_spmv_dot(case, prec):
 
 
 @pytest.mark.parametrize("val_f32", [0, 1])
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 def test_spmv_variants_f64(lanes, val_f32):
     """Every SpMV configuration the autotuner can pick gives the same product
     (Heisenberg values are exact in FP32, so the FP32 value copy is lossless)."""
@@ -130,13 +130,48 @@ def test_spmv_variants_f64(lanes, val_f32):
     s = kw.Solver("f64")
     s.set_spmv_config(lanes, val_f32)
     s.set_csr(H.rowptr, H.col, H.val)
-    assert s.spmv_config() == (lanes, val_f32)
+    assert s.spmv_config() == (lanes, 0 if lanes == 32 else val_f32)   # lanes 32: SELL-32 (FP64 values)
     rd = torch.as_tensor(r, device="cuda")
     qd = torch.empty_like(rd)
     t = s.spmv_dot(0.3 + 0.2j, rd, qd)
     q_ref = (0.3 + 0.2j) * r - H.to_scipy() @ r
     np.testing.assert_allclose(qd.cpu().numpy(), q_ref, rtol=0, atol=1e-13 * np.abs(q_ref).max())
     assert abs(t - np.dot(r, q_ref)) <= 1e-12 * np.sum(np.abs(r * q_ref))
+
+
+@pytest.mark.parametrize("case", ["ragged_empty_rows_4097", "dense_row_33", "one_by_one", "anderson_L10"])
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_sell_layout_matches_csr(case, prec):
+    """The SELL-32 copy (sorted windows, ragged last slice, empty rows, a row
+    longer than a slice is wide) gives the same product as the CSR kernel."""
+    H = SPMV_CASES[case]()
+    rng = np.random.default_rng(17)
+    r = torch.as_tensor(rng.standard_normal(H.m) + 1j * rng.standard_normal(H.m), device="cuda")
+    out = []
+    for lanes in (1, 32):
+        s = kw.Solver(prec)
+        s.set_spmv_config(lanes, -1)
+        s.set_csr(H.rowptr, H.col, H.val)
+        rd = to_pairs(r) if prec == "df64" else r
+        qd = torch.empty_like(rd)
+        t = s.spmv_dot(0.2 - 0.7j, rd, qd)
+        out.append((t, (from_pairs(qd) if prec == "df64" else qd).cpu().numpy()))
+    (t1, q1), (t2, q2) = out
+    np.testing.assert_allclose(q2, q1, rtol=0, atol=1e-13 * np.abs(q1).max())
+    assert abs(t2 - t1) <= 1e-12 * abs(t1) + 1e-300
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_fixed_iterations_sell(prec):
+    """A whole solve on the SELL-32 layout follows the oracle's iterates."""
+    p = w.anderson_small(L=12, K=24, delta=0.1)
+    orc = oc.shifted_cocg(p.H.to_scipy(), p.b, p.z, tol=0.0, maxiter=20, full=True)
+    s = kw.Solver(prec, tol=0.0, maxiter=20)
+    s.set_spmv_config(32, -1)
+    s.set_csr(p.H.rowptr, p.H.col, p.H.val)
+    g = s.solve(p.b, p.z, full=True)
+    assert s.spmv_config()[0] == 32
+    _compare_iterates(g, orc, True, 1e-10)
 
 
 def test_inexact_values_never_use_fp32_in_f64_mode():
@@ -147,7 +182,7 @@ def test_inexact_values_never_use_fp32_in_f64_mode():
     assert s.spmv_config() == (4, 0)
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
 def test_spmv_variants_c32(lanes):
     H = w.j1j2_chain(10, 1.0, 0.4, 0.2, seed=5).assemble()
     rng = np.random.default_rng(9)
