@@ -66,3 +66,35 @@ def test_fullsize_projected_vs_sampled_full_solutions(problem, prec):
     assert np.all(np.abs(got - ref) <= bound)
     # the full-mode run's own projections are the same numbers
     np.testing.assert_allclose(full.proj, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_fullsize_anderson_contour_sampled():
+    """Anderson L=160 (M=4,096,000, W=4), 2048 real-axis shifts (delta=0.005) and
+    2048 contour points, 16 Gaussian left vectors, tol 1e-8, projected mode in the
+    FP32-pair form; 4 sampled shifts (including the near-axis circle points, the
+    slowest) re-solved in full mode and checked on the CPU."""
+    from paper_2001_08707_gb300 import build
+
+    build.build()
+    p = w.anderson_contour()
+    assert p.H.m == 4096000 and p.z.size == 4096 and p.left.shape == (16, 4096000)
+    bd = torch.as_tensor(p.b, device="cuda")
+    ld = torch.as_tensor(p.left, device="cuda")
+    s = kw.Solver("df64", tol=p.tol, maxiter=300000)
+    s.set_csr(p.H.rowptr, p.H.col, p.H.val)
+    proj = s.solve(bd, p.z, left=ld)
+    print(f"contour: {proj.iters} iterations, status {proj.status}")
+    assert proj.status == "KW_OK" and proj.n_converged == p.z.size
+    near_axis = 2048 + int(np.argmin(np.abs(p.z[2048:].imag)))
+    sample = np.array([5, 1024, 2048 + 512, near_axis])
+    zs = p.z[sample]
+    full = s.solve(bd, zs, left=ld, full=True)
+    assert full.status == "KW_OK"
+    x = full.x.cpu().numpy()
+    tr = oc.true_residuals(p.H.to_scipy(), p.b, zs, x)
+    print(f"contour: true residuals {tr}")
+    assert np.all(tr <= 10 * p.tol)
+    P = np.vstack([p.b, p.left])
+    ref = x @ P.T
+    bound = 2 * p.tol * np.linalg.norm(P, axis=1)[None, :] / np.abs(zs.imag)[:, None]
+    assert np.all(np.abs(proj.proj[sample] - ref) <= bound)
