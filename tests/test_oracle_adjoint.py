@@ -1,0 +1,54 @@
+"""CPU pins for the oracle gradient of the spectrum (oracle/adjoint.py).
+
+* Dense: dA_k/dtheta_m from the explicit inverse, -(1/pi) Im b^T G H_m G b.
+* Central differences of the oracle's own spectrum (forward solves only).
+* A step along -grad lowers the loss.
+"""
+import numpy as np
+
+from oracle import adjoint as oa
+from paper_2001_08707_gb300 import workloads as w
+
+
+def _model(N=8, seed=3):
+    j = w.j1j2_chain(N, 1.0, 0.4, 0.2, seed=seed)
+    terms = [t.to_scipy() for t in j.terms]
+    b = w.gaussian_unit(j.terms[0].m, seed)
+    z = w.shiftk_grid(-3.0, 2.0, 12, 0.2)
+    return j, terms, b, z
+
+
+def test_gradient_matches_dense_inverse():
+    j, terms, b, z = _model()
+    _, _, _, dA = oa.spectrum_and_gradient(terms, j.theta, b, z, np.zeros(z.size), tol=1e-13)
+    H = oa.assemble(terms, j.theta).toarray()
+    M = H.shape[0]
+    for k, zk in enumerate(z):
+        G = np.linalg.inv(zk * np.eye(M) - H)
+        for m, Hm in enumerate(terms):
+            ref = -np.imag(b @ G @ Hm.toarray() @ G @ b) / np.pi
+            assert abs(dA[k, m] - ref) <= 1e-9 * (1 + abs(ref))
+
+
+def test_gradient_matches_central_differences():
+    j, terms, b, z = _model(N=10, seed=5)
+    rng = np.random.default_rng(0)
+    target = oa.spectrum(terms, j.theta + rng.normal(0, 0.05, j.theta.size), b, z, tol=1e-13)[0]
+    A, loss, grad, _ = oa.spectrum_and_gradient(terms, j.theta, b, z, target, tol=1e-13)
+    h = 1e-5
+    for m in range(j.theta.size):
+        e = np.zeros_like(j.theta)
+        e[m] = h
+        Ap = oa.spectrum(terms, j.theta + e, b, z, tol=1e-13)[0]
+        Am = oa.spectrum(terms, j.theta - e, b, z, tol=1e-13)[0]
+        fd = (0.5 * np.sum((Ap - target) ** 2) - 0.5 * np.sum((Am - target) ** 2)) / (2 * h)
+        assert abs(fd - grad[m]) <= 1e-6 * (abs(grad[m]) + 1e-3), (m, fd, grad[m])
+
+
+def test_descent_direction_lowers_loss():
+    j, terms, b, z = _model()
+    target = oa.spectrum(terms, j.theta * 1.02, b, z, tol=1e-13)[0]
+    _, loss, grad, _ = oa.spectrum_and_gradient(terms, j.theta, b, z, target, tol=1e-13)
+    _, loss2, _, _ = oa.spectrum_and_gradient(terms, j.theta - 1e-3 * grad / np.linalg.norm(grad), b, z, target,
+                                              tol=1e-13)
+    assert loss2 < loss
