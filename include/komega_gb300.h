@@ -204,6 +204,30 @@ kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out);
  * FP64 dot. */
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host);
 
+/* One parameter matrix H_t of H(theta) = sum_t theta_t H_t, as a device CSR
+ * matrix with the layout of kw_set_csr (int64 rowptr [m+1], int32 col, f64 val). */
+typedef struct {
+    int64_t nnz;
+    const int64_t* rowptr_dev;
+    const int32_t* col_dev;
+    const double* val_dev;
+} kw_csr_term;
+
+/* Adjoint bilinear forms for the parameter derivative of the Green's function.
+ * With G(z) = (z I - H)^{-1} (Eq. 2) and H = sum_t theta_t H_t,
+ * dG/dtheta_t = G H_t G, and G^T = G for real symmetric H, so
+ *     d(a^T G(z_k) b)/dtheta_t = y_k^T H_t x_k,  x_k = G(z_k) b,  y_k = G(z_k) a
+ * (y_k = x_k when a = b).  This call forms out[k][t] = y_k^T H_t x_k
+ * (unconjugated) for every shift k and term t.
+ *   m: rows; terms_host: nterm term descriptors (device arrays, m x m each);
+ *   X_dev, Y_dev: [nshift][m] kw_c128 device arrays (x_k from kw_solve in full
+ *   mode with KW_F64 or KW_DF64); Y_dev NULL means Y = X.
+ *   out_host: kw_c128 [nshift][nterm].
+ * FP64 arithmetic; uses the context's stream and workspace.  Errors:
+ * KW_ERR_ARG (sizes, NULL pointers), KW_ERR_OOM, KW_ERR_CUDA. */
+kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms_host, int64_t nshift,
+                      const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host);
+
 /* Most thread blocks kw_spmv_dot_noalloc launches; its static scratch holds
  * one FP64 complex partial per block (64 KiB) plus a counter and the result. */
 #define KW_NOALLOC_MAX_BLOCKS 4096

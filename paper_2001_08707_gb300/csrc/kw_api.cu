@@ -77,6 +77,7 @@ struct kw_ctx {
   // host-solve copies
   DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
   // workspace
+  DBuf bil_part, bil_out;     // kw_bilinear scratch and result
   DBuf rA, rB, q, proj_rows, z, pi1, pi0, active, conv_iter, final_res, coef, coef_pair, Y, U, w, w0, hist, list,
       X, P, part, st, projx, tdot;
   kw::State* st_host = nullptr;   // pinned
@@ -168,7 +169,7 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
 void kw_destroy(kw_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
-  DBuf* bufs[] = {&ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->sell_perm, &ctx->sell_len,
+  DBuf* bufs[] = {&ctx->bil_part, &ctx->bil_out, &ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->sell_perm, &ctx->sell_len,
                   &ctx->sell_slen, &ctx->sell_ptr, &ctx->sell_col, &ctx->sell_val, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
@@ -654,6 +655,32 @@ kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec
   if (hist_host && ctx->last_nrec > 0)
     KW_CUDA(cudaMemcpy(hist_host, ctx->hist.p, (size_t)ctx->last_nrec * ctx->last_K * 8, cudaMemcpyDeviceToHost),
             "read history");
+  return KW_OK;
+}
+
+kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms, int64_t nshift,
+                      const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host) {
+  if (!ctx) return KW_ERR_ARG;
+  if (m < 1 || m > 0x7fffffffLL || nterm < 1 || nshift < 1 || nshift > 0x7fffffffLL || !terms || !X_dev || !out_host)
+    return fail(ctx, KW_ERR_ARG, "kw_bilinear: invalid sizes or NULL pointer");
+  for (int64_t t = 0; t < nterm; ++t)
+    if (!terms[t].rowptr_dev || terms[t].nnz < 0 || terms[t].nnz > 0x7fffffffLL ||
+        (terms[t].nnz > 0 && (!terms[t].col_dev || !terms[t].val_dev)))
+      return fail(ctx, KW_ERR_ARG, "kw_bilinear: term %lld is invalid", (long long)t);
+  const int nblk = 2 * ctx->num_sms;
+  const int64_t ntile = (nshift + kw::kBilinearTile - 1) / kw::kBilinearTile;
+  KW_CUDA(ctx->bil_part.ensure((size_t)ntile * nblk * kw::kBilinearTile * 16), "kw_bilinear: scratch");
+  KW_CUDA(ctx->bil_out.ensure((size_t)nshift * nterm * 16), "kw_bilinear: result");
+  const double2* X = (const double2*)X_dev;
+  const double2* Y = Y_dev ? (const double2*)Y_dev : X;
+  for (int64_t t = 0; t < nterm; ++t)
+    KW_CUDA(kw::launch_bilinear((int)m, (int)nshift, terms[t].rowptr_dev, terms[t].col_dev, terms[t].val_dev, X, Y,
+                                nblk, (double2*)ctx->bil_part.p, (int)t, (int)nterm, (double2*)ctx->bil_out.p,
+                                ctx->stream),
+            "kw_bilinear launch");
+  KW_CUDA(cudaMemcpyAsync(out_host, ctx->bil_out.p, (size_t)nshift * nterm * 16, cudaMemcpyDeviceToHost, ctx->stream),
+          "kw_bilinear read");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_bilinear sync");
   return KW_OK;
 }
 

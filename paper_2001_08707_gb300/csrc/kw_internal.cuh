@@ -123,6 +123,12 @@ template <class RV>
 cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,
                              const int* col, const void* val, int* scol, void* sval, cudaStream_t s);
 
+// Adjoint bilinear forms (kw_bilinear): shifts per tile and the launcher.
+constexpr int kBilinearTile = 8;
+cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,
+                            const double2* X, const double2* Y, int nblk, double2* part, int term, int nterm,
+                            double2* out, cudaStream_t s);
+
 // Upper bound on resident 256-thread blocks per SM (2048 threads per SM).
 constexpr int kMaxBlocksPerSM = 8;
 

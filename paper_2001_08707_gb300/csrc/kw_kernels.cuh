@@ -742,6 +742,70 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
   }
 }
 
+// ================================================================ adjoint bilinear forms
+// out[k] = y_k^T H x_k (unconjugated) for a tile of BT shifts: one thread per
+// row reads the row's indices and values once and applies them to every shift
+// of the tile.  X, Y: [K][m] FP64 complex, shift-major.  Per-block partials
+// part[(tile * gridDim.x + block) * BT + t] are summed by k_bilinear_reduce.
+template <int BT>
+__global__ void __launch_bounds__(256)
+k_bilinear(int m, int K, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+           const double* __restrict__ val, const double2* __restrict__ X, const double2* __restrict__ Y,
+           double2* __restrict__ part) {
+  const int tile = blockIdx.y, k0 = tile * BT;
+  const int nt = min(BT, K - k0);
+  double re[BT], im[BT];
+#pragma unroll
+  for (int t = 0; t < BT; ++t) re[t] = im[t] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int beg = (int)rowptr[i], end = (int)rowptr[i + 1];
+#pragma unroll
+    for (int t = 0; t < BT; ++t) {
+      if (t < nt) {
+        const double2* xk = X + (size_t)(k0 + t) * m;
+        double2 s = make_double2(0.0, 0.0);
+        for (int j = beg; j < end; ++j) {
+          const double v = val[j];
+          const double2 x = xk[col[j]];
+          s.x = fma(v, x.x, s.x);
+          s.y = fma(v, x.y, s.y);
+        }
+        const double2 y = Y[(size_t)(k0 + t) * m + i];
+        re[t] = fma(y.x, s.x, fma(-y.y, s.y, re[t]));
+        im[t] = fma(y.x, s.y, fma(y.y, s.x, im[t]));
+      }
+    }
+  }
+  __shared__ double red[2 * BT];
+  double v[2 * BT];
+#pragma unroll
+  for (int t = 0; t < BT; ++t) {
+    v[2 * t] = re[t];
+    v[2 * t + 1] = im[t];
+  }
+  block_sum<2 * BT, double>(v, 2 * BT, red);
+  if (threadIdx.x < BT) {
+    const size_t o = ((size_t)tile * gridDim.x + blockIdx.x) * BT + threadIdx.x;
+    part[o] = make_double2(red[2 * threadIdx.x], red[2 * threadIdx.x + 1]);
+  }
+}
+
+// out[k * nterm + term] = sum over blocks of the partials, fixed order.
+template <int BT>
+__global__ void k_bilinear_reduce(int K, int nblk, int term, int nterm, const double2* __restrict__ part,
+                                  double2* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const int tile = k / BT, t = k % BT;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) {
+    const double2 p = part[((size_t)tile * nblk + b) * BT + t];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  out[(size_t)k * nterm + term] = s;
+}
+
 // ================================================================ initialisation
 template <int P>
 __global__ void k_init_vectors(int m, int np, const double* __restrict__ b, const double* __restrict__ left,

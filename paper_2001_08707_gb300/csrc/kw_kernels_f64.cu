@@ -45,4 +45,17 @@ template cudaError_t launch_sell_fill<float>(int, const int*, const int*, const 
                                               const int*, const void*, int*, void*, cudaStream_t);
 template cudaError_t launch_sell_fill<df>(int, const int*, const int*, const int64_t*, const int64_t*, const int*,
                                            const void*, int*, void*, cudaStream_t);
+
+// Bilinear forms y_k^T H x_k of one term for every shift; partials need
+// kBilinearTile * nblk * ceil(K / kBilinearTile) double2.
+cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,
+                            const double2* X, const double2* Y, int nblk, double2* part, int term, int nterm,
+                            double2* out, cudaStream_t s) {
+  const int ntile = (K + kBilinearTile - 1) / kBilinearTile;
+  k_bilinear<kBilinearTile><<<dim3(nblk, ntile), 256, 0, s>>>(m, K, rowptr, col, val, X, Y, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_bilinear_reduce<kBilinearTile><<<(K + 127) / 128, 128, 0, s>>>(K, nblk, term, nterm, part, out);
+  return cudaGetLastError();
+}
 }  // namespace kw

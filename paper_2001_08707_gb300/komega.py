@@ -41,6 +41,10 @@ class kw_solve_info(C.Structure):
                 ("n_seed_switch", C.c_int64), ("updates", C.c_int64), ("seed", C.c_int64), ("status", C.c_int)]
 
 
+class kw_csr_term(C.Structure):
+    _fields_ = [("nnz", C.c_int64), ("rowptr_dev", C.c_void_p), ("col_dev", C.c_void_p), ("val_dev", C.c_void_p)]
+
+
 class kw_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("timed_iters", C.c_int64), ("kernel_ms", C.c_double * 4)]
 
@@ -74,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_kernel_timing": (C.c_int, [P, I64]),
         "kw_get_stats": (C.c_int, [P, C.POINTER(kw_stats)]),
         "kw_set_spmv_config": (C.c_int, [P, C.c_int, C.c_int]),
+        "kw_bilinear": (C.c_int, [P, I64, I64, C.POINTER(kw_csr_term), I64, P, P, P]),
         "kw_spmv_dot_noalloc": (C.c_int, [I64, I64, P, P, P, kw_c128, P, P, C.POINTER(kw_c128), P]),
         "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     }
@@ -285,6 +290,20 @@ class Solver:
         if st != KW_OK:
             raise self._err(st, "kw_get_stats")
         return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms)}
+
+    def bilinear(self, terms, X, Y=None) -> np.ndarray:
+        """kw_bilinear: out[k][t] = y_k^T H_t x_k for device CSR terms (each a tuple of
+        CUDA tensors (rowptr int64, col int32, val float64)) and X, Y [K, m] complex128."""
+        K, m = X.shape
+        arr = (kw_csr_term * len(terms))()
+        for i, (rp, cl, vl) in enumerate(terms):
+            arr[i] = kw_csr_term(cl.numel(), rp.data_ptr(), cl.data_ptr(), vl.data_ptr())
+        out = np.zeros((K, len(terms)), dtype=np.complex128)
+        st = self._lib.kw_bilinear(self._ctx, m, len(terms), arr, K, C.c_void_p(X.data_ptr()),
+                                   None if Y is None else C.c_void_p(Y.data_ptr()), out.ctypes.data_as(C.c_void_p))
+        if st != KW_OK:
+            raise self._err(st, "kw_bilinear")
+        return out
 
     def spmv_dot(self, zs: complex, r, q):
         """q = zs r - H r and t = r^T q on the device.  r, q: device tensors in the

@@ -1,0 +1,93 @@
+"""GPU checks of the hand-written adjoint (kw_bilinear + GreenSpectrum).
+
+d A_k / d theta_t = -(1/pi) Im(x_k^T H_t x_k) (from dG/dtheta = G H_t G,
+G^T = G).  Checked against numpy bilinear forms, the oracle gradient (reduced
+size) and central differences of the GPU's own forward solves (full size:
+J1-J2 chain N=20, M=184,756, 22 parameters, K=256 shifts at delta=0.05)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import adjoint as oa
+from paper_2001_08707_gb300 import adjoint
+from paper_2001_08707_gb300 import komega as kw
+from paper_2001_08707_gb300 import workloads as w
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2001_08707_gb300 import build
+
+    build.build()
+
+
+def test_bilinear_matches_numpy():
+    j = w.j1j2_chain(10, 1.0, 0.4, 0.2, seed=2)
+    m = j.terms[0].m
+    rng = np.random.default_rng(3)
+    K = 13                                       # not a multiple of the shift tile
+    X = rng.standard_normal((K, m)) + 1j * rng.standard_normal((K, m))
+    Y = rng.standard_normal((K, m)) + 1j * rng.standard_normal((K, m))
+    s = kw.Solver("f64")
+    ts = adjoint.TermSet(j.terms)
+    Xd, Yd = torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")
+    for y_is_x in (True, False):
+        out = s.bilinear(ts.device_terms, Xd, None if y_is_x else Yd)
+        YY = X if y_is_x else Y
+        ref = np.stack([np.sum(YY * (t.to_scipy() @ X.T).T, axis=1) for t in j.terms], axis=1)
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def _problem(N, K, seed=w.SEED_BASE + 3):
+    j = w.j1j2_chain(N, 1.0, 0.4, 0.2, seed=seed)
+    lo, hi = w.chain_bounds(j.assemble())
+    z = w.shiftk_grid(lo - 0.5, hi + 0.5, K, 0.05)
+    b = w.gaussian_unit(j.terms[0].m, seed)
+    rng = np.random.default_rng([seed, w.STREAM_PERTURB])
+    theta_star = j.theta + rng.normal(0.0, 0.05, j.theta.size)
+    return j, z, b, theta_star
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_gradient_matches_oracle(prec):
+    j, z, b, theta_star = _problem(12, 32)
+    terms = [t.to_scipy() for t in j.terms]
+    target = oa.spectrum(terms, theta_star, b, z, tol=1e-12)[0]
+    A_o, loss_o, grad_o, _ = oa.spectrum_and_gradient(terms, j.theta, b, z, target, tol=1e-12)
+    model = adjoint.GreenSpectrum(j.terms, b, z, prec=prec, tol=1e-12)
+    theta = torch.tensor(j.theta, dtype=torch.float64, requires_grad=True)
+    A = model(theta)
+    loss = 0.5 * torch.sum((A - torch.as_tensor(target)) ** 2)
+    loss.backward()
+    np.testing.assert_allclose(A.detach().numpy(), A_o, rtol=0, atol=1e-10 * np.abs(A_o).max())
+    g = theta.grad.numpy()
+    assert np.abs(g - grad_o).max() <= 1e-8 * np.abs(grad_o).max(), (g, grad_o)
+
+
+def test_fullsize_gradient_vs_central_differences():
+    """J1-J2 N=20 with 22 parameters, K=256 shifts: adjoint gradient of the
+    quadratic spectrum loss against central differences (step 1e-5) of the GPU's
+    own forward solves for J1, J2 and two site fields."""
+    j, z, b, theta_star = _problem(20, 256)
+    assert j.terms[0].m == 184756 and len(j.terms) == 22
+    model = adjoint.GreenSpectrum(j.terms, b, z, prec="df64", tol=1e-12)
+    target = model.solve(theta_star)[0]
+    theta = torch.tensor(j.theta, dtype=torch.float64, requires_grad=True)
+    A = model(theta)
+    loss = 0.5 * torch.sum((A - torch.as_tensor(target)) ** 2)
+    loss.backward()
+    g = theta.grad.numpy()
+    h = 1e-5
+    for t in (0, 1, 2, 11):
+        e = np.zeros(j.theta.size)
+        e[t] = h
+        lp = 0.5 * np.sum((model.solve(j.theta + e)[0] - target) ** 2)
+        lm = 0.5 * np.sum((model.solve(j.theta - e)[0] - target) ** 2)
+        fd = (lp - lm) / (2 * h)
+        print(f"param {t}: adjoint {g[t]:.10e} central difference {fd:.10e}")
+        assert abs(fd - g[t]) <= 1e-5 * abs(g[t]) + 1e-9
