@@ -153,6 +153,33 @@ kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowp
                         const double* left_host, void* x_out_host, kw_c128* proj_out_host,
                         kw_solve_info* info);
 
+/* One problem of a batch: an operator, a right-hand side and its shifts. */
+typedef struct {
+    int64_t m, nnz;
+    const int64_t* rowptr_dev;     /* as in kw_set_csr */
+    const int32_t* col_dev;
+    const double* val_dev;
+    const double* b_dev;           /* [m] */
+    int64_t nshift;
+    const kw_c128* z_host;         /* [nshift] */
+    int64_t nleft;
+    const double* left_dev;        /* [nleft][m] or NULL */
+    void* x_out_dev;               /* full mode: [nshift][m] as in kw_solve; NULL: projected */
+    kw_c128* proj_out_host;        /* [nshift][nleft+1] or NULL */
+    double tol;                    /* > 0 overrides the context's tolerance for this problem */
+} kw_instance;
+
+/* Solve n independent problems (uneven sizes and shift counts) together.
+ * Each instance runs the kw_solve iteration on its own stream and workspace,
+ * owned by the context and reused by later calls; one CUDA graph holds a chunk
+ * of iterations of every instance, and the host replays it until every
+ * instance has stopped (instances that stop early return from their kernels at
+ * the first instruction).  Results are those kw_solve gives for each instance
+ * alone.  info: [n] or NULL.  Returns KW_OK if every instance converged, else
+ * the first other status (per-instance status in info).  Errors: KW_ERR_ARG
+ * (n < 1, NULL pointer, an instance's own argument errors), KW_ERR_CUDA. */
+kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_solve_info* info);
+
 /* Per-shift results of the last solve: the iteration at which shift k met the
  * tolerance (-1 if never) and its last residual estimate ||r_n||/|pi_n^k|.
  * Either pointer may be NULL.  Arrays have the last solve's nshift entries. */

@@ -87,6 +87,15 @@ struct kw_ctx {
   int64_t timing_every = 0;
   cudaEvent_t kev[2][5] = {};
   kw_stats stats = {};
+  // phases of a solve
+  kw::Work work;
+  int64_t work_K = 0;
+  // batched solves: one child context (own stream) per instance
+  std::vector<kw_ctx*> children;
+  cudaStream_t batch_stream = nullptr;   // capturable stream of kw_solve_batched
+  bool owns_stream = false;
+  DBuf child_states, done_count;
+  int* done_host = nullptr;   // pinned
   // last solve
   int64_t last_K = 0;
   int64_t last_nrec = 0;
@@ -175,6 +184,12 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot};
   for (DBuf* b : bufs) b->release();
+  for (kw_ctx* c : ctx->children) kw_destroy(c);
+  if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
+  ctx->child_states.release();
+  ctx->done_count.release();
+  if (ctx->done_host) cudaFreeHost(ctx->done_host);
+  if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
   if (ctx->flags_host) cudaFreeHost(ctx->flags_host);
   for (int i = 0; i < 2; ++i) {
@@ -496,11 +511,51 @@ static void collect_times(kw_ctx* ctx, int slot, bool full) {
   ctx->stats.timed_iters += 1;
 }
 
-template <int P>
-static kw_status run(kw_ctx* ctx, kw::Work& w) {
-  KW_CUDA(kw::launch_init<P>(w), "init kernels");
-  ctx->stats.launches += w.full ? 5 : 4;
-  const int CH = 16;
+static cudaError_t init_launch(kw::Work& w) {
+  switch (w.prec) {
+    case kw::PREC_C32: return kw::launch_init<kw::PREC_C32>(w);
+    case kw::PREC_DF: return kw::launch_init<kw::PREC_DF>(w);
+    default: return kw::launch_init<kw::PREC_F64>(w);
+  }
+}
+
+static cudaError_t iteration_launch(kw::Work& w, int parity, cudaEvent_t* ev, int64_t* launches) {
+  switch (w.prec) {
+    case kw::PREC_C32: return kw::launch_iteration<kw::PREC_C32>(w, parity, ev, launches);
+    case kw::PREC_DF: return kw::launch_iteration<kw::PREC_DF>(w, parity, ev, launches);
+    default: return kw::launch_iteration<kw::PREC_F64>(w, parity, ev, launches);
+  }
+}
+
+// Phase 1 of a solve: validate, tune, allocate, upload and enqueue the
+// initialisation (no synchronisation).  The descriptor is kept in ctx->work.
+static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
+                             const double* left_dev, void* x_out_dev) {
+  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_solve: kw_set_csr has not been called");
+  if (!b_dev || !z_host || nshift < 1 || nshift > 0x7fffffffLL)
+    return fail(ctx, KW_ERR_ARG, "kw_solve: need b, z and 1 <= nshift < 2^31");
+  if (nleft < 0 || nleft >= KW_MAX_PROJ || (nleft > 0 && !left_dev))
+    return fail(ctx, KW_ERR_ARG, "kw_solve: need 0 <= nleft < %d and left vectors when nleft > 0", KW_MAX_PROJ);
+  for (int64_t k = 0; k < nshift; ++k)
+    if (!isfinite(z_host[k].re) || !isfinite(z_host[k].im))
+      return fail(ctx, KW_ERR_ARG, "kw_solve: shift %lld is not finite", (long long)k);
+  memset(&ctx->stats, 0, sizeof(ctx->stats));
+  kw_status s = tune_spmv(ctx);
+  if (s != KW_OK) return s;
+  s = prepare(ctx, ctx->work, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
+  if (s != KW_OK) return s;
+  ctx->work_K = nshift;
+  KW_CUDA(init_launch(ctx->work), "init kernels");
+  ctx->stats.launches += ctx->work.full ? 5 : 4;
+  return KW_OK;
+}
+
+static const int kChunk = 16;   // iterations per chunk (even: buffer parity repeats)
+
+// Phase 2 for one context: enqueue chunks and poll the device stop flag one
+// chunk behind; returns after the stream has drained.
+static kw_status run_loop(kw_ctx* ctx) {
+  kw::Work& w = ctx->work;
   const bool timing = ctx->timing_every > 0;
   int64_t launched = 0;
   int slot = 0;
@@ -508,13 +563,13 @@ static kw_status run(kw_ctx* ctx, kw::Work& w) {
   int64_t sampled_at[2] = {-1, -1};
   for (;;) {
     sampled_at[slot] = -1;
-    for (int i = 0; i < CH; ++i) {
+    for (int i = 0; i < kChunk; ++i) {
       cudaEvent_t* ev = nullptr;
-      if (timing && i == 0 && (launched / CH) % ctx->timing_every == 0) {
+      if (timing && i == 0 && (launched / kChunk) % ctx->timing_every == 0) {
         ev = ctx->kev[slot];
         sampled_at[slot] = launched;
       }
-      KW_CUDA(kw::launch_iteration<P>(w, (int)(launched & 1), ev, &ctx->stats.launches), "iteration launch");
+      KW_CUDA(iteration_launch(w, (int)(launched & 1), ev, &ctx->stats.launches), "iteration launch");
       ++launched;
     }
     KW_CUDA(cudaMemcpyAsync(ctx->flags_host + slot, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
@@ -528,41 +583,21 @@ static kw_status run(kw_ctx* ctx, kw::Work& w) {
     }
     have_prev = true;
     slot ^= 1;
-    if (launched > ctx->opt.maxiter + 2 * CH) break;   // the device stops at maxiter; never loop forever
+    if (launched > ctx->opt.maxiter + 2 * kChunk) break;   // the device stops at maxiter; never loop forever
   }
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
   return KW_OK;
 }
 
-extern "C" {
-
-kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
-                   const double* left_dev, void* x_out_dev, kw_c128* proj_out_host, kw_solve_info* info) {
-  if (!ctx) return KW_ERR_ARG;
-  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_solve: kw_set_csr has not been called");
-  if (!b_dev || !z_host || nshift < 1 || nshift > 0x7fffffffLL)
-    return fail(ctx, KW_ERR_ARG, "kw_solve: need b, z and 1 <= nshift < 2^31");
-  if (nleft < 0 || nleft >= KW_MAX_PROJ || (nleft > 0 && !left_dev))
-    return fail(ctx, KW_ERR_ARG, "kw_solve: need 0 <= nleft < %d and left vectors when nleft > 0", KW_MAX_PROJ);
-  for (int64_t k = 0; k < nshift; ++k)
-    if (!isfinite(z_host[k].re) || !isfinite(z_host[k].im))
-      return fail(ctx, KW_ERR_ARG, "kw_solve: shift %lld is not finite", (long long)k);
-  kw::Work w;
-  memset(&ctx->stats, 0, sizeof(ctx->stats));
-  kw_status s = tune_spmv(ctx);
-  if (s != KW_OK) return s;
-  s = prepare(ctx, w, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
-  if (s != KW_OK) return s;
-  s = w.prec == kw::PREC_C32 ? run<kw::PREC_C32>(ctx, w)
-      : w.prec == kw::PREC_DF ? run<kw::PREC_DF>(ctx, w)
-                              : run<kw::PREC_F64>(ctx, w);
-  if (s != KW_OK) return s;
-  if (w.full) {   // FP32-pair x is converted to FP64 in place (the caller's buffer holds kw_c128)
-    cudaError_t e = w.prec == kw::PREC_DF ? kw::launch_finish_x<kw::PREC_DF>(w) : cudaSuccess;
-    KW_CUDA(e, "finish x");
+// Phase 3 (the context's stream has drained): outputs and summary.
+static kw_status solve_end(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* info) {
+  kw::Work& w = ctx->work;
+  const int64_t nshift = ctx->work_K;
+  if (w.full && w.prec == kw::PREC_DF) {   // FP32-pair x is converted to FP64 in place (the caller's buffer holds kw_c128)
+    KW_CUDA(kw::launch_finish_x<kw::PREC_DF>(w), "finish x");
   }
-  if (s != KW_OK) return s;
-  KW_CUDA(cudaMemcpy(ctx->st_host, w.st, sizeof(kw::State), cudaMemcpyDeviceToHost), "read state");
+  KW_CUDA(cudaMemcpyAsync(ctx->st_host, w.st, sizeof(kw::State), cudaMemcpyDeviceToHost, ctx->stream), "read state");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "state sync");
   const kw::State& st = *ctx->st_host;
   ctx->last_K = nshift;
   ctx->last_nrec = st.n_rec;
@@ -604,6 +639,145 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
          (long long)st.iter);
   }
   return (kw_status)st.status;
+}
+
+extern "C" {
+
+kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
+                   const double* left_dev, void* x_out_dev, kw_c128* proj_out_host, kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  kw_status s = solve_begin(ctx, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
+  if (s != KW_OK) return s;
+  s = run_loop(ctx);
+  if (s != KW_OK) return s;
+  return solve_end(ctx, proj_out_host, info);
+}
+
+kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  if (n < 1 || n > 65536 || !inst) return fail(ctx, KW_ERR_ARG, "kw_solve_batched: need 1 <= n <= 65536 instances");
+  // the caller's stream may be the legacy default stream, which cannot be
+  // captured: the batch runs on an own stream ordered after the caller's work
+  if (!ctx->batch_stream)
+    KW_CUDA(cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking), "kw_solve_batched: stream");
+  cudaStream_t bs = ctx->batch_stream;
+  {
+    cudaEvent_t e0;
+    KW_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "kw_solve_batched: event");
+    cudaError_t e = cudaEventRecord(e0, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, e0, 0);
+    cudaEventDestroy(e0);
+    KW_CUDA(e, "kw_solve_batched: order after the caller's stream");
+  }
+  // child contexts, one stream each
+  while ((int64_t)ctx->children.size() < n) {
+    cudaStream_t s = nullptr;
+    KW_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "kw_solve_batched: stream");
+    kw_ctx* c = nullptr;
+    kw_status cs = kw_create(&c, &ctx->opt, s);
+    if (cs != KW_OK) {
+      cudaStreamDestroy(s);
+      return fail(ctx, cs, "kw_solve_batched: child context");
+    }
+    c->owns_stream = true;
+    ctx->children.push_back(c);
+  }
+  // begin every instance on its own stream; the batch stream waits for all initialisations
+  std::vector<cudaEvent_t> ev(n + 1, nullptr);
+  for (int64_t i = 0; i <= n; ++i) KW_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "batch events");
+  kw_status result = KW_OK;
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  KW_CUDA(cudaEventRecord(ev[n], bs), "batch event");   // instances start after the caller's work
+  for (int64_t i = 0; i < n; ++i) {
+    kw_ctx* c = ctx->children[i];
+    c->opt = ctx->opt;
+    if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
+    KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
+    kw_status s = kw_set_csr(c, inst[i].m, inst[i].nnz, inst[i].rowptr_dev, inst[i].col_dev, inst[i].val_dev);
+    if (s == KW_OK)
+      s = solve_begin(c, inst[i].b_dev, inst[i].nshift, inst[i].z_host, inst[i].nleft, inst[i].left_dev,
+                      inst[i].x_out_dev);
+    if (s != KW_OK) {
+      cleanup();
+      return fail(ctx, s, "kw_solve_batched: instance %lld: %s", (long long)i, c->err);
+    }
+    KW_CUDA(cudaEventRecord(ev[i], c->stream), "batch event");
+    KW_CUDA(cudaStreamWaitEvent(bs, ev[i], 0), "batch wait");
+  }
+  // device list of the instances' states for the done counter
+  std::vector<kw::State*> sts(n);
+  for (int64_t i = 0; i < n; ++i) sts[i] = ctx->children[i]->work.st;
+  KW_CUDA(ctx->child_states.ensure((size_t)n * sizeof(void*)), "batch alloc");
+  KW_CUDA(ctx->done_count.ensure(sizeof(int)), "batch alloc");
+  if (!ctx->done_host) KW_CUDA(cudaMallocHost((void**)&ctx->done_host, 2 * sizeof(int)), "batch alloc");
+  KW_CUDA(cudaMemcpyAsync(ctx->child_states.p, sts.data(), (size_t)n * sizeof(void*), cudaMemcpyHostToDevice,
+                          bs), "batch upload");
+  KW_CUDA(cudaStreamSynchronize(bs), "batch sync");
+  // one graph: a chunk of iterations of every instance (fork/join over the
+  // instance streams), then the count of finished instances
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  KW_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed), "batch capture");
+  cudaError_t ce = cudaEventRecord(ev[n], bs);
+  for (int64_t i = 0; i < n && ce == cudaSuccess; ++i) {
+    kw_ctx* c = ctx->children[i];
+    ce = cudaStreamWaitEvent(c->stream, ev[n], 0);
+    int64_t dummy = 0;
+    for (int it = 0; it < kChunk && ce == cudaSuccess; ++it) ce = iteration_launch(c->work, it & 1, nullptr, &dummy);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev[i], c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(bs, ev[i], 0);
+    c->stats.launches += 0;
+  }
+  if (ce == cudaSuccess) ce = kw::launch_count_done((int)n, (kw::State* const*)ctx->child_states.p,
+                                                   (int*)ctx->done_count.p, bs);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(ctx->done_host, ctx->done_count.p, sizeof(int), cudaMemcpyDeviceToHost, bs);
+  cudaError_t ee = cudaStreamEndCapture(bs, &graph);
+  if (ce == cudaSuccess) ce = ee;
+  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+  if (ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cleanup();
+    return cuda_fail(ctx, ce, "kw_solve_batched: graph capture");
+  }
+  int64_t maxit = ctx->opt.maxiter;
+  for (int64_t i = 0; i < n; ++i) maxit = std::max<int64_t>(maxit, ctx->children[i]->opt.maxiter);
+  int64_t launches = 0;
+  for (;;) {
+    ce = cudaGraphLaunch(exec, bs);
+    if (ce != cudaSuccess) break;
+    ++launches;
+    ce = cudaStreamSynchronize(bs);   // one chunk of the whole batch per graph launch
+    if (ce != cudaSuccess) break;
+    if (*(volatile int*)ctx->done_host >= n) break;
+    if (launches * kChunk > maxit + 2 * kChunk) break;   // every instance stops at its maxiter
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  cleanup();
+  if (ce != cudaSuccess) return cuda_fail(ctx, ce, "kw_solve_batched: graph launch");
+  for (int64_t i = 0; i < n; ++i) {
+    kw_ctx* c = ctx->children[i];
+    c->stats.launches += launches * kChunk * (c->work.full ? 4 : 3);
+    kw_status s = solve_end(c, inst[i].proj_out_host, info ? &info[i] : nullptr);
+    if (s != KW_OK && result == KW_OK) {
+      result = s;
+      fail(ctx, s, "kw_solve_batched: instance %lld: %s", (long long)i, c->err);
+    }
+  }
+  ctx->stats.launches = launches;
+  {   // the caller's stream is ordered after the batch
+    cudaEvent_t e1;
+    KW_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming), "kw_solve_batched: event");
+    cudaError_t e = cudaEventRecord(e1, bs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, e1, 0);
+    cudaEventDestroy(e1);
+    KW_CUDA(e, "kw_solve_batched: order the caller's stream");
+  }
+  return result;
 }
 
 kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_host, const int32_t* col_host,

@@ -123,6 +123,9 @@ template <class RV>
 cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,
                              const int* col, const void* val, int* scol, void* sval, cudaStream_t s);
 
+// Batched solves: count of instances whose solve has stopped (written to *out).
+cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_t s);
+
 // Adjoint bilinear forms (kw_bilinear): shifts per tile and the launcher.
 constexpr int kBilinearTile = 8;
 cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,

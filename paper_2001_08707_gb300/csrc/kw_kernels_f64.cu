@@ -46,6 +46,26 @@ template cudaError_t launch_sell_fill<float>(int, const int*, const int*, const 
 template cudaError_t launch_sell_fill<df>(int, const int*, const int*, const int64_t*, const int64_t*, const int*,
                                            const void*, int*, void*, cudaStream_t);
 
+// Number of instances of a batch whose solve has stopped.
+static __global__ void k_count_done(int n, State* const* states, int* out) {
+  int c = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) c += states[i]->done ? 1 : 0;
+  c = warp_sum((unsigned long long)c);
+  __shared__ int sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    *out = t;
+  }
+}
+
+cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_t s) {
+  k_count_done<<<1, 256, 0, s>>>(n, states, out);
+  return cudaGetLastError();
+}
+
 // Bilinear forms y_k^T H x_k of one term for every shift; partials need
 // kBilinearTile * nblk * ceil(K / kBilinearTile) double2.
 cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,

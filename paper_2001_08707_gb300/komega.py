@@ -45,6 +45,13 @@ class kw_csr_term(C.Structure):
     _fields_ = [("nnz", C.c_int64), ("rowptr_dev", C.c_void_p), ("col_dev", C.c_void_p), ("val_dev", C.c_void_p)]
 
 
+class kw_instance(C.Structure):
+    _fields_ = [("m", C.c_int64), ("nnz", C.c_int64), ("rowptr_dev", C.c_void_p), ("col_dev", C.c_void_p),
+                ("val_dev", C.c_void_p), ("b_dev", C.c_void_p), ("nshift", C.c_int64), ("z_host", C.c_void_p),
+                ("nleft", C.c_int64), ("left_dev", C.c_void_p), ("x_out_dev", C.c_void_p),
+                ("proj_out_host", C.c_void_p), ("tol", C.c_double)]
+
+
 class kw_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("timed_iters", C.c_int64), ("kernel_ms", C.c_double * 4)]
 
@@ -79,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "kw_get_stats": (C.c_int, [P, C.POINTER(kw_stats)]),
         "kw_set_spmv_config": (C.c_int, [P, C.c_int, C.c_int]),
         "kw_bilinear": (C.c_int, [P, I64, I64, C.POINTER(kw_csr_term), I64, P, P, P]),
+        "kw_solve_batched": (C.c_int, [P, I64, C.POINTER(kw_instance), C.POINTER(kw_solve_info)]),
         "kw_spmv_dot_noalloc": (C.c_int, [I64, I64, P, P, P, kw_c128, P, P, C.POINTER(kw_c128), P]),
         "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     }
@@ -290,6 +298,40 @@ class Solver:
         if st != KW_OK:
             raise self._err(st, "kw_get_stats")
         return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms)}
+
+    def solve_batched(self, problems, check: bool = True):
+        """kw_solve_batched over a list of problems, each a dict with keys H (CSR with
+        rowptr, col, val arrays), b, z and optionally left, full (default True) and
+        tol.  Returns one SolveResult per problem."""
+        t = self._torch
+        n = len(problems)
+        arr = (kw_instance * n)()
+        infos = (kw_solve_info * n)()
+        keep, outs = [], []
+        for i, pr in enumerate(problems):
+            H = pr["H"]
+            rp, cl, vl = self._dev(H.rowptr, t.int64), self._dev(H.col, t.int32), self._dev(H.val, t.float64)
+            bd = self._dev(pr["b"], t.float64)
+            zz, zp = _z_array(pr["z"])
+            left = pr.get("left")
+            ld = None if left is None else self._dev(np.atleast_2d(left), t.float64)
+            nleft = 0 if ld is None else ld.shape[0]
+            x = t.empty((zz.size, rp.numel() - 1), dtype=self.vec_dtype, device="cuda") if pr.get("full", True) \
+                else None
+            proj = np.zeros((zz.size, nleft + 1), dtype=np.complex128)
+            keep += [rp, cl, vl, bd, zz, ld, x, proj]
+            arr[i] = kw_instance(rp.numel() - 1, cl.numel(), rp.data_ptr(), cl.data_ptr(), vl.data_ptr(),
+                                 bd.data_ptr(), zz.size, zp.value, nleft, None if ld is None else ld.data_ptr(),
+                                 None if x is None else x.data_ptr(), proj.ctypes.data, float(pr.get("tol", 0.0)))
+            outs.append((proj, x))
+        st = self._lib.kw_solve_batched(self._ctx, n, arr, infos)
+        if check and st not in (KW_OK, KW_NOT_CONVERGED):
+            raise self._err(st, "kw_solve_batched")
+        res = []
+        for (proj, x), info in zip(outs, infos):
+            res.append(SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch,
+                                   info.updates, info.seed, STATUS.get(info.status, str(info.status))))
+        return res
 
     def bilinear(self, terms, X, Y=None) -> np.ndarray:
         """kw_bilinear: out[k][t] = y_k^T H_t x_k for device CSR terms (each a tuple of

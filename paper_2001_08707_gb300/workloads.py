@@ -284,6 +284,28 @@ def heisenberg_projected(N: int = 24, K: int = 1024, delta: float = 0.01, n_gaus
     return Problem(f"heisenberg_N{N}_K{K}_proj{left.shape[0]}", H, b, z, left, tol, False)
 
 
+def anderson_batch(n: int = 48, L_range=(16, 48), W_range=(2.0, 16.0), K_range=(32, 512),
+                   delta_range=(0.02, 0.1), seed: int = SEED_BASE + 2, tol: float = 1e-8) -> list:
+    """n independent Anderson cubes of uneven size: L integer-uniform in L_range,
+    disorder W uniform in W_range, K integer-uniform in K_range shifts on the
+    cube's Gershgorin interval +-0.5 with delta uniform in delta_range; each with
+    its own seeded b; full x returned."""
+    rng = np.random.default_rng([seed, STREAM_BATCH])
+    out = []
+    for i in range(n):
+        L = int(rng.integers(L_range[0], L_range[1] + 1))
+        W = float(rng.uniform(*W_range))
+        K = int(rng.integers(K_range[0], K_range[1] + 1))
+        delta = float(rng.uniform(*delta_range))
+        H = anderson_3d(L, W, seed * 1000 + i)
+        b = gaussian_unit(H.m, seed * 1000 + i)
+        lo, hi = anderson_bounds(W)
+        z = shiftk_grid(lo - 0.5, hi + 0.5, K, delta)
+        out.append(Problem(f"anderson_batch{i}_L{L}_K{K}", H, b, z, None, tol, True,
+                           {"L": L, "W": W, "delta": delta}))
+    return out
+
+
 def anderson_contour(L: int = 160, W: float = 4.0, n_real: int = 2048, n_circle: int = 2048,
                      n_left: int = 16, seed: int = SEED_BASE + 4, tol: float = 1e-8) -> Problem:
     """Anderson cube (L=160: M=4,096,000), 16 Gaussian left vectors, real-axis + circle shifts."""
