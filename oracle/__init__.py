@@ -6,7 +6,12 @@ the Komega paper (arXiv:2001.08707):
 * ``dense``: the plain definitions x_k = (z_k I - H)^{-1} b (Eq. 4-5) and the
   spectral (Lehmann) sum of Eq. 3, for small M.
 * ``shifted_cocg``: the shifted COCG iteration step by step (Sec. 2.2,
-  Appendix A), full and projected modes, seed switching.
+  Appendix A), full and projected modes, seed switching; with ``log=True`` it
+  also keeps the per-iteration record used for recalculation.
+* ``recalc``: projections at new shifts replayed from that record without
+  matrix-vector products (Sec. 3.3 (iv); Eqs. 20-22, 25-26).
+* ``adjoint``: the gradient of the spectrum with respect to the Hamiltonian's
+  parameters.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path

@@ -62,6 +62,27 @@ class OracleResult:
     alpha: list = field(default_factory=list)       # seed alpha_n per iteration
     beta: list = field(default_factory=list)        # seed beta_n per iteration
     updates: int = 0                 # sum over iterations of the number of active shifts
+    log: "KrylovLog | None" = None   # per-iteration record for recalculation (log=True)
+
+
+@dataclass
+class KrylovLog:
+    """What a run keeps so the projections can be recomputed at other shifts
+    without matrix-vector products (Sec. 3.3 (iv)): per iteration n the seed
+    shift used, the seed's alpha_n, c_n, beta_n, ||r_{n+1}||^2, the projected
+    residual P r_{n+1} (before any seed switch of that iteration) and the
+    switch factors pi^j_{n+1}, pi^j_n of the new seed j (1, 1 when the seed
+    was kept).  w0 = P r_0 = P b; thresh = tol * ||b||."""
+    zs: np.ndarray        # [n] complex
+    alpha: np.ndarray     # [n] complex
+    c: np.ndarray         # [n] complex
+    beta: np.ndarray      # [n] complex
+    nu: np.ndarray        # [n] real
+    pj1: np.ndarray       # [n] complex
+    pj0: np.ndarray       # [n] complex
+    w: np.ndarray         # [n, L+1] complex
+    w0: np.ndarray        # [L+1] complex
+    thresh: float
 
 
 def _matvec(H, v):
@@ -69,12 +90,13 @@ def _matvec(H, v):
 
 
 def shifted_cocg(H, b, z, left=None, tol=1e-10, maxiter=100000, full=True,
-                 seed_switch=True, hist_stride=1, seed0=0):
+                 seed_switch=True, hist_stride=1, seed0=0, log=False):
     """Solve (z_k I - H) x_k = b for all shifts z by shifted COCG.
 
     H: real symmetric matrix supporting ``H @ v`` (scipy sparse or dense).
     b: real [M].  z: complex [K].  left: real [L, M] or None.
     full: keep the x_k (Eqs. 23-24); otherwise only the projections (Eqs. 25-26).
+    log: also return the KrylovLog of the run (for ``oracle.recalc``).
     Returns an OracleResult; proj[:, 0] is b^T x_k in both modes.
     """
     b = np.asarray(b, dtype=np.float64)
@@ -113,6 +135,8 @@ def shifted_cocg(H, b, z, left=None, tol=1e-10, maxiter=100000, full=True,
     res = OracleResult(proj=None, x=None, iters=0, conv_iter=conv_iter, final_res=final_res,
                        hist=None, n_seed_switch=0, status=STATUS_NOT_CONVERGED)
 
+    lg = {key: [] for key in ("zs", "alpha", "c", "beta", "nu", "pj1", "pj0", "w")}
+
     n = 0
     while n < maxiter and active.any():
         # --- seed system: q = A r_n, alpha_n (Eq. 17), three-term update (Eq. 16)
@@ -133,6 +157,16 @@ def shifted_cocg(H, b, z, left=None, tol=1e-10, maxiter=100000, full=True,
         if not (np.isfinite(alpha) and np.isfinite(beta) and np.isfinite(nu_new)):
             res.status = STATUS_NONFINITE
             break
+
+        if log:
+            lg["zs"].append(z[s])
+            lg["alpha"].append(alpha)
+            lg["c"].append(c)
+            lg["beta"].append(beta)
+            lg["nu"].append(nu_new)
+            lg["w"].append(P @ r_new)
+            lg["pj1"].append(1.0 + 0.0j)
+            lg["pj0"].append(1.0 + 0.0j)
 
         # --- shifted systems (Eqs. 20-26), active shifts only
         k = np.nonzero(active)[0]
@@ -177,6 +211,9 @@ def shifted_cocg(H, b, z, left=None, tol=1e-10, maxiter=100000, full=True,
             j = ka[np.argmin(mag2)]                            # lowest index on ties
             if mag2.min() < 1.0:
                 pj_new, pj_old = pi[j], pi_old[j]
+                if log:
+                    lg["pj1"][-1] = pj_new
+                    lg["pj0"][-1] = pj_old
                 r = r / pj_new
                 r_old = r_old / pj_old
                 rho = np.dot(r, r)
@@ -199,6 +236,14 @@ def shifted_cocg(H, b, z, left=None, tol=1e-10, maxiter=100000, full=True,
     else:
         res.proj = Y
     res.hist = np.array(hist).reshape(-1, K)
+    if log:
+        n_log = n                                              # completed iterations only
+        cplx = lambda key: np.array(lg[key][:n_log], dtype=np.complex128).reshape(n_log)
+        res.log = KrylovLog(zs=cplx("zs"), alpha=cplx("alpha"), c=cplx("c"), beta=cplx("beta"),
+                            nu=np.array(lg["nu"][:n_log], dtype=np.float64).reshape(n_log), pj1=cplx("pj1"),
+                            pj0=cplx("pj0"),
+                            w=np.array(lg["w"][:n_log], dtype=np.complex128).reshape(n_log, P.shape[0]),
+                            w0=(P @ b).astype(np.complex128), thresh=float(thresh))
     return res
 
 
