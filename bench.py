@@ -49,7 +49,12 @@ PREC_NAMES = {"f64": "complex FP64 vectors, FP64 scalars",
               "c32": "complex FP32 vectors, FP64 scalars",
               "df64": "complex FP32-pair vectors (error-free FP32 arithmetic), FP64 scalars"}
 PREC_BYTES = {"f64": (16, 8), "c32": (8, 4), "df64": (16, 8)}   # complex vector element, real element
-FP64_PEAK_TFLOPS = 1.25   # nominal dense FP64 of a GB300 (a register-only FMA loop measured 1.20)
+FP64_PEAK_TFLOPS = 1.25
+# FP64 flops of one shift advanced by one logged row in k_recalc: the pi
+# recurrence, 1/pi, alpha^k, beta^k and the residual (scalar part), plus the
+# two complex updates of Eqs. 25-26 per projection column.
+RECALC_FLOPS_SCALAR = 62
+RECALC_FLOPS_COLUMN = 22   # nominal dense FP64 of a GB300 (a register-only FMA loop measured 1.20)
 
 
 def load_peaks():
@@ -367,6 +372,36 @@ def run_ours(args):
                    "iter_cap": cap, "status": c_res.status, "spectrum_rel_err_vs_headline": e_spec,
                    "projection_rel_err_vs_headline": e_proj}
 
+    # Recalculation at new shifts (Sec. 3.3 (iv)): one logged solve of the
+    # headline form (untimed), then kw_recalc at the K midpoints from the
+    # device log, timed with CUDA events (each call copies its outputs to the host).
+    sr = solver(HEADLINE, 200000)
+    sr.set_krylov_log(200000)
+    lr = sr.solve(bd, p.z, left=ld)
+    zm = p.z + (p.z[1] - p.z[0]).real / 2
+    sr.recalc(zm)
+    rc_times = []
+    for _ in range(max(args.steps, 3)):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = sr.recalc(zm)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rc_times.append(e0.elapsed_time(e1))
+    sr.close()
+    rc_ms = reduce_max(statistics.mean(rc_times), ws, device)
+    rc_flops = RECALC_FLOPS_SCALAR + RECALC_FLOPS_COLUMN * nproj
+    rc_tflops = rc_flops * rc.updates / (rc_ms * 1e-3) / 1e12
+    recalc = {"shifts": int(zm.size), "rows": rc.iters, "shift_rows": rc.updates, "n_converged": rc.n_converged,
+              "ms": rc_ms, "shift_rows_per_s": ws * rc.updates / (rc_ms * 1e-3),
+              "logged_solve_ms_equivalent": t_max, "speedup_vs_direct_solve": t_max / rc_ms,
+              "log_bytes": int(lr.iters * (kw.LOG_FIXED + nproj) * 16),
+              "roofline": {"kernel": "k_recalc", "bound": "alu", "achieved": rc_tflops, "peak": FP64_PEAK_TFLOPS,
+                           "unit": "TFLOP/s", "frac": rc_tflops / FP64_PEAK_TFLOPS,
+                           "flops_per_shift_row": rc_flops, "peak_kind": "nominal FP64"}}
+
     peak, peak_kind = load_peaks()
     kh = kernels[HEADLINE]
     launches = sum(s["launches"] for s in h_stats)
@@ -422,6 +457,7 @@ def run_ours(args):
             "roofline": roofline,
             "kernels": kernels,
             "legs": legs,
+            "recalc": recalc,
             "e2e": {"value": ws * work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": 1e3 * e2e_s, "api": "kw_solve_host (pinned host buffers)"},
             "gpu_launches": launches,

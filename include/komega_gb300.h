@@ -190,6 +190,63 @@ kw_status kw_get_shift_status(kw_ctx* ctx, int64_t* conv_iter_host, double* fina
  * query *n_rec; otherwise it must hold hist_max * nshift doubles. */
 kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec);
 
+/* ---------------------------------------------------------------------------
+ * Recalculation at new shifts (Sec. 3.3 (iv)).  A solve can record, per
+ * iteration, what the shift recurrences consume; the projections a_l^T x at
+ * shifts that were not in the solve then follow from Eqs. 20-22 and 25-26
+ * alone, with no product with H.
+ *
+ * Log row n (iteration n, 0-based) holds KW_LOG_FIXED + nproj kw_c128 values:
+ *   [0] z_s   the seed shift used by iteration n
+ *   [1] alpha_n, [2] c_n = alpha_n beta_{n-1}/alpha_{n-1}, [3] beta_n   (Eq. 17)
+ *   [4] (||r_{n+1}||_2^2, 0)
+ *   [5] pi^j_{n+1}, [6] pi^j_n: the factors of a seed switch to shift j after
+ *       iteration n (Sec. 2.2.4), both 1 when the seed was kept
+ *   [7 + l] (P r_{n+1})_l, l < nproj: row 0 of P is b, rows 1.. the left
+ *       vectors; taken before the switch of that iteration.
+ * w0 holds P r_0 = P b (nproj values).  A projected-mode solve logs nproj =
+ * nleft + 1 columns; a full-mode solve logs nproj = 0 (the seed scalars only).
+ * --------------------------------------------------------------------------- */
+#define KW_LOG_FIXED 7
+
+/* Record the log in the next solves of ctx (kw_solve, kw_solve_host), at most
+ * max_iters rows (0 = off, the default).  The device log takes
+ * max_iters * (KW_LOG_FIXED + nproj) * 16 bytes, allocated at the next solve.
+ * Errors: KW_ERR_ARG (max_iters < 0). */
+kw_status kw_set_krylov_log(kw_ctx* ctx, int64_t max_iters);
+
+/* The log of the last solve.  *n_iter = rows recorded (fewer than *n_run, the
+ * solve's iteration count, when max_iters cut it short), *nproj = columns of
+ * P, *thresh = the solve's absolute threshold tol*||b||_2.  log_host (NULL to
+ * query sizes) receives n_iter rows of KW_LOG_FIXED + nproj values; w0_host
+ * (may be NULL) receives nproj values.  Any output pointer may be NULL.
+ * Errors: KW_ERR_ARG (the last solve recorded no log). */
+kw_status kw_get_krylov_log(kw_ctx* ctx, int64_t* n_iter, int64_t* n_run, int64_t* nproj, double* thresh,
+                            kw_c128* log_host, kw_c128* w0_host);
+
+/* Projections at nshift new shifts z_host from a log, on the GPU (one thread
+ * per shift replays Eq. 20, Eqs. 21-22 and Eqs. 25-26 row by row, then the
+ * seed-switch rescale of pi).  A shift freezes at the first row where
+ * ||r_{n+1}|| / |pi_{n+1}| <= thresh (thresh <= 0: never).
+ *   log_host != NULL: a log of n_iter rows and nproj columns (0..KW_MAX_PROJ)
+ *       in the layout above, and w0_host its P b; both are copied to the
+ *       device.
+ *   log_host == NULL: the device log of the last solve of ctx (nproj and
+ *       w0_host are ignored; n_iter < 0 or above the recorded rows means all
+ *       recorded rows).
+ *   proj_out_host: [nshift][nproj] (column 0 = b^T x) or NULL;
+ *   conv_iter_host: [nshift], the row count at which the shift froze, -1 if
+ *       never, or NULL;  final_res_host: [nshift] last residual estimate or NULL.
+ *   info (may be NULL): iters = rows replayed, n_converged, max_res,
+ *       updates = shift-rows replayed, status.
+ * Returns KW_OK when every shift froze, else KW_NOT_CONVERGED, with every
+ * output filled (a shift that did not freeze has its last iterate).  Errors:
+ * KW_ERR_ARG (bad sizes, NULL log without a logged solve, non-finite shift),
+ * KW_ERR_BREAKDOWN (pi_{n+1} = 0 for some shift), KW_ERR_OOM, KW_ERR_CUDA. */
+kw_status kw_recalc(kw_ctx* ctx, int64_t n_iter, int64_t nproj, double thresh, const kw_c128* log_host,
+                    const kw_c128* w0_host, int64_t nshift, const kw_c128* z_host, kw_c128* proj_out_host,
+                    int64_t* conv_iter_host, double* final_res_host, kw_solve_info* info);
+
 /* Per-solve statistics for measurement.  kernel_ms[i] sums the device time
  * of kernel i (0: SpMV + r^T q, 1: three-term update + dots, 2: shift
  * scalars, 3: x/p update) over timed_iters iterations sampled by

@@ -99,6 +99,15 @@ struct kw_ctx {
   // last solve
   int64_t last_K = 0;
   int64_t last_nrec = 0;
+  // Krylov log (kw_set_krylov_log) and the last solve's record of it
+  int64_t log_max = 0;
+  DBuf klog;
+  int64_t last_log_rows = -1;   // -1: the last solve recorded no log
+  int64_t last_run = 0;
+  int last_log_np = 0;
+  double last_thresh = 0.0;
+  // kw_recalc buffers
+  DBuf rc_log, rc_w0, rc_z, rc_proj, rc_conv, rc_res, rc_flag;
 };
 
 static kw_status fail(kw_ctx* c, kw_status s, const char* fmt, ...) {
@@ -182,7 +191,9 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->sell_slen, &ctx->sell_ptr, &ctx->sell_col, &ctx->sell_val, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
-                  &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot};
+                  &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot,
+                  &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
+                  &ctx->rc_flag};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
   if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
@@ -458,6 +469,13 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->projx, Ks * w.nout * 16},
   };
   for (auto& pl : plan) KW_CUDA(pl.b->ensure(pl.bytes), "workspace allocation");
+  w.log = nullptr;
+  w.log_max = 0;
+  if (ctx->log_max > 0) {
+    KW_CUDA(ctx->klog.ensure((size_t)ctx->log_max * (KW_LOG_FIXED + w.nproj) * 16), "Krylov log allocation");
+    w.log = (double2*)ctx->klog.p;
+    w.log_max = ctx->log_max;
+  }
   w.rA = ctx->rA.p;
   w.rB = ctx->rB.p;
   w.q = ctx->q.p;
@@ -601,6 +619,10 @@ static kw_status solve_end(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* i
   const kw::State& st = *ctx->st_host;
   ctx->last_K = nshift;
   ctx->last_nrec = st.n_rec;
+  ctx->last_run = st.iter;
+  ctx->last_log_rows = w.log ? std::min<int64_t>(st.iter, w.log_max) : -1;
+  ctx->last_log_np = w.nproj;
+  ctx->last_thresh = st.thresh;
   if (proj_out_host) {
     if (w.full) {
       cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_project_x<kw::PREC_C32>(w, (double2*)ctx->projx.p)
@@ -661,6 +683,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   if (!ctx->batch_stream)
     KW_CUDA(cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking), "kw_solve_batched: stream");
   cudaStream_t bs = ctx->batch_stream;
+  ctx->last_log_rows = -1;   // the instances run on child contexts, which keep no log
   {
     cudaEvent_t e0;
     KW_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "kw_solve_batched: event");
@@ -856,6 +879,121 @@ kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* 
           "kw_bilinear read");
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_bilinear sync");
   return KW_OK;
+}
+
+kw_status kw_set_krylov_log(kw_ctx* ctx, int64_t max_iters) {
+  if (!ctx) return KW_ERR_ARG;
+  if (max_iters < 0) return fail(ctx, KW_ERR_ARG, "kw_set_krylov_log: max_iters < 0");
+  ctx->log_max = max_iters;
+  if (max_iters == 0) {
+    KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_set_krylov_log: sync");
+    ctx->klog.release();
+    ctx->last_log_rows = -1;
+  }
+  return KW_OK;
+}
+
+kw_status kw_get_krylov_log(kw_ctx* ctx, int64_t* n_iter, int64_t* n_run, int64_t* nproj, double* thresh,
+                            kw_c128* log_host, kw_c128* w0_host) {
+  if (!ctx) return KW_ERR_ARG;
+  if (ctx->last_log_rows < 0) return fail(ctx, KW_ERR_ARG, "kw_get_krylov_log: the last solve recorded no log");
+  const int64_t rows = ctx->last_log_rows;
+  const int np = ctx->last_log_np;
+  if (n_iter) *n_iter = rows;
+  if (n_run) *n_run = ctx->last_run;
+  if (nproj) *nproj = np;
+  if (thresh) *thresh = ctx->last_thresh;
+  if (log_host && rows > 0)
+    KW_CUDA(cudaMemcpy(log_host, ctx->klog.p, (size_t)rows * (KW_LOG_FIXED + np) * 16, cudaMemcpyDeviceToHost),
+            "kw_get_krylov_log: read log");
+  if (w0_host && np > 0)
+    KW_CUDA(cudaMemcpy(w0_host, ctx->w0.p, (size_t)np * 16, cudaMemcpyDeviceToHost), "kw_get_krylov_log: read w0");
+  return KW_OK;
+}
+
+kw_status kw_recalc(kw_ctx* ctx, int64_t n_iter, int64_t nproj, double thresh, const kw_c128* log_host,
+                    const kw_c128* w0_host, int64_t nshift, const kw_c128* z_host, kw_c128* proj_out_host,
+                    int64_t* conv_iter_host, double* final_res_host, kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  if (!z_host || nshift < 1 || nshift > 0x7fffffffLL)
+    return fail(ctx, KW_ERR_ARG, "kw_recalc: need z and 1 <= nshift < 2^31");
+  for (int64_t k = 0; k < nshift; ++k)
+    if (!isfinite(z_host[k].re) || !isfinite(z_host[k].im))
+      return fail(ctx, KW_ERR_ARG, "kw_recalc: shift %lld is not finite", (long long)k);
+  if (isnan(thresh)) return fail(ctx, KW_ERR_ARG, "kw_recalc: thresh is NaN");
+  int64_t rows;
+  int np;
+  const double2* dlog;
+  const double2* dw0;
+  if (log_host) {
+    if (n_iter < 0 || nproj < 0 || nproj > KW_MAX_PROJ || (nproj > 0 && !w0_host))
+      return fail(ctx, KW_ERR_ARG, "kw_recalc: need n_iter >= 0, 0 <= nproj <= %d and w0 when nproj > 0",
+                  KW_MAX_PROJ);
+    rows = n_iter;
+    np = (int)nproj;
+    const size_t lb = (size_t)rows * (KW_LOG_FIXED + np) * 16;
+    KW_CUDA(ctx->rc_log.ensure(std::max<size_t>(lb, 16)), "kw_recalc: allocation");
+    KW_CUDA(ctx->rc_w0.ensure((size_t)std::max(np, 1) * 16), "kw_recalc: allocation");
+    if (lb) KW_CUDA(cudaMemcpyAsync(ctx->rc_log.p, log_host, lb, cudaMemcpyHostToDevice, ctx->stream), "kw_recalc: upload");
+    if (np)
+      KW_CUDA(cudaMemcpyAsync(ctx->rc_w0.p, w0_host, (size_t)np * 16, cudaMemcpyHostToDevice, ctx->stream),
+              "kw_recalc: upload");
+    dlog = (const double2*)ctx->rc_log.p;
+    dw0 = (const double2*)ctx->rc_w0.p;
+  } else {
+    if (ctx->last_log_rows < 0) return fail(ctx, KW_ERR_ARG, "kw_recalc: no log given and the last solve recorded none");
+    rows = (n_iter < 0 || n_iter > ctx->last_log_rows) ? ctx->last_log_rows : n_iter;
+    np = ctx->last_log_np;
+    dlog = (const double2*)ctx->klog.p;
+    dw0 = (const double2*)ctx->w0.p;
+  }
+  const size_t K = (size_t)nshift;
+  KW_CUDA(ctx->rc_z.ensure(K * 16), "kw_recalc: allocation");
+  KW_CUDA(ctx->rc_proj.ensure(K * std::max(np, 1) * 16), "kw_recalc: allocation");
+  KW_CUDA(ctx->rc_conv.ensure(K * 8), "kw_recalc: allocation");
+  KW_CUDA(ctx->rc_res.ensure(K * 8), "kw_recalc: allocation");
+  KW_CUDA(ctx->rc_flag.ensure(4), "kw_recalc: allocation");
+  KW_CUDA(cudaMemcpyAsync(ctx->rc_z.p, z_host, K * 16, cudaMemcpyHostToDevice, ctx->stream), "kw_recalc: upload");
+  KW_CUDA(cudaMemsetAsync(ctx->rc_flag.p, 0, 4, ctx->stream), "kw_recalc: memset");
+  KW_CUDA(kw::launch_recalc((int)nshift, np, (long long)rows, dlog, dw0, (const double2*)ctx->rc_z.p,
+                            thresh > 0.0 ? thresh : -1.0, (double2*)ctx->rc_proj.p, (long long*)ctx->rc_conv.p,
+                            (double*)ctx->rc_res.p, (int*)ctx->rc_flag.p, ctx->num_sms, ctx->stream),
+          "kw_recalc: launch");
+  ctx->stats.launches += 1;
+  std::vector<long long> ci(K);
+  std::vector<double> res(K);
+  int flag = 0;
+  KW_CUDA(cudaMemcpyAsync(ci.data(), ctx->rc_conv.p, K * 8, cudaMemcpyDeviceToHost, ctx->stream), "kw_recalc: read");
+  KW_CUDA(cudaMemcpyAsync(res.data(), ctx->rc_res.p, K * 8, cudaMemcpyDeviceToHost, ctx->stream), "kw_recalc: read");
+  KW_CUDA(cudaMemcpyAsync(&flag, ctx->rc_flag.p, 4, cudaMemcpyDeviceToHost, ctx->stream), "kw_recalc: read");
+  if (proj_out_host && np > 0)
+    KW_CUDA(cudaMemcpyAsync(proj_out_host, ctx->rc_proj.p, K * np * 16, cudaMemcpyDeviceToHost, ctx->stream),
+            "kw_recalc: read");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_recalc: sync");
+  int64_t nc = 0, upd = 0;
+  double mx = 0.0;
+  for (size_t k = 0; k < K; ++k) {
+    nc += ci[k] >= 0;
+    upd += ci[k] >= 0 ? ci[k] : rows;
+    mx = std::max(mx, res[k]);
+  }
+  if (conv_iter_host) memcpy(conv_iter_host, ci.data(), K * 8);
+  if (final_res_host) memcpy(final_res_host, res.data(), K * 8);
+  const kw_status st = flag ? KW_ERR_BREAKDOWN : nc == (int64_t)K ? KW_OK : KW_NOT_CONVERGED;
+  if (info) {
+    info->iters = rows;
+    info->n_converged = nc;
+    info->max_res = mx;
+    info->n_seed_switch = 0;
+    info->updates = upd;
+    info->seed = -1;
+    info->status = st;
+  }
+  if (st == KW_ERR_BREAKDOWN) return fail(ctx, st, "kw_recalc: pi_{n+1} = 0 for some shift");
+  if (st == KW_NOT_CONVERGED)
+    fail(ctx, st, "kw_recalc: %lld of %lld shifts did not freeze within %lld rows", (long long)(nshift - nc),
+         (long long)nshift, (long long)rows);
+  return st;
 }
 
 kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every) {

@@ -98,6 +98,9 @@ struct Work {
   int* list;
   void* X;           // full mode [K][m]
   void* P;           // full mode [K][m]
+  // Krylov log for recalculation (NULL = off): rows [log_max][KW_LOG_FIXED + nproj]
+  double2* log = nullptr;
+  long long log_max = 0;
   // reduction scratch
   double* part;
   State* st;
@@ -131,6 +134,14 @@ constexpr int kBilinearTile = 8;
 cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,
                             const double2* X, const double2* Y, int nblk, double2* part, int term, int nterm,
                             double2* out, cudaStream_t s);
+
+// Recalculation at new shifts (kw_recalc): threads per block, log rows per
+// shared-memory chunk, and the launcher (flag: set to 1 on breakdown).
+constexpr int kRecalcThreads = 32;
+constexpr int kRecalcChunk = 16;
+cudaError_t launch_recalc(int K, int np, long long n_iter, const double2* log, const double2* w0, const double2* z,
+                          double thresh, double2* proj, long long* conv_iter, double* final_res, int* flag,
+                          int num_sms, cudaStream_t s);
 
 // Upper bound on resident 256-thread blocks per SM (2048 threads per SM).
 constexpr int kMaxBlocksPerSM = 8;

@@ -513,6 +513,8 @@ struct ShiftArgs {
   double* hist;
   int* list;
   double* part;      // per block: [best |pi|^2, best index, n still active]
+  double2* log;      // Krylov log rows [log_max][KW_LOG_FIXED + np], or NULL
+  long long log_max;
 };
 
 // One warp per block, LPS lanes per shift (LPS = 1 in full mode, else the
@@ -642,6 +644,11 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
     n_still += __shfl_xor_sync(KW_FULL_MASK, n_still, off);
     any_brk |= __shfl_xor_sync(KW_FULL_MASK, any_brk, off);
   }
+  // Krylov log row of this iteration (Sec. 3.3 (iv)): P r_{n+1} by the lanes,
+  // the scalars by lane 0 once the seed switch is decided.
+  double2* lrow = (a.log && iter < a.log_max) ? a.log + (size_t)iter * (KW_LOG_FIXED + a.np) : nullptr;
+  if (lrow)
+    for (int l = lane; l < a.np; l += 32) lrow[KW_LOG_FIXED + l] = a.w[l];
   if (lane != 0) return;
   const int nl = *((volatile int*)&st->n_list);
   const bool do_switch = st->seed_switch && n_still > 0 && gb < 1.0;
@@ -663,6 +670,16 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   if (any_brk) {                                        // pi_{n+1} = 0 (Eq. 20)
     set_fail(st, KW_ERR_BREAKDOWN);
     return;
+  }
+  if (lrow) {
+    const double2 one = make_double2(1.0, 0.0);
+    lrow[0] = zs;
+    lrow[1] = alpha;
+    lrow[2] = c;
+    lrow[3] = beta;
+    lrow[4] = make_double2(nu, 0.0);
+    lrow[5] = do_switch ? __ldcg(a.pi1 + gk) : one;   // pi^j_{n+1}, written by the shift's owner lane
+    lrow[6] = do_switch ? pj0 : one;
   }
   double2 rho1 = rho1_in;
   double2 boa = cmul(rho1_in, st->inv_rho_alpha);       // beta_n / alpha_n
@@ -693,6 +710,93 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   } else if (iter + 1 >= maxiter) {
     st->status = KW_NOT_CONVERGED;
     st->done = 1;
+  }
+}
+
+// ================================================================ recalculation at new shifts
+// Sec. 3.3 (iv): the logged iterations are replayed for each new shift with
+// the same arithmetic as K3 (Eq. 20, Eqs. 21-22, Eqs. 25-26, the pi rescale of
+// a seed switch).  LPS lanes per shift: they compute the shift's scalars
+// redundantly (one warp instruction for all of them) and each updates the
+// projection columns l = sub, sub + LPS, ... (at most NPL).  The host picks
+// LPS so that there are enough warps to spread over the SMs.  Log rows are
+// staged through shared memory in chunks of kRecalcChunk rows, loaded by the
+// whole block at once.
+template <int LPS, int NPL>
+__global__ void __launch_bounds__(kRecalcThreads)
+    k_recalc(int K, int np, long long n_iter, const double2* __restrict__ log, const double2* __restrict__ w0,
+             const double2* __restrict__ z, double thresh, double2* __restrict__ proj,
+             long long* __restrict__ conv_iter, double* __restrict__ final_res, int* __restrict__ flag) {
+  extern __shared__ double2 srows[];   // [kRecalcChunk][KW_LOG_FIXED + np]
+  constexpr int SPB = kRecalcThreads / LPS;   // shifts per block
+  const int R = KW_LOG_FIXED + np;
+  const int sub = threadIdx.x % LPS;
+  const int k = blockIdx.x * SPB + threadIdx.x / LPS;
+  double2 y[NPL], u[NPL];
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int l = sub + i * LPS;
+    y[i] = make_double2(0.0, 0.0);
+    u[i] = l < np ? w0[l] : make_double2(0.0, 0.0);   // u_0 = P b
+  }
+  double2 p1 = make_double2(1.0, 0.0), p0 = p1;
+  const double2 zk = k < K ? z[k] : make_double2(0.0, 0.0);
+  bool act = k < K;
+  long long ci = -1;
+  double fr = INFINITY;
+  for (long long n0 = 0; n0 < n_iter; n0 += kRecalcChunk) {
+    if (!__syncthreads_or(act)) break;
+    const int rows = (int)min((long long)kRecalcChunk, n_iter - n0);
+    for (int i = threadIdx.x; i < rows * R; i += blockDim.x) srows[i] = log[(size_t)n0 * R + i];
+    __syncthreads();
+    for (int j = 0; act && j < rows; ++j) {
+      const double2* row = srows + j * R;
+      const double2 zs = row[0], alpha = row[1], c = row[2], beta = row[3];
+      const double nu = row[4].x;
+      const double2 f = cadd(make_double2(1.0 + c.x, c.y), cmul(alpha, csub(zk, zs)));
+      const double2 pn = csub(cmul(f, p1), cmul(c, p0));               // Eq. 20
+      if (pn.x == 0.0 && pn.y == 0.0) {
+        if (sub == 0) atomicOr(flag, 1);
+        act = false;
+        break;
+      }
+      const double2 ipn = crecip(pn);
+      const double2 ratio = cmul(p1, ipn);
+      const double2 ak = cmul(ratio, alpha);                            // Eq. 21
+      const double2 bk = cmul(cmul(ratio, ratio), beta);                // Eq. 22
+#pragma unroll
+      for (int i = 0; i < NPL; ++i) {
+        const int l = sub + i * LPS;
+        if (l < np) {                                                   // Eqs. 25-26
+          y[i] = cadd(y[i], cmul(ak, u[i]));
+          u[i] = cadd(cmul(row[KW_LOG_FIXED + l], ipn), cmul(bk, u[i]));
+        }
+      }
+      fr = sqrt(nu * (ipn.x * ipn.x + ipn.y * ipn.y));
+      p0 = p1;
+      p1 = pn;
+      if (fr <= thresh) {
+        act = false;
+        ci = n0 + j + 1;
+        break;
+      }
+      const double2 s1 = row[5], s0 = row[6];
+      if (s1.x != 1.0 || s1.y != 0.0 || s0.x != 1.0 || s0.y != 0.0) {  // seed switch (Sec. 2.2.4)
+        p1 = cmul(p1, crecip(s1));
+        p0 = cmul(p0, crecip(s0));
+      }
+    }
+    __syncthreads();
+  }
+  if (k >= K) return;
+#pragma unroll
+  for (int i = 0; i < NPL; ++i) {
+    const int l = sub + i * LPS;
+    if (l < np) proj[(size_t)k * np + l] = y[i];
+  }
+  if (sub == 0) {
+    conv_iter[k] = ci;
+    final_res[k] = fr;
   }
 }
 
@@ -1065,6 +1169,8 @@ cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* laun
   a.hist = w.hist;
   a.list = w.list;
   a.part = w.part;
+  a.log = w.log;
+  a.log_max = w.log_max;
   const int lps = w.full ? 1 : (w.nproj <= 1 ? 1 : w.nproj <= 2 ? 2 : w.nproj <= 4 ? 4 : w.nproj <= 8 ? 8
                                                                      : w.nproj <= 16 ? 16 : 32);
   const int spw = 32 / lps;

@@ -78,4 +78,63 @@ cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col,
   k_bilinear_reduce<kBilinearTile><<<(K + 127) / 128, 128, 0, s>>>(K, nblk, term, nterm, part, out);
   return cudaGetLastError();
 }
+
+template <int LPS, int NPL>
+static cudaError_t recalc_launch(int K, int np, long long n_iter, const double2* log, const double2* w0,
+                                 const double2* z, double thresh, double2* proj, long long* conv_iter,
+                                 double* final_res, int* flag, cudaStream_t s) {
+  const size_t smem = (size_t)kRecalcChunk * (KW_LOG_FIXED + np) * sizeof(double2);
+  constexpr int spb = kRecalcThreads / LPS;
+  const int grid = (K + spb - 1) / spb;
+  k_recalc<LPS, NPL><<<grid, kRecalcThreads, smem, s>>>(K, np, n_iter, log, w0, z, thresh, proj, conv_iter,
+                                                        final_res, flag);
+  return cudaGetLastError();
+}
+
+// Columns per lane, rounded up to a power of two, for LPS lanes per shift.
+template <int LPS>
+static cudaError_t recalc_npl(int K, int np, long long n_iter, const double2* log, const double2* w0,
+                              const double2* z, double thresh, double2* proj, long long* conv_iter, double* final_res,
+                              int* flag, cudaStream_t s) {
+  const int per_lane = (np + LPS - 1) / LPS;
+#define KW_RC(NPL) recalc_launch<LPS, NPL>(K, np, n_iter, log, w0, z, thresh, proj, conv_iter, final_res, flag, s)
+  if (per_lane <= 1) return KW_RC(1);
+  if constexpr (LPS <= 16) {
+    if (per_lane <= 2) return KW_RC(2);
+  }
+  if constexpr (LPS <= 8) {
+    if (per_lane <= 4) return KW_RC(4);
+  }
+  if constexpr (LPS <= 4) {
+    if (per_lane <= 8) return KW_RC(8);
+  }
+  if constexpr (LPS <= 2) {
+    if (per_lane <= 16) return KW_RC(16);
+  }
+  if constexpr (LPS == 1) return KW_RC(32);
+#undef KW_RC
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_recalc(int K, int np, long long n_iter, const double2* log, const double2* w0, const double2* z,
+                          double thresh, double2* proj, long long* conv_iter, double* final_res, int* flag,
+                          int num_sms, cudaStream_t s) {
+  if (K < 1 || np < 0 || np > KW_MAX_PROJ || n_iter < 0 || !z || !proj || !conv_iter || !final_res || !flag ||
+      (n_iter > 0 && !log) || (np > 0 && !w0))
+    return cudaErrorInvalidValue;
+  // Lanes per shift: double while there are fewer than two warps per SM and
+  // a shift still has more than one column per lane.
+  int lps = 1;
+  while (lps < 32 && lps < np && (long long)K * lps < 2LL * 32 * num_sms) lps *= 2;
+#define KW_RL(L) recalc_npl<L>(K, np, n_iter, log, w0, z, thresh, proj, conv_iter, final_res, flag, s)
+  switch (lps) {
+    case 1: return KW_RL(1);
+    case 2: return KW_RL(2);
+    case 4: return KW_RL(4);
+    case 8: return KW_RL(8);
+    case 16: return KW_RL(16);
+    default: return KW_RL(32);
+  }
+#undef KW_RL
+}
 }  // namespace kw

@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH):
         "kw_solve_batched": (C.c_int, [P, I64, C.POINTER(kw_instance), C.POINTER(kw_solve_info)]),
         "kw_spmv_dot_noalloc": (C.c_int, [I64, I64, P, P, P, kw_c128, P, P, C.POINTER(kw_c128), P]),
         "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "kw_set_krylov_log": (C.c_int, [P, I64]),
+        "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
+        "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -132,6 +135,35 @@ class SolveResult:
     n_seed_switch: int
     updates: int
     seed: int
+    status: str
+
+
+# Columns of a Krylov log row before P r_{n+1}: z_s, alpha_n, c_n, beta_n,
+# ||r_{n+1}||^2, pi^j_{n+1}, pi^j_n (see kw_get_krylov_log).
+LOG_FIXED = 7
+
+
+@dataclass
+class KrylovLog:
+    """A solve's per-iteration record for recalculation at new shifts."""
+    rows: np.ndarray          # [n_iter, LOG_FIXED + nproj] complex128
+    w0: np.ndarray            # [nproj] complex128: P b
+    thresh: float             # the solve's tol * ||b||
+    n_run: int                # iterations of the solve (> n_iter when the log was cut short)
+
+    @property
+    def nproj(self) -> int:
+        return self.rows.shape[1] - LOG_FIXED
+
+
+@dataclass
+class RecalcResult:
+    proj: np.ndarray          # [K, nproj] complex128; column 0 = b^T x
+    conv_iter: np.ndarray     # [K] rows replayed when the shift froze, -1 if never
+    final_res: np.ndarray     # [K] last residual estimate
+    iters: int                # rows replayed
+    n_converged: int
+    updates: int              # shift-rows replayed
     status: str
 
 
@@ -274,6 +306,59 @@ class Solver:
             if st != KW_OK:
                 raise self._err(st, "kw_get_residual_history")
         return h
+
+    def set_krylov_log(self, max_iters: int):
+        """Record the Krylov log (at most max_iters rows) in the next solves; 0 = off."""
+        st = self._lib.kw_set_krylov_log(self._ctx, int(max_iters))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_krylov_log")
+
+    def krylov_log(self) -> KrylovLog:
+        """The Krylov log of the last solve, copied to the host."""
+        n, run, np_, thr = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+        st = self._lib.kw_get_krylov_log(self._ctx, C.byref(n), C.byref(run), C.byref(np_), C.byref(thr), None, None)
+        if st != KW_OK:
+            raise self._err(st, "kw_get_krylov_log")
+        rows = np.zeros((n.value, LOG_FIXED + np_.value), dtype=np.complex128)
+        w0 = np.zeros(np_.value, dtype=np.complex128)
+        st = self._lib.kw_get_krylov_log(self._ctx, C.byref(n), C.byref(run), C.byref(np_), C.byref(thr),
+                                         rows.ctypes.data_as(C.c_void_p), w0.ctypes.data_as(C.c_void_p))
+        if st != KW_OK:
+            raise self._err(st, "kw_get_krylov_log")
+        return KrylovLog(rows, w0, thr.value, run.value)
+
+    def recalc(self, z, log: KrylovLog | None = None, thresh: float | None = None, n_iter: int = -1,
+               check: bool = True) -> RecalcResult:
+        """kw_recalc: projections at shifts z from ``log`` (host) or, when log is
+        None, from the device log of the last solve.  thresh defaults to the
+        logged solve's tol*||b||."""
+        zz, zp = _z_array(z)
+        K = zz.size
+        if log is not None:
+            rows = np.ascontiguousarray(log.rows, dtype=np.complex128)
+            w0 = np.ascontiguousarray(log.w0, dtype=np.complex128)
+            n, npj = rows.shape[0] if n_iter < 0 else min(n_iter, rows.shape[0]), rows.shape[1] - LOG_FIXED
+            thr = log.thresh if thresh is None else thresh
+            lp, wp = rows.ctypes.data_as(C.c_void_p), w0.ctypes.data_as(C.c_void_p)
+        else:
+            nn, run, np_, t0 = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+            st = self._lib.kw_get_krylov_log(self._ctx, C.byref(nn), C.byref(run), C.byref(np_), C.byref(t0),
+                                             None, None)
+            if st != KW_OK:
+                raise self._err(st, "kw_get_krylov_log")
+            n, npj = n_iter, np_.value
+            thr = t0.value if thresh is None else thresh
+            lp, wp = None, None
+        proj = np.zeros((K, max(npj, 1)), dtype=np.complex128)
+        ci = np.zeros(K, dtype=np.int64)
+        fr = np.zeros(K, dtype=np.float64)
+        info = kw_solve_info()
+        st = self._lib.kw_recalc(self._ctx, n, npj, thr, lp, wp, K, zp, proj.ctypes.data_as(C.c_void_p),
+                                 ci.ctypes.data_as(C.c_void_p), fr.ctypes.data_as(C.c_void_p), C.byref(info))
+        if check and st not in (KW_OK, KW_NOT_CONVERGED):
+            raise self._err(st, "kw_recalc")
+        return RecalcResult(proj[:, :npj], ci, fr, info.iters, info.n_converged, info.updates,
+                            STATUS.get(st, str(st)))
 
     def set_kernel_timing(self, every: int):
         st = self._lib.kw_set_kernel_timing(self._ctx, every)

@@ -68,6 +68,41 @@ def test_fullsize_projected_vs_sampled_full_solutions(problem, prec):
     np.testing.assert_allclose(full.proj, ref, rtol=1e-12, atol=1e-14)
 
 
+def test_fullsize_recalc_at_midpoints(problem):
+    """Sec. 3.3 (iv) at the benchmark size: the 1024-shift DF64 run records its
+    Krylov log; the projections at the 1024 midpoints w + dw/2 + 0.01i are
+    recomputed from it, and 4 sampled midpoints are re-solved in full mode and
+    checked on the CPU (true residual, then a_l^T x against the recalculated
+    projections within 2 max(tol, res_k) ||a_l|| / Im z_k)."""
+    p = problem
+    bd = torch.as_tensor(p.b, device="cuda")
+    ld = torch.as_tensor(p.left, device="cuda")
+    s = kw.Solver("df64", tol=p.tol, maxiter=200000)
+    s.set_csr(p.H.rowptr, p.H.col, p.H.val)
+    s.set_krylov_log(200000)
+    r = s.solve(bd, p.z, left=ld)
+    assert r.status == "KW_OK"
+    lg = s.krylov_log()
+    assert lg.rows.shape == (r.iters, kw.LOG_FIXED + 1 + p.left.shape[0]) and lg.n_run == r.iters
+    zm = p.z + (p.z[1] - p.z[0]).real / 2
+    rc = s.recalc(zm)
+    print(f"recalc: {rc.n_converged}/{zm.size} midpoints froze within {rc.iters} rows, "
+          f"max res {rc.final_res.max():.2e}")
+    assert rc.iters == r.iters and rc.n_converged >= 0.95 * zm.size
+    zs = zm[SAMPLE]
+    full = s.solve(bd, zs, left=ld, full=True)
+    assert full.status == "KW_OK"
+    x = full.x.cpu().numpy()
+    tr = oc.true_residuals(p.H.to_scipy(), p.b, zs, x)
+    assert np.all(tr <= 10 * p.tol)
+    P = np.vstack([p.b, p.left])
+    ref = x @ P.T
+    res = np.maximum(rc.final_res[SAMPLE], p.tol)
+    bound = 2 * res[:, None] * np.linalg.norm(P, axis=1)[None, :] / np.abs(zs.imag)[:, None]
+    print(f"recalc: max |recalc - a^T x| {np.abs(rc.proj[SAMPLE] - ref).max():.3e}")
+    assert np.all(np.abs(rc.proj[SAMPLE] - ref) <= bound)
+
+
 def test_fullsize_anderson_contour_sampled():
     """Anderson L=160 (M=4,096,000, W=4), 2048 real-axis shifts (delta=0.005) and
     2048 contour points, 16 Gaussian left vectors, tol 1e-8, projected mode in the
