@@ -123,6 +123,35 @@ kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
 kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev,
                      const int32_t* col_dev, const double* val_dev);
 
+/* Element types of the vectors handed to a matrix-vector callback. */
+#define KW_ELEM_C128 0   /* kw_c128 */
+#define KW_ELEM_C64 1    /* complex FP32: {float re, im} */
+
+/* Matrix-vector callback: enqueue on cuda_stream (a cudaStream_t) the work
+ * that writes q = H r into all m entries of q_dev, reading r_dev, both device
+ * vectors of element type elem; return 0, or nonzero to stop the solve with
+ * KW_ERR_CALLBACK.  The pointers are valid only for the work enqueued by this
+ * call. */
+typedef int (*kw_matvec_fn)(void* user, const void* r_dev, void* q_dev, int64_t m, int elem, void* cuda_stream);
+
+/* Set the operator H (M x M) as a caller-supplied product instead of a matrix
+ * (Sec. 3.1 (i): the library leaves "q = H r" to the application, which may
+ * generate the matrix elements on the fly, as HPhi does).  H must be symmetric
+ * (H^T = H; real, or complex symmetric, since COCG only needs A = zI - H to be
+ * complex symmetric).  Until the next kw_set_csr, kw_solve and kw_spmv_dot
+ * call fn once per iteration from the calling thread while they enqueue work
+ * (the host runs up to 32 iterations ahead of the GPU, so fn may be called for
+ * iterations after the solve has converged; their products are ignored).
+ * elem is KW_ELEM_C64 in the KW_C32V_F64S form and KW_ELEM_C128 otherwise (the
+ * KW_DF64 form converts its FP32-pair vectors to and from kw_c128 around the
+ * call).  r_dev holds the seed residual, possibly still in the previous seed's
+ * normalisation (the library applies the seed-switch factor to q itself, which
+ * is exact by linearity).  kw_solve_batched and kw_bilinear take their own
+ * matrices and ignore the callback; kw_solve_host sets its matrix as the
+ * operator (as kw_set_csr does), which ends the callback.  Errors: KW_ERR_ARG
+ * (m < 1, m >= 2^31, fn NULL). */
+kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user);
+
 /* Solve (z_k I - H) x_k = b for all nshift shifts (Eq. 4) by shifted COCG.
  *   b_dev       float64 [m], real right-hand side (||b|| > 0).
  *   z_host      kw_c128 [nshift], finite shifts; the initial seed is z_0 (Eq. 6).

@@ -64,6 +64,10 @@ struct kw_ctx {
   const int64_t* rowptr = nullptr;
   const int32_t* col = nullptr;
   const double* val = nullptr;
+  // operator as a caller's callback (kw_set_matvec); the FP32-pair form hands it kw_c128 copies
+  kw_matvec_fn mv_fn = nullptr;
+  void* mv_user = nullptr;
+  DBuf mv_r, mv_q;
   DBuf val32;
   DBuf valpair;               // FP32-pair copy of the values (KW_DF64, values not exact in FP32)
   DBuf inexact;
@@ -192,7 +196,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot,
-                  &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
+                  &ctx->mv_r, &ctx->mv_q, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
@@ -223,6 +227,8 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   if (m < 1 || m > 0x7fffffffLL || nnz < 0 || nnz > 0x7fffffffLL || !rowptr_dev ||
       (nnz > 0 && (!col_dev || !val_dev)))
     return fail(ctx, KW_ERR_ARG, "kw_set_csr: need 1 <= m < 2^31, 0 <= nnz < 2^31 and non-NULL arrays");
+  ctx->mv_fn = nullptr;
+  ctx->mv_user = nullptr;
   ctx->m = m;
   ctx->nnz = nnz;
   ctx->rowptr = rowptr_dev;
@@ -249,6 +255,23 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   return KW_OK;
 }
 
+kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user) {
+  if (!ctx) return KW_ERR_ARG;
+  if (m < 1 || m > 0x7fffffffLL || !fn) return fail(ctx, KW_ERR_ARG, "kw_set_matvec: need 1 <= m < 2^31 and fn");
+  ctx->mv_fn = fn;
+  ctx->mv_user = user;
+  ctx->m = m;
+  ctx->nnz = 0;
+  ctx->rowptr = nullptr;
+  ctx->col = nullptr;
+  ctx->val = nullptr;
+  ctx->val32_exact = false;
+  ctx->spmv_lanes = 1;   // nothing to tune
+  ctx->spmv_val_f32 = 0;
+  ctx->sell_built = false;
+  return KW_OK;
+}
+
 }  // extern "C"
 
 static size_t part_doubles(const kw_ctx* ctx, int64_t K) {
@@ -270,6 +293,10 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.val = w.val_f32 ? (const void*)ctx->val32.p
                     : (p == KW_DF64 ? (const void*)ctx->valpair.p : (const void*)ctx->val);
   w.spmv_lanes = lanes;
+  w.mv_fn = ctx->mv_fn;
+  w.mv_user = ctx->mv_user;
+  w.mv_r = ctx->mv_r.p;
+  w.mv_q = ctx->mv_q.p;
   if (lanes == kw::KW_SPMV_SELL) {
     if (p == KW_F64) w.val_f32 = 0;       // the SELL copy keeps FP64 values in the FP64 form
     w.sell_perm = (const int*)ctx->sell_perm.p;
@@ -332,8 +359,16 @@ static kw_status build_sell(kw_ctx* ctx) {
   return KW_OK;
 }
 
+// kw_c128 staging vectors of the callback operator in the FP32-pair form.
+static kw_status ensure_mv_buffers(kw_ctx* ctx) {
+  if (!ctx->mv_fn || ctx->opt.prec != KW_DF64) return KW_OK;
+  KW_CUDA(ctx->mv_r.ensure((size_t)ctx->m * 16), "callback staging allocation");
+  KW_CUDA(ctx->mv_q.ensure((size_t)ctx->m * 16), "callback staging allocation");
+  return KW_OK;
+}
+
 static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 zs, double2* t) {
-  if (!w.st || !w.part || !t || !w.rowptr) return cudaErrorInvalidValue;   // workspace must exist
+  if (!w.st || !w.part || !t || (!w.rowptr && !w.mv_fn)) return cudaErrorInvalidValue;   // workspace must exist
   const float4 zp = host_pair(zs.x, zs.y);
   switch (w.prec) {
     case kw::PREC_C32: return kw::launch_spmv_dot<kw::PREC_C32>(w, r, q, zs, zp, t);
@@ -349,6 +384,11 @@ static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 
 static const int64_t kTuneMinNnz = 1 << 20;
 
 static kw_status tune_spmv(kw_ctx* ctx) {
+  if (ctx->mv_fn) {   // the caller's callback is the operator: nothing to tune
+    ctx->spmv_lanes = 1;
+    ctx->spmv_val_f32 = 0;
+    return KW_OK;
+  }
   if (ctx->spmv_lanes > 0) return KW_OK;
   const kw_precision p = ctx->opt.prec;
   if (ctx->nnz < kTuneMinNnz || ctx->force_lanes == kw::KW_SPMV_SELL) {
@@ -549,7 +589,7 @@ static cudaError_t iteration_launch(kw::Work& w, int parity, cudaEvent_t* ev, in
 // initialisation (no synchronisation).  The descriptor is kept in ctx->work.
 static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
                              const double* left_dev, void* x_out_dev) {
-  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_solve: kw_set_csr has not been called");
+  if (!ctx->rowptr && !ctx->mv_fn) return fail(ctx, KW_ERR_ARG, "kw_solve: no operator (kw_set_csr or kw_set_matvec)");
   if (!b_dev || !z_host || nshift < 1 || nshift > 0x7fffffffLL)
     return fail(ctx, KW_ERR_ARG, "kw_solve: need b, z and 1 <= nshift < 2^31");
   if (nleft < 0 || nleft >= KW_MAX_PROJ || (nleft > 0 && !left_dev))
@@ -559,6 +599,8 @@ static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, c
       return fail(ctx, KW_ERR_ARG, "kw_solve: shift %lld is not finite", (long long)k);
   memset(&ctx->stats, 0, sizeof(ctx->stats));
   kw_status s = tune_spmv(ctx);
+  if (s != KW_OK) return s;
+  s = ensure_mv_buffers(ctx);
   if (s != KW_OK) return s;
   s = prepare(ctx, ctx->work, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
   if (s != KW_OK) return s;
@@ -587,7 +629,14 @@ static kw_status run_loop(kw_ctx* ctx) {
         ev = ctx->kev[slot];
         sampled_at[slot] = launched;
       }
-      KW_CUDA(iteration_launch(w, (int)(launched & 1), ev, &ctx->stats.launches), "iteration launch");
+      cudaError_t le = iteration_launch(w, (int)(launched & 1), ev, &ctx->stats.launches);
+      if (le != cudaSuccess) {
+        if (w.mv_failed) {
+          cudaStreamSynchronize(ctx->stream);   // let the iterations already enqueued finish
+          return fail(ctx, KW_ERR_CALLBACK, "kw_solve: the matrix-vector callback returned nonzero");
+        }
+        return cuda_fail(ctx, le, "iteration launch");
+      }
       ++launched;
     }
     KW_CUDA(cudaMemcpyAsync(ctx->flags_host + slot, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
@@ -1036,9 +1085,11 @@ kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out) {
 
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host) {
   if (!ctx) return KW_ERR_ARG;
-  if (!ctx->rowptr) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: kw_set_csr has not been called");
+  if (!ctx->rowptr && !ctx->mv_fn) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: no operator (kw_set_csr or kw_set_matvec)");
   if (!r_dev || !q_dev || !t_host) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: NULL pointer");
   kw_status ts = tune_spmv(ctx);
+  if (ts != KW_OK) return ts;
+  ts = ensure_mv_buffers(ctx);
   if (ts != KW_OK) return ts;
   KW_CUDA(ctx->part.ensure(part_doubles(ctx, 1) * 8), "alloc partials");
   KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "alloc state");
@@ -1048,6 +1099,10 @@ kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, k
   KW_CUDA(cudaMemsetAsync(&w.st->cnt_spmv, 0, sizeof(unsigned int), ctx->stream), "reset counter");
   const double2 z2 = make_double2(zs.re, zs.im);
   cudaError_t e = spmv_dot_launch(w, r_dev, q_dev, z2, (double2*)ctx->tdot.p);
+  if (e != cudaSuccess && w.mv_failed) {
+    cudaStreamSynchronize(ctx->stream);
+    return fail(ctx, KW_ERR_CALLBACK, "kw_spmv_dot: the matrix-vector callback returned nonzero");
+  }
   KW_CUDA(e, "kw_spmv_dot launch");
   KW_CUDA(cudaMemcpyAsync(t_host, ctx->tdot.p, 16, cudaMemcpyDeviceToHost, ctx->stream), "read dot");
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_spmv_dot sync");

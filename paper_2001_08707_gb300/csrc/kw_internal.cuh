@@ -98,6 +98,12 @@ struct Work {
   int* list;
   void* X;           // full mode [K][m]
   void* P;           // full mode [K][m]
+  // operator given as a callback (kw_set_matvec) instead of the CSR arrays
+  kw_matvec_fn mv_fn = nullptr;
+  void* mv_user = nullptr;
+  void* mv_r = nullptr;   // FP32-pair form: kw_c128 copy of r handed to the callback
+  void* mv_q = nullptr;   // FP32-pair form: the callback's H r (kw_c128)
+  int mv_failed = 0;      // set when the callback returned nonzero
   // Krylov log for recalculation (NULL = off): rows [log_max][KW_LOG_FIXED + nproj]
   double2* log = nullptr;
   long long log_max = 0;

@@ -337,6 +337,75 @@ k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restri
   spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
 }
 
+// K1 for an operator given as a callback (kw_set_matvec).  The caller's work
+// has left H r in hq (kw_c128 in the FP64 and FP32-pair forms, complex FP32 in
+// the FP32 form; in place in q except in the pair form); this pass forms
+// q = z_s r - H r with the lazy seed-switch scale and r^T q exactly as
+// k_spmv_dot does, then the same K1 tail.
+template <int P> struct MvT;
+template <> struct MvT<PREC_F64> { typedef double2 H; };
+template <> struct MvT<PREC_C32> { typedef float2 H; };
+template <> struct MvT<PREC_DF> { typedef double2 H; };
+__device__ __forceinline__ double2 mv_in(double2 h, double2*) { return h; }
+__device__ __forceinline__ float2 mv_in(float2 h, float2*) { return h; }
+__device__ __forceinline__ dfc mv_in(double2 h, dfc*) { return {df_from_double(h.x), df_from_double(h.y)}; }
+
+template <int P>
+__global__ void __launch_bounds__(256)
+k_matvec_finish(int m, const typename PT<P>::V* r, const typename MvT<P>::H* hq, typename PT<P>::V* q, State* st,
+                double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  V zsv, scv = vzero<V>();
+  bool scaled = false;
+  if (mode.solver) {
+    if (st->done) return;
+    zsv = vscalar<V>(st->zs, st->p_zs);
+    if (st->vec_scale_pending) {
+      scv = vscalar<V>(st->scale_rn, st->p_s1);
+      scaled = true;
+    }
+  } else {
+    zsv = vscalar<V>(mode.zs, mode.zs_pair);
+  }
+  const int lane = threadIdx.x & 31;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  const int stride = gridDim.x * blockDim.x;
+  // the trip count is uniform across a warp (rows past m do no work)
+  for (int base = blockIdx.x * blockDim.x; base < m; base += stride) {
+    const int row = base + (int)threadIdx.x;
+    if (row < m) {
+      V ri = r[row];
+      V qi = csub(cmul(zsv, ri), mv_in(hq[row], (V*)nullptr));   // z_s r - H r
+      if (scaled) {
+        qi = cmul(scv, qi);
+        ri = cmul(scv, ri);
+      }
+      q[row] = qi;
+      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
+    }
+    if (++in_chunk == PT<P>::CHUNK) {
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
+// FP32-pair form: r as kw_c128 for the callback (skipped once the solve stopped).
+static __global__ void k_pairs_to_c128(int m, const dfc* __restrict__ r, double2* __restrict__ out,
+                                       const State* st, int solver) {
+  if (solver && st->done) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const dfc v = r[i];
+    out[i] = make_double2((double)v.re.hi + (double)v.re.lo, (double)v.im.hi + (double)v.im.lo);
+  }
+}
+
 // ---------------------------------------------------------------- SELL-32 construction
 // One block of 1024 threads per window of 1024 rows: bitonic sort of
 // (descending length, row) keys; writes the sorted order and lengths.
@@ -1093,8 +1162,36 @@ static cudaError_t spmv_dispatch_v(Work& w, const void* r, void* q, SpmvMode mod
   }
 }
 
+// K1 through the caller's matrix-vector callback.
+template <int P>
+static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename MvT<P>::H H;
+  const void* rin = r;
+  void* hq = q;
+  if constexpr (P == PREC_DF) {
+    if (!w.mv_r || !w.mv_q) return cudaErrorInvalidValue;
+    k_pairs_to_c128<<<4 * w.num_sms, 256, 0, w.stream>>>((int)w.m, (const dfc*)r, (double2*)w.mv_r, w.st,
+                                                        mode.solver);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    rin = w.mv_r;
+    hq = w.mv_q;
+  }
+  if (w.mv_fn(w.mv_user, rin, hq, w.m, P == PREC_C32 ? KW_ELEM_C64 : KW_ELEM_C128, (void*)w.stream) != 0) {
+    w.mv_failed = 1;
+    return cudaErrorUnknown;
+  }
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_matvec_finish<P>, 256, w.num_sms);
+  const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
+  k_matvec_finish<P><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)r, (const H*)hq, (V*)q, w.st, w.part, mode);
+  return cudaGetLastError();
+}
+
 template <int P>
 static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
+  if (w.mv_fn) return matvec_dispatch<P>(w, r, q, mode);
   if constexpr (P == PREC_F64) {
     if (w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);
     return spmv_dispatch_v<P, double>(w, r, q, mode);
@@ -1185,7 +1282,7 @@ cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* laun
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   KW_MARK(3);
-  *launches += 3;
+  *launches += (w.mv_fn && P == PREC_DF) ? 4 : 3;
   if (w.full) {
     static int nblk_xp = 0;
     if (nblk_xp == 0) nblk_xp = resident_blocks(k_update_xp<P, 8>, 256, w.num_sms);

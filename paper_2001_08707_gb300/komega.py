@@ -23,7 +23,7 @@ PRECISIONS = {"f64": KW_F64, "c32v_f64s": KW_C32V_F64S, "c32": KW_C32V_F64S, "df
 
 STATUS = {0: "KW_OK", 1: "KW_ERR_ARG", 2: "KW_ERR_CUDA", 3: "KW_ERR_OOM", 4: "KW_ERR_BREAKDOWN",
           5: "KW_ERR_NONFINITE", 6: "KW_ERR_CALLBACK", 7: "KW_ERR_TIMEOUT", 8: "KW_NOT_CONVERGED"}
-KW_OK, KW_ERR_ARG, KW_NOT_CONVERGED = 0, 1, 8
+KW_OK, KW_ERR_ARG, KW_ERR_CALLBACK, KW_NOT_CONVERGED = 0, 1, 6, 8
 MAX_PROJ = 32
 
 
@@ -59,6 +59,19 @@ class kw_stats(C.Structure):
 _lib = None
 
 
+# kw_matvec_fn: (user, r_dev, q_dev, m, elem, cuda_stream) -> int
+MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p)
+KW_ELEM_C128, KW_ELEM_C64 = 0, 1
+
+
+class _DeviceVector:
+    """A borrowed device vector as (m, 2) real numbers, for torch.as_tensor."""
+
+    def __init__(self, ptr: int, m: int, real_typestr: str):
+        self.__cuda_array_interface__ = {"shape": (m, 2), "typestr": real_typestr, "data": (ptr, False),
+                                         "strides": None, "version": 2}
+
+
 def load_library(path: str = LIB_PATH):
     """Load the shared library (raises if it has not been built)."""
     global _lib
@@ -89,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "kw_solve_batched": (C.c_int, [P, I64, C.POINTER(kw_instance), C.POINTER(kw_solve_info)]),
         "kw_spmv_dot_noalloc": (C.c_int, [I64, I64, P, P, P, kw_c128, P, P, C.POINTER(kw_c128), P]),
         "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "kw_set_matvec": (C.c_int, [P, I64, MATVEC_FN, P]),
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
         "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
@@ -258,7 +272,7 @@ class Solver:
         st = self._lib.kw_solve(self._ctx, C.c_void_p(bd.data_ptr()), K, zp, nleft, lp, xp,
                                 proj.ctypes.data_as(C.c_void_p), C.byref(info))
         if check and st not in (KW_OK, KW_NOT_CONVERGED):
-            raise self._err(st, "kw_solve")
+            raise self._err(st, "kw_solve") from getattr(self, "_mv_error", None)
         return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
                            info.seed, STATUS.get(st, str(st)))
 
@@ -306,6 +320,36 @@ class Solver:
             if st != KW_OK:
                 raise self._err(st, "kw_get_residual_history")
         return h
+
+    def set_matvec(self, fn, m: int):
+        """kw_set_matvec: use ``fn(r, q)`` as the operator, where r and q are
+        borrowed complex CUDA tensors of length m (complex64 in the FP32 form,
+        complex128 otherwise) and fn must write H r into q with torch work on
+        the current stream (the solver's).  kw_set_csr ends it."""
+        torch = self._torch
+        self._mv_error = None
+
+        def trampoline(user, r, q, mm, elem, stream):
+            try:
+                ts = "<f8" if elem == KW_ELEM_C128 else "<f4"
+                rt = torch.view_as_complex(torch.as_tensor(_DeviceVector(r, mm, ts), device="cuda"))
+                qt = torch.view_as_complex(torch.as_tensor(_DeviceVector(q, mm, ts), device="cuda"))
+                # ctypes hands a NULL stream (the legacy default stream) over as None
+                cs = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                with torch.cuda.stream(cs):
+                    fn(rt, qt)
+                return 0
+            except BaseException as exc:          # reported as KW_ERR_CALLBACK
+                self._mv_error = exc
+                return 1
+
+        cb = MATVEC_FN(trampoline)
+        st = self._lib.kw_set_matvec(self._ctx, int(m), cb, None)
+        if st != KW_OK:
+            raise self._err(st, "kw_set_matvec")
+        self._mv_cb = cb                          # the library keeps the pointer
+        self._keep = []
+        self.m = int(m)
 
     def set_krylov_log(self, max_iters: int):
         """Record the Krylov log (at most max_iters rows) in the next solves; 0 = off."""
@@ -440,5 +484,5 @@ class Solver:
         st = self._lib.kw_spmv_dot(self._ctx, kw_c128(zs.real, zs.imag), C.c_void_p(r.data_ptr()),
                                    C.c_void_p(q.data_ptr()), C.byref(t))
         if st != KW_OK:
-            raise self._err(st, "kw_spmv_dot")
+            raise self._err(st, "kw_spmv_dot") from getattr(self, "_mv_error", None)
         return complex(t.re, t.im)
