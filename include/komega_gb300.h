@@ -296,6 +296,12 @@ kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
  * row of the CSR kernel (1, 2, 4, 8 or 16), or 32 = the SELL-32 layout (an
  * internal sliced-ELLPACK copy: rows sorted by length within windows of 1024
  * rows, 32 rows per slice, column-major inside a slice, one thread per row);
+ * 64 + G (G = 1, 2, 4, 8, 16) = the uniform off-diagonal layout with G threads
+ * per row, for operators whose off-diagonal entries all have one value (lattice
+ * hoppings, spin-flip amplitudes): an internal copy holding int32 row offsets,
+ * the off-diagonal columns only and the summed diagonal, so that
+ * H r = d_i r_i + v * (sum of r over the row's off-diagonal columns); forcing
+ * it on another operator fails with KW_ERR_ARG at the next solve;
  * 0 = choose by timing every candidate on the current operator at the next
  * solve, the default (operators with fewer than 2^20 non-zeros are not timed
  * and use 1).  val_f32 (KW_F64 mode only): 1 =

@@ -78,6 +78,11 @@ struct kw_ctx {
   // SELL-32 copy of the operator (built when the tuner tries it or it is forced)
   DBuf sell_perm, sell_len, sell_slen, sell_ptr, sell_col, sell_val;
   bool sell_built = false;
+  // uniform off-diagonal copy (built when the tuner tries it or it is forced)
+  int u_state = 0;            // 0: not examined, 1: built, -1: off-diagonal values differ
+  double u_v = 0.0;
+  int u_kind = 0;             // diagonal/value storage for the context's form (kw::Work::u_kind)
+  DBuf u_fm, u_dcount, u_scratch, u_rowptr, u_col, u_diag64, u_diag32, u_diagpair;
   // host-solve copies
   DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
   // workspace
@@ -196,7 +201,8 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot,
-                  &ctx->mv_r, &ctx->mv_q, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
+                  &ctx->mv_r, &ctx->mv_q, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
+                  &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
@@ -237,6 +243,7 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   ctx->val32_exact = false;
   ctx->spmv_lanes = 0;   // re-tune for the new operator
   ctx->sell_built = false;
+  ctx->u_state = 0;
   if (nnz > 0) {
     KW_CUDA(ctx->val32.ensure((size_t)nnz * sizeof(float)), "kw_set_csr: FP32 value copy");
     KW_CUDA(ctx->inexact.ensure(sizeof(unsigned long long)), "kw_set_csr: counter");
@@ -293,6 +300,13 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.val = w.val_f32 ? (const void*)ctx->val32.p
                     : (p == KW_DF64 ? (const void*)ctx->valpair.p : (const void*)ctx->val);
   w.spmv_lanes = lanes;
+  if (lanes > kw::KW_SPMV_UNIFORM && ctx->u_state == 1) {
+    w.u_rowptr = (const int*)ctx->u_rowptr.p;
+    w.u_col = (const int*)ctx->u_col.p;
+    w.u_kind = ctx->u_kind;
+    w.u_diag = ctx->u_kind == 0 ? ctx->u_diag64.p : ctx->u_kind == 1 ? ctx->u_diag32.p : ctx->u_diagpair.p;
+    w.u_v = ctx->u_v;
+  }
   w.mv_fn = ctx->mv_fn;
   w.mv_user = ctx->mv_user;
   w.mv_r = ctx->mv_r.p;
@@ -359,6 +373,60 @@ static kw_status build_sell(kw_ctx* ctx) {
   return KW_OK;
 }
 
+// Uniform off-diagonal copy of the CSR operator: detect (every off-diagonal
+// value bitwise equal), then build int32 offsets, the off-diagonal columns and
+// the summed diagonal in the storage the context's form reads.
+static kw_status build_uniform(kw_ctx* ctx) {
+  if (ctx->u_state != 0) return KW_OK;
+  const int m = (int)ctx->m;
+  KW_CUDA(ctx->u_fm.ensure(2 * sizeof(unsigned long long)), "uniform layout allocation");
+  KW_CUDA(ctx->u_dcount.ensure((size_t)m * 4), "uniform layout allocation");
+  KW_CUDA(kw::launch_uniform_check(m, ctx->rowptr, ctx->col, ctx->val, (unsigned long long*)ctx->u_fm.p,
+                                   (int*)ctx->u_dcount.p, ctx->stream), "uniform layout check");
+  unsigned long long fm[2] = {0, 0};
+  KW_CUDA(cudaMemcpyAsync(fm, ctx->u_fm.p, sizeof(fm), cudaMemcpyDeviceToHost, ctx->stream), "uniform layout check");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "uniform layout check");
+  if (fm[1] != 0) {
+    ctx->u_state = -1;
+    return KW_OK;
+  }
+  double v = 0.0;
+  if (fm[0] != ~0ull)
+    KW_CUDA(cudaMemcpy(&v, ctx->val + fm[0], sizeof(double), cudaMemcpyDeviceToHost), "uniform layout value");
+  const int64_t noff = ctx->nnz;   // upper bound: the diagonal entries are dropped
+  KW_CUDA(ctx->u_scratch.ensure((size_t)((m + 1023) / 1024) * 4), "uniform layout allocation");
+  KW_CUDA(ctx->u_rowptr.ensure((size_t)(m + 1) * 4), "uniform layout allocation");
+  KW_CUDA(ctx->u_col.ensure((size_t)std::max<int64_t>(noff, 1) * 4), "uniform layout allocation");
+  KW_CUDA(ctx->u_diag64.ensure((size_t)m * 8), "uniform layout allocation");
+  KW_CUDA(kw::launch_uniform_build(m, ctx->rowptr, ctx->col, ctx->val, (int*)ctx->u_dcount.p,
+                                   (int*)ctx->u_scratch.p, (int*)ctx->u_rowptr.p, (int*)ctx->u_col.p,
+                                   (double*)ctx->u_diag64.p, ctx->stream), "uniform layout build");
+  // FP32 copy of the diagonal and whether it (and the value) is exact in FP32
+  KW_CUDA(ctx->u_diag32.ensure((size_t)m * 4), "uniform layout allocation");
+  KW_CUDA(ctx->inexact.ensure(sizeof(unsigned long long)), "uniform layout allocation");
+  KW_CUDA(cudaMemsetAsync(ctx->inexact.p, 0, sizeof(unsigned long long), ctx->stream), "uniform layout memset");
+  KW_CUDA(kw::launch_convert_f64_to_f32((const double*)ctx->u_diag64.p, (float*)ctx->u_diag32.p, m,
+                                        (unsigned long long*)ctx->inexact.p, ctx->stream), "uniform layout convert");
+  unsigned long long bad = 0;
+  KW_CUDA(cudaMemcpyAsync(&bad, ctx->inexact.p, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream), "uniform layout");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "uniform layout sync");
+  const bool exact32 = bad == 0 && (double)(float)v == v;
+  const kw_precision p = ctx->opt.prec;
+  if (p == KW_C32V_F64S || exact32) {
+    ctx->u_kind = 1;
+  } else if (p == KW_DF64) {
+    ctx->u_kind = 2;
+    KW_CUDA(ctx->u_diagpair.ensure((size_t)m * 8), "uniform layout allocation");
+    KW_CUDA(kw::launch_convert_f64_to_pair((const double*)ctx->u_diag64.p, ctx->u_diagpair.p, m, ctx->stream),
+            "uniform layout convert");
+  } else {
+    ctx->u_kind = 0;
+  }
+  ctx->u_v = v;
+  ctx->u_state = 1;
+  return KW_OK;
+}
+
 // kw_c128 staging vectors of the callback operator in the FP32-pair form.
 static kw_status ensure_mv_buffers(kw_ctx* ctx) {
   if (!ctx->mv_fn || ctx->opt.prec != KW_DF64) return KW_OK;
@@ -391,9 +459,19 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   }
   if (ctx->spmv_lanes > 0) return KW_OK;
   const kw_precision p = ctx->opt.prec;
-  if (ctx->nnz < kTuneMinNnz || ctx->force_lanes == kw::KW_SPMV_SELL) {
+  if (ctx->nnz < kTuneMinNnz || ctx->force_lanes == kw::KW_SPMV_SELL || ctx->force_lanes > kw::KW_SPMV_UNIFORM) {
     ctx->spmv_lanes = ctx->force_lanes > 0 ? ctx->force_lanes : 1;
     ctx->spmv_val_f32 = (p == KW_F64 && ctx->force_val == 1 && ctx->val32_exact) ? 1 : 0;
+    if (ctx->spmv_lanes > kw::KW_SPMV_UNIFORM) {
+      kw_status us = build_uniform(ctx);
+      if (us != KW_OK) return us;
+      if (ctx->u_state != 1) {
+        ctx->spmv_lanes = 0;
+        return fail(ctx, KW_ERR_ARG, "uniform off-diagonal layout requested, but the off-diagonal values differ");
+      }
+      ctx->spmv_val_f32 = ctx->u_kind == 1 ? 1 : 0;
+      return KW_OK;
+    }
     if (ctx->spmv_lanes == kw::KW_SPMV_SELL) {
       if (p == KW_F64) ctx->spmv_val_f32 = 0;   // the SELL copy keeps FP64 values in the FP64 form
       return build_sell(ctx);
@@ -408,7 +486,8 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   KW_CUDA(ctx->tdot.ensure(16), "tune alloc");
   KW_CUDA(cudaMemsetAsync(ctx->rA.p, 0, ctx->m * vs, ctx->stream), "tune memset");
   KW_CUDA(cudaMemsetAsync(ctx->st.p, 0, sizeof(kw::State), ctx->stream), "tune memset");
-  const int lane_opts[] = {1, 2, 4, 8, 16, kw::KW_SPMV_SELL};
+  const int lane_opts[] = {1, 2, 4, 8, 16, kw::KW_SPMV_SELL, kw::KW_SPMV_UNIFORM + 1, kw::KW_SPMV_UNIFORM + 2,
+                           kw::KW_SPMV_UNIFORM + 4, kw::KW_SPMV_UNIFORM + 8};
   // value storage candidates: only the FP64 form has a choice (FP64 or exact FP32 values)
   int vals[2] = {0, 1}, nvals = 1;
   if (p == KW_F64 && ctx->val32_exact) nvals = 2;
@@ -430,6 +509,12 @@ static kw_status tune_spmv(kw_ctx* ctx) {
         if (vi > 0) continue;   // the SELL copy has one value type per form
         kw_status bs = build_sell(ctx);
         if (bs != KW_OK) return bs;
+      }
+      if (l > kw::KW_SPMV_UNIFORM) {
+        if (vi > 0) continue;   // one storage per form, chosen when the copy is built
+        kw_status us = build_uniform(ctx);
+        if (us != KW_OK) return us;
+        if (ctx->u_state != 1) continue;
       }
       kw::Work w;
       spmv_work(ctx, w, l, vals[vi]);
@@ -453,6 +538,7 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   KW_CUDA(cudaGetLastError(), "tune launches");
   ctx->spmv_lanes = best_l;
   ctx->spmv_val_f32 = best_l == kw::KW_SPMV_SELL ? (p == KW_F64 ? 0 : best_v) : best_v;
+  if (best_l > kw::KW_SPMV_UNIFORM) ctx->spmv_val_f32 = ctx->u_kind == 1 ? 1 : 0;
   if (best_l != kw::KW_SPMV_SELL && ctx->sell_built) {   // not chosen: give the memory back
     ctx->sell_col.release();
     ctx->sell_val.release();
@@ -1058,7 +1144,8 @@ kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every) {
 kw_status kw_set_spmv_config(kw_ctx* ctx, int lanes, int val_f32) {
   if (!ctx ||
       !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
-        lanes == kw::KW_SPMV_SELL) ||
+        lanes == kw::KW_SPMV_SELL || lanes == kw::KW_SPMV_UNIFORM + 1 || lanes == kw::KW_SPMV_UNIFORM + 2 ||
+        lanes == kw::KW_SPMV_UNIFORM + 4 || lanes == kw::KW_SPMV_UNIFORM + 8 || lanes == kw::KW_SPMV_UNIFORM + 16) ||
       val_f32 < -1 || val_f32 > 1)
     return KW_ERR_ARG;
   ctx->force_lanes = lanes;
@@ -1073,7 +1160,8 @@ kw_status kw_get_spmv_config(kw_ctx* ctx, int* lanes, int* val_f32) {
   kw_status s = tune_spmv(ctx);
   if (s != KW_OK) return s;
   *lanes = ctx->spmv_lanes;
-  *val_f32 = ctx->opt.prec == KW_F64 ? ctx->spmv_val_f32 : (ctx->opt.prec == KW_C32V_F64S ? 1 : (ctx->val32_exact ? 1 : 0));
+  if (ctx->spmv_lanes > kw::KW_SPMV_UNIFORM) *val_f32 = ctx->u_kind == 1 ? 1 : 0;
+  else *val_f32 = ctx->opt.prec == KW_F64 ? ctx->spmv_val_f32 : (ctx->opt.prec == KW_C32V_F64S ? 1 : (ctx->val32_exact ? 1 : 0));
   return KW_OK;
 }
 

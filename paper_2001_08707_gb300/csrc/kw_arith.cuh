@@ -164,6 +164,23 @@ __device__ __forceinline__ void mac(dfc& acc, df v, dfc x) {
   mac_pair(acc.re, v, x.re);
   mac_pair(acc.im, v, x.im);
 }
+// acc += x for vectors; the pair form adds the leading parts exactly (TwoSum)
+// and collects every trailing part in acc.lo (normalise once at the end).
+__device__ __forceinline__ void vacc(double2& acc, double2 x) {
+  acc.x += x.x;
+  acc.y += x.y;
+}
+__device__ __forceinline__ void vacc(float2& acc, float2 x) {
+  acc.x += x.x;
+  acc.y += x.y;
+}
+__device__ __forceinline__ void vacc(dfc& acc, dfc x) {
+  const df sr = two_sum(acc.re.hi, x.re.hi), si = two_sum(acc.im.hi, x.im.hi);
+  acc.re.hi = sr.hi;
+  acc.re.lo = __fadd_rn(acc.re.lo, __fadd_rn(sr.lo, x.re.lo));
+  acc.im.hi = si.hi;
+  acc.im.lo = __fadd_rn(acc.im.lo, __fadd_rn(si.lo, x.im.lo));
+}
 __device__ __forceinline__ dfc normalize(dfc a) {
   return {fast_two_sum(a.re.hi, a.re.lo), fast_two_sum(a.im.hi, a.im.lo)};
 }

@@ -73,6 +73,13 @@ struct Work {
   const int64_t* sell_ptr;   // [nslice + 1] start of each slice
   const int* sell_col;       // [padded nnz]
   const void* sell_val;      // [padded nnz] in the SpMV value type
+  // Uniform off-diagonal copy of the operator (spmv_lanes >= KW_SPMV_UNIFORM):
+  // H r = diag * r + u_v * (sum of r over the off-diagonal columns of the row).
+  const int* u_rowptr;       // [m + 1] int32 offsets into u_col
+  const int* u_col;          // off-diagonal columns only
+  const void* u_diag;        // [m] diagonal: double, float (u_kind 1) or FP32 pair (u_kind 2)
+  int u_kind;                // 0: FP64 diagonal and value, 1: FP32 (exact), 2: FP32 pair
+  double u_v;                // the off-diagonal value
   int val_f32;       // matrix values stored as FP32 (always in C32 mode; in F64 mode when lossless)
   // seed vectors
   void* rA;          // two rotating residual buffers and q
@@ -127,6 +134,17 @@ cudaError_t launch_convert_f64_to_pair(const double* in, void* out, int64_t n, c
 
 // spmv_lanes value that selects the SELL-32 layout.
 constexpr int KW_SPMV_SELL = 32;
+// spmv_lanes = KW_SPMV_UNIFORM + G selects the uniform off-diagonal layout with
+// G lanes per row (G = 1, 2, 4, 8, 16).
+constexpr int KW_SPMV_UNIFORM = 64;
+// Uniform off-diagonal layout: find the first off-diagonal entry and count the
+// off-diagonal values that differ from it (bitwise) and the diagonal entries
+// per row (dcount [m]); then build u_rowptr, u_col and the FP64 diagonal.
+// scratch: [nblk] ints for the scan, nblk = ceil(m / 1024).
+cudaError_t launch_uniform_check(int m, const int64_t* rowptr, const int* col, const double* val,
+                                 unsigned long long* first_and_mismatch, int* dcount, cudaStream_t s);
+cudaError_t launch_uniform_build(int m, const int64_t* rowptr, const int* col, const double* val, int* dcount,
+                                 int* scratch, int* u_rowptr, int* u_col, double* diag, cudaStream_t s);
 cudaError_t launch_sell_order(int m, const int64_t* rowptr, int* perm, int* rlen, int* slen, cudaStream_t s);
 template <class RV>
 cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,

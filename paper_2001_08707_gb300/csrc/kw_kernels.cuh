@@ -337,6 +337,85 @@ k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restri
   spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
 }
 
+// K1 on the uniform off-diagonal layout: every off-diagonal entry of H has the
+// same value u_v (lattice hoppings, spin-flip amplitudes), so a row needs only
+// its off-diagonal columns and its diagonal: H r = d_i r_i + u_v sum_j r_{c_j}.
+// G lanes per row as in k_spmv_dot; the sum is taken in the vector type (the
+// pair form with one normalisation per row), then scaled once.
+template <int P, class DV, int G>
+__global__ void __launch_bounds__(256)
+k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, const DV* __restrict__ diag, DV uv,
+         const typename PT<P>::V* __restrict__ r, typename PT<P>::V* __restrict__ q, State* st,
+         double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  V zsv, scv = vzero<V>();
+  bool scaled = false;
+  if (mode.solver) {
+    if (st->done) return;
+    zsv = vscalar<V>(st->zs, st->p_zs);
+    if (st->vec_scale_pending) {
+      scv = vscalar<V>(st->scale_rn, st->p_s1);
+      scaled = true;
+    }
+  } else {
+    zsv = vscalar<V>(mode.zs, mode.zs_pair);
+  }
+  const int lane = threadIdx.x & 31, sub = lane % G, gw = lane / G;
+  const int RPW = 32 / G;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  for (int base = warp_global * RPW; base < m; base += nwarps * RPW) {
+    const int row = base + gw;
+    V sum = vzero<V>();
+    if (row < m) {
+      const int beg = rowptr[row], end = rowptr[row + 1];
+      if (G == 1) {
+        int j = beg;
+        for (; j + 3 < end; j += 4) {        // four independent gathers in flight
+          const int c0 = col[j], c1 = col[j + 1], c2 = col[j + 2], c3 = col[j + 3];
+          const V x0 = r[c0], x1 = r[c1], x2 = r[c2], x3 = r[c3];
+          vacc(sum, x0);
+          vacc(sum, x1);
+          vacc(sum, x2);
+          vacc(sum, x3);
+        }
+        for (; j < end; ++j) vacc(sum, r[col[j]]);
+      } else {
+        for (int j = beg + sub; j < end; j += G) vacc(sum, r[col[j]]);
+      }
+    }
+    sum = normalize(sum);
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) vshfl_add(sum, off);
+    if (sub == 0 && row < m) {
+      V ri = r[row];
+      V hr = vzero<V>();
+      mac(hr, diag[row], ri);
+      mac(hr, uv, sum);
+      hr = normalize(hr);
+      V qi = csub(cmul(zsv, ri), hr);         // z_s r - H r
+      if (scaled) {                           // lazy seed switch: r <- s r, q <- s q
+        qi = cmul(scv, qi);
+        ri = cmul(scv, ri);
+      }
+      q[row] = qi;
+      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
+    }
+    if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
 // K1 for an operator given as a callback (kw_set_matvec).  The caller's work
 // has left H r in hq (kw_c128 in the FP64 and FP32-pair forms, complex FP32 in
 // the FP32 form; in place in q except in the pair form); this pass forms
@@ -1162,6 +1241,52 @@ static cudaError_t spmv_dispatch_v(Work& w, const void* r, void* q, SpmvMode mod
   }
 }
 
+template <int P, class DV, int G>
+static cudaError_t uniform_launch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_spmv_u<P, DV, G>, 256, w.num_sms);
+  const int need = (int)((w.m * G + 255) / 256);
+  const int grid = std::max(1, std::min(nblk, need));
+  DV uv;
+  if constexpr (std::is_same<DV, double>::value) uv = w.u_v;
+  else if constexpr (std::is_same<DV, float>::value) uv = (float)w.u_v;
+  else {
+    uv.hi = (float)w.u_v;
+    uv.lo = (float)(w.u_v - (double)uv.hi);
+  }
+  k_spmv_u<P, DV, G><<<grid, 256, 0, w.stream>>>((int)w.m, w.u_rowptr, w.u_col, (const DV*)w.u_diag, uv,
+                                                 (const V*)r, (V*)q, w.st, w.part, mode);
+  return cudaGetLastError();
+}
+
+template <int P, class DV>
+static cudaError_t uniform_dispatch_g(Work& w, const void* r, void* q, SpmvMode mode) {
+  switch (w.spmv_lanes - KW_SPMV_UNIFORM) {
+    case 1: return uniform_launch<P, DV, 1>(w, r, q, mode);
+    case 2: return uniform_launch<P, DV, 2>(w, r, q, mode);
+    case 4: return uniform_launch<P, DV, 4>(w, r, q, mode);
+    case 8: return uniform_launch<P, DV, 8>(w, r, q, mode);
+    default: return uniform_launch<P, DV, 16>(w, r, q, mode);
+  }
+}
+
+// The diagonal/value type per form: FP64 (kind 0) only in the FP64 form, FP32
+// (kind 1) when exact (always in the FP32 form), FP32 pairs (kind 2) in the pair form.
+template <int P>
+static cudaError_t uniform_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
+  if (!w.u_rowptr || !w.u_col || !w.u_diag) return cudaErrorInvalidValue;
+  if constexpr (P == PREC_F64) {
+    if (w.u_kind == 1) return uniform_dispatch_g<P, float>(w, r, q, mode);
+    return uniform_dispatch_g<P, double>(w, r, q, mode);
+  } else if constexpr (P == PREC_C32) {
+    return uniform_dispatch_g<P, float>(w, r, q, mode);
+  } else {
+    if (w.u_kind == 1) return uniform_dispatch_g<P, float>(w, r, q, mode);
+    return uniform_dispatch_g<P, df>(w, r, q, mode);
+  }
+}
+
 // K1 through the caller's matrix-vector callback.
 template <int P>
 static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
@@ -1192,6 +1317,7 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
 template <int P>
 static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
   if (w.mv_fn) return matvec_dispatch<P>(w, r, q, mode);
+  if (w.spmv_lanes > KW_SPMV_UNIFORM) return uniform_dispatch<P>(w, r, q, mode);
   if constexpr (P == PREC_F64) {
     if (w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);
     return spmv_dispatch_v<P, double>(w, r, q, mode);

@@ -79,6 +79,144 @@ cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- uniform off-diagonal layout
+// fm[0]: smallest index of an off-diagonal entry (ULLONG_MAX if none);
+// fm[1]: off-diagonal entries whose value differs bitwise from that entry's.
+static __global__ void k_u_first(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                 unsigned long long* fm) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      if (col[j] != i) {
+        atomicMin(fm, (unsigned long long)j);
+        break;
+      }
+    }
+  }
+}
+
+static __global__ void k_u_count(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                 const double* __restrict__ val, unsigned long long* fm, int* __restrict__ dcount) {
+  const unsigned long long first = fm[0];
+  const long long v0 = first == ~0ull ? 0 : __double_as_longlong(val[first]);
+  unsigned long long bad = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    int d = 0;
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      if (col[j] == i) ++d;
+      else bad += __double_as_longlong(val[j]) != v0;
+    }
+    dcount[i] = d;
+  }
+  bad = warp_sum(bad);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(fm + 1, bad);
+}
+
+cudaError_t launch_uniform_check(int m, const int64_t* rowptr, const int* col, const double* val,
+                                 unsigned long long* fm, int* dcount, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(fm, 0xff, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fm + 1, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(4096, (m + 255) / 256));
+  k_u_first<<<grid, 256, 0, s>>>(m, rowptr, col, fm);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_u_count<<<grid, 256, 0, s>>>(m, rowptr, col, val, fm, dcount);
+  return cudaGetLastError();
+}
+
+// Exclusive scan of dcount in blocks of 1024 (in place), block totals to tot.
+static __global__ void __launch_bounds__(1024) k_scan_blocks(int m, int* __restrict__ v, int* __restrict__ tot) {
+  __shared__ int ws[32];
+  const int i = blockIdx.x * 1024 + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int x = i < m ? v[i] : 0;
+  int inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(KW_FULL_MASK, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = ws[lane], wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(KW_FULL_MASK, wi, o);
+      if (lane >= o) wi += y;
+    }
+    ws[lane] = wi - w;   // exclusive prefix of the warp totals
+    if (lane == 31) tot[blockIdx.x] = wi;
+  }
+  __syncthreads();
+  if (i < m) v[i] = ws[warp] + inc - x;
+}
+
+// Exclusive scan of the nb block totals in place (one block of 1024 threads,
+// each owning a contiguous segment).
+static __global__ void __launch_bounds__(1024) k_scan_tops(int nb, int* __restrict__ tot) {
+  __shared__ int ws[32];
+  const int seg = (nb + 1023) / 1024, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int b0 = min(nb, t * seg), b1 = min(nb, b0 + seg);
+  int local = 0;
+  for (int b = b0; b < b1; ++b) local += tot[b];
+  int inc = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(KW_FULL_MASK, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) ws[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = ws[lane], wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(KW_FULL_MASK, wi, o);
+      if (lane >= o) wi += y;
+    }
+    ws[lane] = wi - w;
+  }
+  __syncthreads();
+  int run = ws[warp] + inc - local;
+  for (int b = b0; b < b1; ++b) {
+    const int x = tot[b];
+    tot[b] = run;
+    run += x;
+  }
+}
+
+// Row i: its off-diagonal columns start at rowptr[i] minus the diagonal entries
+// of the rows before it; the diagonal entries of the row are summed.
+static __global__ void k_u_fill(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                const double* __restrict__ val, const int* __restrict__ dpre,
+                                const int* __restrict__ tops, int* __restrict__ u_rowptr, int* __restrict__ u_col,
+                                double* __restrict__ diag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int64_t b = rowptr[i] - (dpre[i] + tops[i >> 10]);
+    int k = 0;
+    double d = 0.0;
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      if (col[j] == i) d += val[j];
+      else u_col[b + k++] = col[j];
+    }
+    u_rowptr[i] = (int)b;
+    diag[i] = d;
+    if (i == m - 1) u_rowptr[m] = (int)(b + k);
+  }
+}
+
+cudaError_t launch_uniform_build(int m, const int64_t* rowptr, const int* col, const double* val, int* dcount,
+                                 int* scratch, int* u_rowptr, int* u_col, double* diag, cudaStream_t s) {
+  const int nb = (m + 1023) / 1024;
+  k_scan_blocks<<<nb, 1024, 0, s>>>(m, dcount, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_scan_tops<<<1, 1024, 0, s>>>(nb, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(4096, (m + 255) / 256));
+  k_u_fill<<<grid, 256, 0, s>>>(m, rowptr, col, val, dcount, scratch, u_rowptr, u_col, diag);
+  return cudaGetLastError();
+}
+
 template <int LPS, int NPL>
 static cudaError_t recalc_launch(int K, int np, long long n_iter, const double2* log, const double2* w0,
                                  const double2* z, double thresh, double2* proj, long long* conv_iter,
