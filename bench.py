@@ -66,17 +66,44 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def _definition(src: str, name: str) -> str:
+    """Text of the (first) definition of function `name` in src: from the
+    template line above its name to the matching closing brace."""
+    i = src.find("\n" + name + "(")
+    if i < 0:
+        i = src.find(" " + name + "(")
+    if i < 0:
+        raise KeyError(name)
+    start = src.rfind("\ntemplate", 0, i)
+    start = start if start >= 0 and i - start < 300 else src.rfind("\n", 0, i)
+    depth, j = 0, src.index("{", i)
+    while True:
+        if src[j] == "{":
+            depth += 1
+        elif src[j] == "}":
+            depth -= 1
+            if depth == 0:
+                return src[start:j + 1]
+        j += 1
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """sha256 (16 hex) of the kernel's definition, the shared K1 tail and the
+    arithmetic header: what a change of which voids a recorded ncu count."""
+    with open(KERNEL_SRC) as f:
+        src = f.read()
+    with open(os.path.join(os.path.dirname(KERNEL_SRC), "kw_arith.cuh")) as f:
+        arith = f.read()
+    text = _definition(src, kernel) + _definition(src, "spmv_finish") + arith
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def recorded_traffic(kernel_key: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source (else None).  kernel_key: '<kernel><form>:<workload>'."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
-    h = kernel_source_hash()
+    h = kernel_source_hash(kernel_key.split("<")[0])
     with open(TRAFFIC_FILE) as f:
         for line in f:
             parts = line.split()
@@ -85,10 +112,13 @@ def recorded_traffic(kernel_key: str):
     return None
 
 
+CHAIN_N = 24
+
+
 def make_problem():
     from paper_2001_08707_gb300 import workloads as w
 
-    return w.heisenberg_projected(N=24, K=1024, delta=0.01, tol=1e-10)
+    return w.heisenberg_projected(N=CHAIN_N, K=1024, delta=0.01, tol=1e-10)
 
 
 def spmv_bytes(m, nnz, vec_bytes, val_bytes):
@@ -296,12 +326,16 @@ def run_ours(args):
         # profiling mode: the headline kernels on the same workload, one solve capped at N iterations
         prec = args.profile_prec or HEADLINE
         s = kw.Solver(prec, tol=p.tol, maxiter=args.profile_iters)
-        s.set_spmv_config(args.profile_lanes, 0)
-        s.set_csr(p.H.rowptr, p.H.col, p.H.val)
+        if args.profile_op == "spin":
+            s.set_spin_operator(CHAIN_N, CHAIN_N // 2, [(i, (i + 1) % CHAIN_N) for i in range(CHAIN_N)], 1.0)
+            cfg = "spin operator"
+        else:
+            s.set_spmv_config(args.profile_lanes, 0)
+            s.set_csr(p.H.rowptr, p.H.col, p.H.val)
+            cfg = s.spmv_config()
         r = s.solve(bd, p.z, left=ld)
         torch.cuda.synchronize()
-        print(json.dumps({"profile": prec, "iters": r.iters, "status": r.status,
-                          "spmv_config": s.spmv_config()}))
+        print(json.dumps({"profile": prec, "iters": r.iters, "status": r.status, "spmv_config": cfg}))
         return 0
 
     def device_leg(prec, warmup, steps, maxiter, sampler=None):
@@ -417,6 +451,37 @@ def run_ours(args):
                            "unit": "TFLOP/s", "frac": rc_tflops / FP64_PEAK_TFLOPS,
                            "flops_per_shift_row": rc_flops, "peak_kind": "nominal FP64"}}
 
+    # Matrix-free form of the same Hamiltonian (Sec. 3.1 (i)): the spin operator
+    # generated inside K1 (basis word and diagonal per row, no index arrays),
+    # headline form, one warm-up and one timed solve.
+    smf = kw.Solver(HEADLINE, tol=p.tol, maxiter=200000)
+    smf.set_spin_operator(CHAIN_N, CHAIN_N // 2, [(i, (i + 1) % CHAIN_N) for i in range(CHAIN_N)], 1.0)
+    smf.set_kernel_timing(1)
+    smf.solve(bd, p.z, left=ld)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    mf_res = smf.solve(bd, p.z, left=ld)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mf_ms = reduce_max(e0.elapsed_time(e1), ws, device)
+    mf_stats = smf.stats()
+    smf.close()
+    ti, k = kstats([mf_stats])
+    vb = PREC_BYTES[HEADLINE][0]
+    mf_bytes = (4 + 4 + 2 * vb) * m          # basis word, FP32 diagonal (exact), r read, q written
+    kernels[HEADLINE + "_matrix_free"] = {
+        "spmv_us": 1e3 * k[0], "spmv_gbs": mf_bytes / (k[0] * 1e-3) / 1e9, "spmv_bytes": mf_bytes,
+        "seed_update_us": 1e3 * k[1], "shift_us": 1e3 * k[2], "iteration_us": mf_ms * 1e3 / max(mf_res.iters, 1),
+        "sampled_iterations": ti, "operator": "kw_set_spin_operator (k_spmv_spin)",
+        "traffic": recorded_traffic(f"k_spmv_spin<{HEADLINE}>:heisenberg_N24")}
+    e_spec, e_proj = compare(mf_res)
+    legs["matrix_free"] = {"value": ws * work / (mf_ms / 1e3), "ms_per_step": mf_ms, "iters": mf_res.iters,
+                           "status": mf_res.status, "spectrum_rel_err_vs_headline": e_spec,
+                           "projection_rel_err_vs_headline": e_proj,
+                           "note": "same Hamiltonian generated on the fly instead of the CSR input"}
+
     peak, peak_kind = load_peaks()
     kh = kernels[HEADLINE]
     launches = sum(s["launches"] for s in h_stats)
@@ -506,6 +571,8 @@ def main(argv=None):
                     help="profiling mode: one solve capped at N iterations, no timing")
     ap.add_argument("--profile-prec", choices=["f64", "c32", "df64"], default=None,
                     help="precision form of the profiling-mode solve (default: the headline form)")
+    ap.add_argument("--profile-op", choices=["csr", "spin"], default="csr",
+                    help="profiling mode: the CSR input (default) or the same chain generated on the fly")
     ap.add_argument("--profile-lanes", type=int, default=1,
                     help="SpMV lanes per row in profiling mode (the autotuner's timings are not "
                          "meaningful under a profiler; 1 is its pick on this workload)")

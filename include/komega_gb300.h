@@ -152,6 +152,39 @@ typedef int (*kw_matvec_fn)(void* user, const void* r_dev, void* q_dev, int64_t 
  * (m < 1, m >= 2^31, fn NULL). */
 kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user);
 
+/* Most bonds and sites of a spin operator (kw_set_spin_operator). */
+#define KW_SPIN_MAX_BONDS 256
+#define KW_SPIN_MAX_SITES 31
+
+/* Set the operator H to a spin-1/2 Hamiltonian generated on the fly (matrix-
+ * free, Sec. 3.1 (i): the matrix elements are produced inside the product and
+ * never stored, the paper's route to large M):
+ *   H = sum_b J_b S_{i_b} . S_{j_b} + sum_i h_i S^z_i
+ * on the basis of all nsite-bit words with nup set bits (bit i set = spin i up;
+ * fixed S^z_total sector), in increasing order, so M = C(nsite, nup) and the
+ * row of a word is its rank in the combinatorial number system.  A bond
+ * contributes J_b/4 (parallel spins) or -J_b/4 (antiparallel) to the diagonal
+ * and J_b/2 between two words that differ by exchanging its two spins; h_i
+ * contributes +h_i/2 (up) or -h_i/2 (down).  bonds_host int32 [nbond][2] (site
+ * pairs, i != j, each < nsite), J_host [nbond], h_host [nsite] or NULL (no
+ * field).  The context builds the basis table (4 bytes per row) and the
+ * diagonal (4 or 8 bytes per row) on the device; a product then reads only
+ * these, r and q.  Ends any CSR matrix or callback.  Errors: KW_ERR_ARG
+ * (1 <= nup < nsite <= KW_SPIN_MAX_SITES, 1 <= nbond <= KW_SPIN_MAX_BONDS, bad
+ * bond, M >= 2^31, non-finite J or h), KW_ERR_OOM. */
+kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const int32_t* bonds_host,
+                               const double* J_host, const double* h_host);
+
+/* Set the operator H to a tight-binding model on a periodic nx x ny x nz
+ * lattice, generated on the fly: H_ii = eps_i, H_ij = hopping for the six
+ * nearest neighbours j of site i = x + nx (y + ny z) (the Anderson model of
+ * Sec. 4 with eps_i the disorder).  eps_dev float64 [nx ny nz] (device; the
+ * context keeps its own copy in the form's precision).  Each extent must be at
+ * least 3 (six distinct neighbours).  Ends any CSR matrix or callback.  Errors:
+ * KW_ERR_ARG (extent < 3, nx ny nz >= 2^31, eps_dev NULL, hopping not finite),
+ * KW_ERR_OOM. */
+kw_status kw_set_lattice3d(kw_ctx* ctx, int64_t nx, int64_t ny, int64_t nz, const double* eps_dev, double hopping);
+
 /* Solve (z_k I - H) x_k = b for all nshift shifts (Eq. 4) by shifted COCG.
  *   b_dev       float64 [m], real right-hand side (||b|| > 0).
  *   z_host      kw_c128 [nshift], finite shifts; the initial seed is z_0 (Eq. 6).

@@ -64,6 +64,14 @@ struct kw_ctx {
   const int64_t* rowptr = nullptr;
   const int32_t* col = nullptr;
   const double* val = nullptr;
+  // operator generated on the fly (kw_set_spin_operator, kw_set_lattice3d)
+  int op = kw::OP_CSR;
+  DBuf sp_binom, sp_basis, sp_bond, sp_J, sp_h, sp_val;
+  int sp_nbond = 0, sp_uniform = 0;
+  int lx = 0, ly = 0, lz = 0;
+  DBuf g_diag64, g_diag32, g_diagpair;   // diagonal (spin) or on-site energies (lattice)
+  int g_kind = 0;                        // storage read by the form (kw::Work::u_kind)
+  double g_v = 0.0;                      // uniform off-diagonal value (J/2 or the hopping)
   // operator as a caller's callback (kw_set_matvec); the FP32-pair form hands it kw_c128 copies
   kw_matvec_fn mv_fn = nullptr;
   void* mv_user = nullptr;
@@ -201,7 +209,8 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot,
-                  &ctx->mv_r, &ctx->mv_q, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
+                  &ctx->mv_r, &ctx->mv_q, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
+                  &ctx->sp_h, &ctx->sp_val, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag};
   for (DBuf* b : bufs) b->release();
@@ -235,6 +244,7 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
     return fail(ctx, KW_ERR_ARG, "kw_set_csr: need 1 <= m < 2^31, 0 <= nnz < 2^31 and non-NULL arrays");
   ctx->mv_fn = nullptr;
   ctx->mv_user = nullptr;
+  ctx->op = kw::OP_CSR;
   ctx->m = m;
   ctx->nnz = nnz;
   ctx->rowptr = rowptr_dev;
@@ -262,11 +272,139 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   return KW_OK;
 }
 
+// Storage of a generated operator's diagonal for the context's form: FP32 when
+// it and the off-diagonal values are exact in FP32 (always in the FP32 form),
+// else FP64 (FP64 form) or FP32 pairs (pair form).  offdiag_exact32: the
+// off-diagonal values are exact in FP32.
+static kw_status generated_diag(kw_ctx* ctx, int64_t m, bool offdiag_exact32) {
+  KW_CUDA(ctx->g_diag32.ensure((size_t)m * 4), "operator allocation");
+  KW_CUDA(ctx->inexact.ensure(sizeof(unsigned long long)), "operator allocation");
+  KW_CUDA(cudaMemsetAsync(ctx->inexact.p, 0, sizeof(unsigned long long), ctx->stream), "operator memset");
+  KW_CUDA(kw::launch_convert_f64_to_f32((const double*)ctx->g_diag64.p, (float*)ctx->g_diag32.p, m,
+                                        (unsigned long long*)ctx->inexact.p, ctx->stream), "operator convert");
+  unsigned long long bad = 0;
+  KW_CUDA(cudaMemcpyAsync(&bad, ctx->inexact.p, sizeof(bad), cudaMemcpyDeviceToHost, ctx->stream), "operator read");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "operator sync");
+  const kw_precision p = ctx->opt.prec;
+  if (p == KW_C32V_F64S || (bad == 0 && offdiag_exact32)) {
+    ctx->g_kind = 1;
+  } else if (p == KW_DF64) {
+    ctx->g_kind = 2;
+    KW_CUDA(ctx->g_diagpair.ensure((size_t)m * 8), "operator allocation");
+    KW_CUDA(kw::launch_convert_f64_to_pair((const double*)ctx->g_diag64.p, ctx->g_diagpair.p, m, ctx->stream),
+            "operator convert");
+  } else {
+    ctx->g_kind = 0;
+  }
+  return KW_OK;
+}
+
+// The context's operator becomes a generated one: forget the CSR and callback.
+static void become_generated(kw_ctx* ctx, int op, int64_t m) {
+  ctx->op = op;
+  ctx->m = m;
+  ctx->nnz = 0;
+  ctx->rowptr = nullptr;
+  ctx->col = nullptr;
+  ctx->val = nullptr;
+  ctx->mv_fn = nullptr;
+  ctx->mv_user = nullptr;
+  ctx->val32_exact = false;
+  ctx->spmv_lanes = 1;
+  ctx->spmv_val_f32 = 0;
+  ctx->sell_built = false;
+  ctx->u_state = 0;
+}
+
+kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const int32_t* bonds_host,
+                               const double* J_host, const double* h_host) {
+  if (!ctx) return KW_ERR_ARG;
+  if (nsite < 2 || nsite > KW_SPIN_MAX_SITES || nup < 1 || nup >= nsite || nbond < 1 || nbond > KW_SPIN_MAX_BONDS ||
+      !bonds_host || !J_host)
+    return fail(ctx, KW_ERR_ARG, "kw_set_spin_operator: need 1 <= nup < nsite <= %d, 1 <= nbond <= %d, bonds, J",
+                KW_SPIN_MAX_SITES, KW_SPIN_MAX_BONDS);
+  double M = 1.0;
+  for (int k = 0; k < nup; ++k) M = M * (nsite - k) / (k + 1);
+  if (M >= 2147483647.0) return fail(ctx, KW_ERR_ARG, "kw_set_spin_operator: C(nsite, nup) >= 2^31");
+  const int64_t m = (int64_t)(M + 0.5);
+  std::vector<int> bond(nbond);
+  bool uniform = true, exact32 = true;
+  for (int b = 0; b < nbond; ++b) {
+    const int i = bonds_host[2 * b], j = bonds_host[2 * b + 1];
+    if (i < 0 || j < 0 || i >= nsite || j >= nsite || i == j || !isfinite(J_host[b]))
+      return fail(ctx, KW_ERR_ARG, "kw_set_spin_operator: bond %d (%d, %d) or its J is invalid", b, i, j);
+    bond[b] = std::min(i, j) | (std::max(i, j) << 8);
+    uniform = uniform && J_host[b] == J_host[0];
+    const double v = 0.5 * J_host[b];
+    exact32 = exact32 && (double)(float)v == v;
+  }
+  if (h_host)
+    for (int i = 0; i < nsite; ++i)
+      if (!isfinite(h_host[i])) return fail(ctx, KW_ERR_ARG, "kw_set_spin_operator: field %d is not finite", i);
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_set_spin_operator: sync");
+  KW_CUDA(ctx->sp_binom.ensure((size_t)kw::KW_BINOM_N * kw::KW_BINOM_K * 4), "operator allocation");
+  KW_CUDA(ctx->sp_basis.ensure((size_t)m * 4), "operator allocation");
+  KW_CUDA(ctx->sp_bond.ensure((size_t)nbond * 4), "operator allocation");
+  KW_CUDA(ctx->sp_J.ensure((size_t)nbond * 8), "operator allocation");
+  KW_CUDA(ctx->sp_h.ensure((size_t)nsite * 8), "operator allocation");
+  KW_CUDA(ctx->g_diag64.ensure((size_t)m * 8), "operator allocation");
+  KW_CUDA(cudaMemcpy(ctx->sp_bond.p, bond.data(), (size_t)nbond * 4, cudaMemcpyHostToDevice), "operator upload");
+  KW_CUDA(cudaMemcpy(ctx->sp_J.p, J_host, (size_t)nbond * 8, cudaMemcpyHostToDevice), "operator upload");
+  if (h_host) KW_CUDA(cudaMemcpy(ctx->sp_h.p, h_host, (size_t)nsite * 8, cudaMemcpyHostToDevice), "operator upload");
+  KW_CUDA(kw::launch_spin_setup((int)m, nsite, nup, nbond, (const int*)ctx->sp_bond.p, (const double*)ctx->sp_J.p,
+                                h_host ? (const double*)ctx->sp_h.p : nullptr, (int*)ctx->sp_binom.p,
+                                (unsigned*)ctx->sp_basis.p, (double*)ctx->g_diag64.p, ctx->stream),
+          "kw_set_spin_operator: set-up");
+  become_generated(ctx, kw::OP_SPIN, m);
+  kw_status st = generated_diag(ctx, m, exact32);
+  if (st != KW_OK) return st;
+  ctx->sp_nbond = nbond;
+  ctx->sp_uniform = uniform ? 1 : 0;
+  ctx->g_v = 0.5 * J_host[0];
+  // per-bond amplitudes J_b/2 in the diagonal's storage (read when the J_b differ)
+  KW_CUDA(ctx->sp_val.ensure((size_t)nbond * 8), "operator allocation");
+  std::vector<unsigned char> vals((size_t)nbond * 8);
+  for (int b = 0; b < nbond; ++b) {
+    const double v = 0.5 * J_host[b];
+    if (ctx->g_kind == 0) {
+      memcpy(&vals[(size_t)b * 8], &v, 8);
+    } else if (ctx->g_kind == 1) {
+      const float f = (float)v;
+      memcpy(&vals[(size_t)b * 4], &f, 4);
+    } else {
+      const float hi = (float)v, lo = (float)(v - (double)hi);
+      memcpy(&vals[(size_t)b * 8], &hi, 4);
+      memcpy(&vals[(size_t)b * 8 + 4], &lo, 4);
+    }
+  }
+  KW_CUDA(cudaMemcpy(ctx->sp_val.p, vals.data(), vals.size(), cudaMemcpyHostToDevice), "operator upload");
+  return KW_OK;
+}
+
+kw_status kw_set_lattice3d(kw_ctx* ctx, int64_t nx, int64_t ny, int64_t nz, const double* eps_dev, double hopping) {
+  if (!ctx) return KW_ERR_ARG;
+  if (nx < 3 || ny < 3 || nz < 3 || !eps_dev || !isfinite(hopping) || (double)nx * ny * nz >= 2147483647.0)
+    return fail(ctx, KW_ERR_ARG, "kw_set_lattice3d: need extents >= 3, nx ny nz < 2^31, eps and a finite hopping");
+  const int64_t m = nx * ny * nz;
+  KW_CUDA(ctx->g_diag64.ensure((size_t)m * 8), "operator allocation");
+  KW_CUDA(cudaMemcpyAsync(ctx->g_diag64.p, eps_dev, (size_t)m * 8, cudaMemcpyDeviceToDevice, ctx->stream),
+          "kw_set_lattice3d: copy");
+  become_generated(ctx, kw::OP_LATTICE, m);
+  kw_status st = generated_diag(ctx, m, (double)(float)hopping == hopping);
+  if (st != KW_OK) return st;
+  ctx->lx = (int)nx;
+  ctx->ly = (int)ny;
+  ctx->lz = (int)nz;
+  ctx->g_v = hopping;
+  return KW_OK;
+}
+
 kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user) {
   if (!ctx) return KW_ERR_ARG;
   if (m < 1 || m > 0x7fffffffLL || !fn) return fail(ctx, KW_ERR_ARG, "kw_set_matvec: need 1 <= m < 2^31 and fn");
   ctx->mv_fn = fn;
   ctx->mv_user = user;
+  ctx->op = kw::OP_CALLBACK;
   ctx->m = m;
   ctx->nnz = 0;
   ctx->rowptr = nullptr;
@@ -306,6 +444,21 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
     w.u_kind = ctx->u_kind;
     w.u_diag = ctx->u_kind == 0 ? ctx->u_diag64.p : ctx->u_kind == 1 ? ctx->u_diag32.p : ctx->u_diagpair.p;
     w.u_v = ctx->u_v;
+  }
+  w.op = ctx->op;
+  if (ctx->op == kw::OP_SPIN || ctx->op == kw::OP_LATTICE) {
+    w.u_kind = ctx->g_kind;
+    w.u_diag = ctx->g_kind == 0 ? ctx->g_diag64.p : ctx->g_kind == 1 ? ctx->g_diag32.p : ctx->g_diagpair.p;
+    w.u_v = ctx->g_v;
+    w.sp_basis = (const unsigned*)ctx->sp_basis.p;
+    w.sp_binom = (const int*)ctx->sp_binom.p;
+    w.sp_bond = (const int*)ctx->sp_bond.p;
+    w.sp_val = ctx->sp_val.p;
+    w.sp_nbond = ctx->sp_nbond;
+    w.sp_uniform = ctx->sp_uniform;
+    w.lx = ctx->lx;
+    w.ly = ctx->ly;
+    w.lz = ctx->lz;
   }
   w.mv_fn = ctx->mv_fn;
   w.mv_user = ctx->mv_user;
@@ -436,7 +589,8 @@ static kw_status ensure_mv_buffers(kw_ctx* ctx) {
 }
 
 static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 zs, double2* t) {
-  if (!w.st || !w.part || !t || (!w.rowptr && !w.mv_fn)) return cudaErrorInvalidValue;   // workspace must exist
+  if (!w.st || !w.part || !t || (!w.rowptr && !w.mv_fn && w.op < kw::OP_SPIN))
+    return cudaErrorInvalidValue;   // workspace and operator must exist
   const float4 zp = host_pair(zs.x, zs.y);
   switch (w.prec) {
     case kw::PREC_C32: return kw::launch_spmv_dot<kw::PREC_C32>(w, r, q, zs, zp, t);
@@ -451,8 +605,10 @@ static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 
 // and the pick would be noise); they use one thread per row and FP64 values.
 static const int64_t kTuneMinNnz = 1 << 20;
 
+static bool has_operator(const kw_ctx* ctx) { return ctx->rowptr || ctx->mv_fn || ctx->op >= kw::OP_SPIN; }
+
 static kw_status tune_spmv(kw_ctx* ctx) {
-  if (ctx->mv_fn) {   // the caller's callback is the operator: nothing to tune
+  if (ctx->op != kw::OP_CSR) {   // callback or generated operator: nothing to tune
     ctx->spmv_lanes = 1;
     ctx->spmv_val_f32 = 0;
     return KW_OK;
@@ -675,7 +831,7 @@ static cudaError_t iteration_launch(kw::Work& w, int parity, cudaEvent_t* ev, in
 // initialisation (no synchronisation).  The descriptor is kept in ctx->work.
 static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
                              const double* left_dev, void* x_out_dev) {
-  if (!ctx->rowptr && !ctx->mv_fn) return fail(ctx, KW_ERR_ARG, "kw_solve: no operator (kw_set_csr or kw_set_matvec)");
+  if (!has_operator(ctx)) return fail(ctx, KW_ERR_ARG, "kw_solve: no operator has been set");
   if (!b_dev || !z_host || nshift < 1 || nshift > 0x7fffffffLL)
     return fail(ctx, KW_ERR_ARG, "kw_solve: need b, z and 1 <= nshift < 2^31");
   if (nleft < 0 || nleft >= KW_MAX_PROJ || (nleft > 0 && !left_dev))
@@ -1173,7 +1329,7 @@ kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out) {
 
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host) {
   if (!ctx) return KW_ERR_ARG;
-  if (!ctx->rowptr && !ctx->mv_fn) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: no operator (kw_set_csr or kw_set_matvec)");
+  if (!has_operator(ctx)) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: no operator has been set");
   if (!r_dev || !q_dev || !t_host) return fail(ctx, KW_ERR_ARG, "kw_spmv_dot: NULL pointer");
   kw_status ts = tune_spmv(ctx);
   if (ts != KW_OK) return ts;

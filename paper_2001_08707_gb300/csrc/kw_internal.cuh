@@ -52,6 +52,10 @@ struct State {
 };
 
 enum Prec { PREC_F64 = 0, PREC_C32 = 1, PREC_DF = 2 };
+enum OpKind { OP_CSR = 0, OP_CALLBACK = 1, OP_SPIN = 2, OP_LATTICE = 3 };
+// Binomial table of the spin operator: C(n, k) for n < KW_BINOM_N, k < KW_BINOM_K.
+constexpr int KW_BINOM_N = 32;
+constexpr int KW_BINOM_K = 34;
 
 // Device buffers of one solve.  Vector buffers are void* and typed by precision.
 struct Work {
@@ -105,6 +109,17 @@ struct Work {
   int* list;
   void* X;           // full mode [K][m]
   void* P;           // full mode [K][m]
+  // operator kind: CSR arrays (spmv_lanes picks the layout), callback, or generated on the fly
+  int op = 0;             // OP_CSR, OP_CALLBACK, OP_SPIN, OP_LATTICE
+  // spin operator (kw_set_spin_operator); diagonal in u_diag/u_kind, uniform J/2 in u_v
+  const unsigned* sp_basis = nullptr;   // [m] basis words, increasing
+  const int* sp_binom = nullptr;        // [KW_BINOM_N][KW_BINOM_K] binomial coefficients
+  const int* sp_bond = nullptr;         // [nbond] a | (c << 8), a < c
+  const void* sp_val = nullptr;         // [nbond] J_b/2 in the diagonal's storage (when not uniform)
+  int sp_nbond = 0;
+  int sp_uniform = 0;                   // every J_b equal: one value u_v
+  // lattice operator (kw_set_lattice3d): eps in u_diag/u_kind, hopping in u_v
+  int lx = 0, ly = 0, lz = 0;
   // operator given as a callback (kw_set_matvec) instead of the CSR arrays
   kw_matvec_fn mv_fn = nullptr;
   void* mv_user = nullptr;
@@ -149,6 +164,11 @@ cudaError_t launch_sell_order(int m, const int64_t* rowptr, int* perm, int* rlen
 template <class RV>
 cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,
                              const int* col, const void* val, int* scol, void* sval, cudaStream_t s);
+
+// Spin operator set-up: binomial table, basis words of rank 0..m-1 (nsite bits,
+// nup set), and the FP64 diagonal (bond terms +-J/4, field terms +-h/2).
+cudaError_t launch_spin_setup(int m, int nsite, int nup, int nbond, const int* bond, const double* J, const double* h,
+                              int* binom, unsigned* basis, double* diag, cudaStream_t s);
 
 // Batched solves: count of instances whose solve has stopped (written to *out).
 cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_t s);

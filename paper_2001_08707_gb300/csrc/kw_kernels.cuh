@@ -416,6 +416,162 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
   spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
 }
 
+// Shared tail of the generated-operator K1 kernels: q = z_s r - H r for one
+// row, the lazy seed-switch scale, the store and the r^T q partial.
+template <class V, class A>
+__device__ __forceinline__ void k1_emit(int row, V ri, V hr, V zsv, bool scaled, V scv, V* __restrict__ q,
+                                        A& c_re, A& c_im) {
+  V qi = csub(cmul(zsv, ri), hr);
+  if (scaled) {
+    qi = cmul(scv, qi);
+    ri = cmul(scv, ri);
+  }
+  q[row] = qi;
+  acc_cplx(c_re, c_im, cmul(ri, qi));
+}
+
+// Seed shift and pending scale of K1 (inside the solve or standalone).
+template <class V>
+__device__ __forceinline__ bool k1_scalars(const State* st, const SpmvMode& mode, V& zsv, V& scv, bool& scaled) {
+  scaled = false;
+  scv = vzero<V>();
+  if (mode.solver) {
+    if (st->done) return false;
+    zsv = vscalar<V>(st->zs, st->p_zs);
+    if (st->vec_scale_pending) {
+      scv = vscalar<V>(st->scale_rn, st->p_s1);
+      scaled = true;
+    }
+  } else {
+    zsv = vscalar<V>(mode.zs, mode.zs_pair);
+  }
+  return true;
+}
+
+// K1 for a spin-1/2 operator generated on the fly (kw_set_spin_operator).  One
+// thread per basis word s (row = its rank).  For every bond (a, c), a < c, whose
+// spins differ, the exchanged word s' is s with the up spin moved across the
+// bond; its rank follows from the combinatorial number system without a
+// search: moving the set bit of index t (t set bits below a) from a up to c
+// past m set bits q_1 < .. < q_m lying between them changes the rank by
+//   C(c, t+m+1) - C(a, t+1) + sum_u [C(q_u, t+u) - C(q_u, t+u+1)],
+// added when the up spin sits at a and subtracted when it sits at c.  All
+// lanes of a warp visit bond b together, so the gathers of 32 neighbouring
+// words land close together.  UNI: every J_b equal (sum first, scale once).
+template <int P, class DV, bool UNI>
+__global__ void __launch_bounds__(256)
+k_spmv_spin(int m, const unsigned* __restrict__ basis, const int* __restrict__ binom_g,
+            const int* __restrict__ bond_g, const DV* __restrict__ val_g, int nbond, const DV* __restrict__ diag,
+            DV uv, const typename PT<P>::V* __restrict__ r, typename PT<P>::V* __restrict__ q, State* st,
+            double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  __shared__ int binom[KW_BINOM_N * KW_BINOM_K];
+  __shared__ int bond[KW_SPIN_MAX_BONDS];
+  __shared__ DV bval[UNI ? 1 : KW_SPIN_MAX_BONDS];
+  for (int i = threadIdx.x; i < KW_BINOM_N * KW_BINOM_K; i += blockDim.x) binom[i] = binom_g[i];
+  for (int i = threadIdx.x; i < nbond; i += blockDim.x) {
+    bond[i] = bond_g[i];
+    if constexpr (!UNI) bval[i] = val_g[i];
+  }
+  __syncthreads();
+  V zsv, scv;
+  bool scaled;
+  if (!k1_scalars<V>(st, mode, zsv, scv, scaled)) return;
+  const int lane = threadIdx.x & 31;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < m; base += stride) {   // uniform trip count per warp
+    const int row = base + (int)threadIdx.x;
+    if (row < m) {
+      const unsigned sw = basis[row];
+      V sum = vzero<V>();
+      for (int b = 0; b < nbond; ++b) {
+        const int a = bond[b] & 255, c = bond[b] >> 8;
+        if ((((sw >> a) ^ (sw >> c)) & 1u) == 0) continue;   // parallel spins: no exchange
+        const int t = __popc(sw & ((1u << a) - 1u));
+        unsigned mid = sw & ((1u << c) - 1u) & ~((2u << a) - 1u);   // set bits strictly between a and c
+        const int mc = __popc(mid);
+        int d = binom[c * KW_BINOM_K + t + mc + 1] - binom[a * KW_BINOM_K + t + 1];
+        for (int u = 1; mid; ++u) {
+          const int qb = __ffs(mid) - 1;
+          d += binom[qb * KW_BINOM_K + t + u] - binom[qb * KW_BINOM_K + t + u + 1];
+          mid &= mid - 1u;
+        }
+        const int colx = ((sw >> a) & 1u) ? row + d : row - d;
+        if constexpr (UNI) vacc(sum, r[colx]);
+        else mac(sum, bval[b], r[colx]);
+      }
+      V hr = vzero<V>();
+      const V ri = r[row];
+      mac(hr, diag[row], ri);
+      if constexpr (UNI) mac(hr, uv, normalize(sum));
+      else vacc(hr, normalize(sum));
+      hr = normalize(hr);
+      k1_emit(row, ri, hr, zsv, scaled, scv, q, c_re, c_im);
+    }
+    if (++in_chunk == PT<P>::CHUNK) {
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
+// K1 for the periodic nx x ny x nz tight-binding lattice (kw_set_lattice3d):
+// H r_i = eps_i r_i + hopping * (sum of r over the six neighbours); one thread
+// per site, so the neighbour loads of a warp are contiguous runs.
+template <int P, class DV>
+__global__ void __launch_bounds__(256)
+k_spmv_lattice(int m, int nx, int ny, int nz, const DV* __restrict__ eps, DV hop,
+               const typename PT<P>::V* __restrict__ r, typename PT<P>::V* __restrict__ q, State* st,
+               double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  V zsv, scv;
+  bool scaled;
+  if (!k1_scalars<V>(st, mode, zsv, scv, scaled)) return;
+  const int lane = threadIdx.x & 31;
+  const int nxy = nx * ny;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < m; base += stride) {
+    const int row = base + (int)threadIdx.x;
+    if (row < m) {
+      const int x = row % nx, yz = row / nx, y = yz % ny, z = yz / ny;
+      const int xm = x == 0 ? row + nx - 1 : row - 1, xp = x == nx - 1 ? row - nx + 1 : row + 1;
+      const int ym = y == 0 ? row + nxy - nx : row - nx, yp = y == ny - 1 ? row - nxy + nx : row + nx;
+      const int zm = z == 0 ? row + m - nxy : row - nxy, zp = z == nz - 1 ? row - m + nxy : row + nxy;
+      const V n0 = r[xp], n1 = r[xm], n2 = r[yp], n3 = r[ym], n4 = r[zp], n5 = r[zm];
+      const V ri = r[row];
+      V sum = n0;
+      vacc(sum, n1);
+      vacc(sum, n2);
+      vacc(sum, n3);
+      vacc(sum, n4);
+      vacc(sum, n5);
+      V hr = vzero<V>();
+      mac(hr, eps[row], ri);
+      mac(hr, hop, normalize(sum));
+      hr = normalize(hr);
+      k1_emit(row, ri, hr, zsv, scaled, scv, q, c_re, c_im);
+    }
+    if (++in_chunk == PT<P>::CHUNK) {
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
 // K1 for an operator given as a callback (kw_set_matvec).  The caller's work
 // has left H r in hq (kw_c128 in the FP64 and FP32-pair forms, complex FP32 in
 // the FP32 form; in place in q except in the pair form); this pass forms
@@ -1287,6 +1443,69 @@ static cudaError_t uniform_dispatch(Work& w, const void* r, void* q, SpmvMode mo
   }
 }
 
+template <class DV>
+__host__ __forceinline__ DV dv_from_double(double v) {
+  if constexpr (std::is_same<DV, double>::value) return v;
+  else if constexpr (std::is_same<DV, float>::value) return (float)v;
+  else {
+    DV d;
+    d.hi = (float)v;
+    d.lo = (float)(v - (double)d.hi);
+    return d;
+  }
+}
+
+template <int P, class DV>
+static cudaError_t spin_launch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  const int need = (int)((w.m + 255) / 256);
+  if (w.sp_uniform) {
+    static int nblk = 0;
+    if (nblk == 0) nblk = resident_blocks(k_spmv_spin<P, DV, true>, 256, w.num_sms);
+    k_spmv_spin<P, DV, true><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
+        (int)w.m, w.sp_basis, w.sp_binom, w.sp_bond, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag,
+        dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part, mode);
+  } else {
+    static int nblk = 0;
+    if (nblk == 0) nblk = resident_blocks(k_spmv_spin<P, DV, false>, 256, w.num_sms);
+    k_spmv_spin<P, DV, false><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
+        (int)w.m, w.sp_basis, w.sp_binom, w.sp_bond, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag,
+        dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part, mode);
+  }
+  return cudaGetLastError();
+}
+
+template <int P, class DV>
+static cudaError_t lattice_launch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_spmv_lattice<P, DV>, 256, w.num_sms);
+  const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
+  k_spmv_lattice<P, DV><<<grid, 256, 0, w.stream>>>((int)w.m, w.lx, w.ly, w.lz, (const DV*)w.u_diag,
+                                                   dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part,
+                                                   mode);
+  return cudaGetLastError();
+}
+
+// Generated operators: the diagonal storage kind selects the value type as in
+// the uniform layout (FP64 in the FP64 form unless exact in FP32, FP32 in the
+// FP32 form, FP32 pairs in the pair form unless exact in FP32).
+template <int P>
+static cudaError_t generated_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
+  if (!w.u_diag || (w.op == OP_SPIN && (!w.sp_basis || !w.sp_binom || !w.sp_bond))) return cudaErrorInvalidValue;
+#define KW_GEN(DV) (w.op == OP_SPIN ? spin_launch<P, DV>(w, r, q, mode) : lattice_launch<P, DV>(w, r, q, mode))
+  if constexpr (P == PREC_F64) {
+    if (w.u_kind == 1) return KW_GEN(float);
+    return KW_GEN(double);
+  } else if constexpr (P == PREC_C32) {
+    return KW_GEN(float);
+  } else {
+    if (w.u_kind == 1) return KW_GEN(float);
+    return KW_GEN(df);
+  }
+#undef KW_GEN
+}
+
 // K1 through the caller's matrix-vector callback.
 template <int P>
 static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
@@ -1317,6 +1536,7 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
 template <int P>
 static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
   if (w.mv_fn) return matvec_dispatch<P>(w, r, q, mode);
+  if (w.op == OP_SPIN || w.op == OP_LATTICE) return generated_dispatch<P>(w, r, q, mode);
   if (w.spmv_lanes > KW_SPMV_UNIFORM) return uniform_dispatch<P>(w, r, q, mode);
   if constexpr (P == PREC_F64) {
     if (w.val_f32) return spmv_dispatch_v<P, float>(w, r, q, mode);

@@ -217,6 +217,61 @@ cudaError_t launch_uniform_build(int m, const int64_t* rowptr, const int* col, c
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- spin operator set-up
+static __global__ void k_binom(int* binom) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int n = 0; n < KW_BINOM_N; ++n)
+    for (int k = 0; k < KW_BINOM_K; ++k)
+      binom[n * KW_BINOM_K + k] =
+          k == 0 ? 1 : (n == 0 || k > n) ? 0 : binom[(n - 1) * KW_BINOM_K + k - 1] + binom[(n - 1) * KW_BINOM_K + k];
+}
+
+// Word of rank `row` among the nsite-bit words with nup set bits (increasing
+// order): greedily take, for t = nup .. 1, the highest position p with
+// C(p, t) <= the remaining rank (the combinatorial number system).
+static __global__ void k_spin_basis(int m, int nsite, int nup, const int* __restrict__ binom, unsigned* basis) {
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < m; row += gridDim.x * blockDim.x) {
+    int rem = row;
+    unsigned wd = 0;
+    int p = nsite - 1;
+    for (int t = nup; t >= 1; --t) {
+      while (binom[p * KW_BINOM_K + t] > rem) --p;
+      wd |= 1u << p;
+      rem -= binom[p * KW_BINOM_K + t];
+      --p;
+    }
+    basis[row] = wd;
+  }
+}
+
+static __global__ void k_spin_diag(int m, int nsite, int nbond, const int* __restrict__ bond,
+                                   const double* __restrict__ J, const double* __restrict__ h,
+                                   const unsigned* __restrict__ basis, double* __restrict__ diag) {
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < m; row += gridDim.x * blockDim.x) {
+    const unsigned wd = basis[row];
+    double d = 0.0;
+    for (int b = 0; b < nbond; ++b) {
+      const int a = bond[b] & 255, c = bond[b] >> 8;
+      d += ((((wd >> a) ^ (wd >> c)) & 1u) ? -0.25 : 0.25) * J[b];
+    }
+    if (h)
+      for (int i = 0; i < nsite; ++i) d += (((wd >> i) & 1u) ? 0.5 : -0.5) * h[i];
+    diag[row] = d;
+  }
+}
+
+cudaError_t launch_spin_setup(int m, int nsite, int nup, int nbond, const int* bond, const double* J, const double* h,
+                              int* binom, unsigned* basis, double* diag, cudaStream_t s) {
+  k_binom<<<1, 1, 0, s>>>(binom);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(8192, (m + 255) / 256));
+  k_spin_basis<<<grid, 256, 0, s>>>(m, nsite, nup, binom, basis);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_spin_diag<<<grid, 256, 0, s>>>(m, nsite, nbond, bond, J, h, basis, diag);
+  return cudaGetLastError();
+}
+
 template <int LPS, int NPL>
 static cudaError_t recalc_launch(int K, int np, long long n_iter, const double2* log, const double2* w0,
                                  const double2* z, double thresh, double2* proj, long long* conv_iter,

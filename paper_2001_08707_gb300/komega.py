@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
         "kw_spmv_dot_noalloc": (C.c_int, [I64, I64, P, P, P, kw_c128, P, P, C.POINTER(kw_c128), P]),
         "kw_get_spmv_config": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "kw_set_matvec": (C.c_int, [P, I64, MATVEC_FN, P]),
+        "kw_set_spin_operator": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P]),
+        "kw_set_lattice3d": (C.c_int, [P, I64, I64, I64, P, D]),
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
         "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
@@ -350,6 +352,33 @@ class Solver:
         self._mv_cb = cb                          # the library keeps the pointer
         self._keep = []
         self.m = int(m)
+
+    def set_spin_operator(self, nsite: int, nup: int, bonds, J, h=None):
+        """kw_set_spin_operator: H = sum_b J_b S_i.S_j + sum_i h_i S^z_i on the
+        nsite-bit words with nup up spins, generated on the fly."""
+        bd = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+        Jv = np.ascontiguousarray(np.broadcast_to(np.asarray(J, dtype=np.float64), (bd.shape[0],)))
+        hv = None if h is None else np.ascontiguousarray(np.asarray(h, dtype=np.float64))
+        st = self._lib.kw_set_spin_operator(self._ctx, int(nsite), int(nup), bd.shape[0],
+                                            bd.ctypes.data_as(C.c_void_p), Jv.ctypes.data_as(C.c_void_p),
+                                            None if hv is None else hv.ctypes.data_as(C.c_void_p))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_spin_operator")
+        from math import comb
+
+        self._keep = []
+        self.m = comb(int(nsite), int(nup))
+
+    def set_lattice3d(self, nx: int, ny: int, nz: int, eps, hopping: float = -1.0):
+        """kw_set_lattice3d: periodic nearest-neighbour lattice, H_ii = eps_i,
+        H_ij = hopping, generated on the fly (site i = x + nx (y + ny z))."""
+        ed = self._dev(eps, self._torch.float64)
+        st = self._lib.kw_set_lattice3d(self._ctx, int(nx), int(ny), int(nz), C.c_void_p(ed.data_ptr()),
+                                        float(hopping))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_lattice3d")
+        self._keep = []
+        self.m = int(nx) * int(ny) * int(nz)
 
     def set_krylov_log(self, max_iters: int):
         """Record the Krylov log (at most max_iters rows) in the next solves; 0 = off."""
