@@ -325,6 +325,14 @@ typedef struct {
  * the context stream (0 turns it off; the default).  Errors: KW_ERR_ARG. */
 kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
 
+/* Schedule of an iteration.  on = 1 (the default): the shift scalars of
+ * iteration n (and the full-mode x/p update) run on a second stream while the
+ * product of iteration n+1 runs, since neither needs the other's results (a
+ * seed switch reaches that product through the next three-term update, by
+ * linearity); on = 0: one stream, in the order K2(n), K1(n+1), K3(n), K4(n).
+ * Both give the same numbers.  Errors: KW_ERR_ARG. */
+kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
+
 /* Configuration of the sparse product kernel.  lanes = threads per matrix
  * row of the CSR kernel (1, 2, 4, 8 or 16), or 32 = the SELL-32 layout (an
  * internal sliced-ELLPACK copy: rows sorted by length within windows of 1024

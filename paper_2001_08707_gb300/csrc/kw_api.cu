@@ -102,7 +102,12 @@ struct kw_ctx {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   // kernel timing: one sampled iteration per chunk, two chunks in flight
   int64_t timing_every = 0;
-  cudaEvent_t kev[2][5] = {};
+  cudaEvent_t kev[2][6] = {};
+  // second stream of a solve (shift scalars and x/p update) and its ordering events
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr;
+  DBuf part_k1;   // K1's block partials (K1 overlaps K3, which uses part)
+  int overlap = 1;
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -208,7 +213,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->sell_slen, &ctx->sell_ptr, &ctx->sell_col, &ctx->sell_val, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
-                  &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->st, &ctx->projx, &ctx->tdot,
+                  &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->part_k1, &ctx->st, &ctx->projx, &ctx->tdot,
                   &ctx->mv_r, &ctx->mv_q, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
@@ -224,9 +229,12 @@ void kw_destroy(kw_ctx* ctx) {
   if (ctx->flags_host) cudaFreeHost(ctx->flags_host);
   for (int i = 0; i < 2; ++i) {
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-    for (int j = 0; j < 5; ++j)
+    for (int j = 0; j < 6; ++j)
       if (ctx->kev[i][j]) cudaEventDestroy(ctx->kev[i][j]);
   }
+  if (ctx->ev_k2) cudaEventDestroy(ctx->ev_k2);
+  if (ctx->ev_k3) cudaEventDestroy(ctx->ev_k3);
+  if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
   delete ctx;
 }
 
@@ -460,6 +468,7 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
     w.ly = ctx->ly;
     w.lz = ctx->lz;
   }
+  w.part_k1 = (double*)ctx->part_k1.p;
   w.mv_fn = ctx->mv_fn;
   w.mv_user = ctx->mv_user;
   w.mv_r = ctx->mv_r.p;
@@ -475,6 +484,7 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.stream = ctx->stream;
   w.num_sms = ctx->num_sms;
   w.part = (double*)ctx->part.p;
+  w.part_k1 = (double*)ctx->part_k1.p;
   w.st = (kw::State*)ctx->st.p;
 }
 
@@ -589,7 +599,7 @@ static kw_status ensure_mv_buffers(kw_ctx* ctx) {
 }
 
 static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 zs, double2* t) {
-  if (!w.st || !w.part || !t || (!w.rowptr && !w.mv_fn && w.op < kw::OP_SPIN))
+  if (!w.st || !w.part_k1 || !t || (!w.rowptr && !w.mv_fn && w.op < kw::OP_SPIN))
     return cudaErrorInvalidValue;   // workspace and operator must exist
   const float4 zp = host_pair(zs.x, zs.y);
   switch (w.prec) {
@@ -637,7 +647,7 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   const size_t vs = vec_bytes(p);
   KW_CUDA(ctx->rA.ensure(ctx->m * vs), "tune alloc");
   KW_CUDA(ctx->q.ensure(ctx->m * vs), "tune alloc");
-  KW_CUDA(ctx->part.ensure(part_doubles(ctx, 1) * 8), "tune alloc");
+  KW_CUDA(ctx->part_k1.ensure(part_doubles(ctx, 1) * 8), "tune alloc");
   KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "tune alloc");
   KW_CUDA(ctx->tdot.ensure(16), "tune alloc");
   KW_CUDA(cudaMemsetAsync(ctx->rA.p, 0, ctx->m * vs, ctx->stream), "tune memset");
@@ -747,6 +757,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->list, Ks * 4},
       {&ctx->P, w.full ? Ks * Ms * vs : 16},
       {&ctx->part, part_d * 8},
+      {&ctx->part_k1, part_d * 8},
       {&ctx->st, sizeof(kw::State)},
       {&ctx->projx, Ks * w.nout * 16},
   };
@@ -779,12 +790,26 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.X = x_out_dev;
   w.P = ctx->P.p;
   w.part = (double*)ctx->part.p;
+  w.part_k1 = (double*)ctx->part_k1.p;
   w.st = (kw::State*)ctx->st.p;
+  if (!ctx->stream2) {   // highest priority: K3's few blocks are placed before the concurrent K1's
+    int lo = 0, hi = 0;
+    KW_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+    KW_CUDA(cudaStreamCreateWithPriority(&ctx->stream2, cudaStreamNonBlocking, hi), "second stream");
+  }
+  if (!ctx->ev_k2) KW_CUDA(cudaEventCreateWithFlags(&ctx->ev_k2, cudaEventDisableTiming), "stream events");
+  if (!ctx->ev_k3) KW_CUDA(cudaEventCreateWithFlags(&ctx->ev_k3, cudaEventDisableTiming), "stream events");
+  w.stream2 = ctx->stream2;
+  w.ev_k2 = ctx->ev_k2;
+  w.ev_k3 = ctx->ev_k3;
+  w.overlap = ctx->overlap;
 
   KW_CUDA(cudaMemcpyAsync(w.z, z_host, K * 16, cudaMemcpyHostToDevice, ctx->stream), "upload shifts");
   kw::State& s = *ctx->st_host;
   memset(&s, 0, sizeof(s));
   s.zs = make_double2(z_host[0].re, z_host[0].im);
+  s.zs_k1 = s.zs;
+  s.p_zs_k1 = host_pair(z_host[0].re, z_host[0].im);
   s.boa = make_double2(0.0, 0.0);
   s.scale_rn = s.scale_rnm1 = make_double2(1.0, 0.0);
   s.p_zs = host_pair(z_host[0].re, z_host[0].im);
@@ -800,12 +825,14 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   return KW_OK;
 }
 
-// Accumulate the sampled kernel times of one chunk (its events are complete).
+// Accumulate the sampled kernel times of one chunk (its events are complete):
+// kernel_ms[0] K1 (ev 1-2), [1] K2 (ev 0-1), [2] K3 (ev 3-4), [3] K4 (ev 4-5).
 static void collect_times(kw_ctx* ctx, int slot, bool full) {
+  static const int from[4] = {1, 0, 3, 4}, to[4] = {2, 1, 4, 5};
   float ms[4] = {0, 0, 0, 0};
   for (int i = 0; i < 4; ++i) {
     if (i == 3 && !full) break;
-    if (cudaEventElapsedTime(&ms[i], ctx->kev[slot][i], ctx->kev[slot][i + 1]) != cudaSuccess) return;
+    if (cudaEventElapsedTime(&ms[i], ctx->kev[slot][from[i]], ctx->kev[slot][to[i]]) != cudaSuccess) return;
   }
   for (int i = 0; i < 4; ++i) ctx->stats.kernel_ms[i] += ms[i];
   ctx->stats.timed_iters += 1;
@@ -819,11 +846,11 @@ static cudaError_t init_launch(kw::Work& w) {
   }
 }
 
-static cudaError_t iteration_launch(kw::Work& w, int parity, cudaEvent_t* ev, int64_t* launches) {
+static cudaError_t iteration_launch(kw::Work& w, int parity, int first, cudaEvent_t* ev, int64_t* launches) {
   switch (w.prec) {
-    case kw::PREC_C32: return kw::launch_iteration<kw::PREC_C32>(w, parity, ev, launches);
-    case kw::PREC_DF: return kw::launch_iteration<kw::PREC_DF>(w, parity, ev, launches);
-    default: return kw::launch_iteration<kw::PREC_F64>(w, parity, ev, launches);
+    case kw::PREC_C32: return kw::launch_iteration<kw::PREC_C32>(w, parity, first, ev, launches);
+    case kw::PREC_DF: return kw::launch_iteration<kw::PREC_DF>(w, parity, first, ev, launches);
+    default: return kw::launch_iteration<kw::PREC_F64>(w, parity, first, ev, launches);
   }
 }
 
@@ -847,8 +874,15 @@ static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, c
   s = prepare(ctx, ctx->work, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
   if (s != KW_OK) return s;
   ctx->work_K = nshift;
-  KW_CUDA(init_launch(ctx->work), "init kernels");
-  ctx->stats.launches += ctx->work.full ? 5 : 4;
+  cudaError_t ie = init_launch(ctx->work);   // ends with the first K1, which may call the callback
+  if (ie != cudaSuccess) {
+    if (ctx->work.mv_failed) {
+      cudaStreamSynchronize(ctx->stream);
+      return fail(ctx, KW_ERR_CALLBACK, "kw_solve: the matrix-vector callback returned nonzero");
+    }
+    return cuda_fail(ctx, ie, "init kernels");
+  }
+  ctx->stats.launches += ctx->work.full ? 6 : 5;
   return KW_OK;
 }
 
@@ -871,7 +905,7 @@ static kw_status run_loop(kw_ctx* ctx) {
         ev = ctx->kev[slot];
         sampled_at[slot] = launched;
       }
-      cudaError_t le = iteration_launch(w, (int)(launched & 1), ev, &ctx->stats.launches);
+      cudaError_t le = iteration_launch(w, (int)(launched & 1), i == 0, ev, &ctx->stats.launches);
       if (le != cudaSuccess) {
         if (w.mv_failed) {
           cudaStreamSynchronize(ctx->stream);   // let the iterations already enqueued finish
@@ -881,6 +915,7 @@ static kw_status run_loop(kw_ctx* ctx) {
       }
       ++launched;
     }
+    KW_CUDA(kw::join_streams(w), "join streams");
     KW_CUDA(cudaMemcpyAsync(ctx->flags_host + slot, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
             "flag copy");
     KW_CUDA(cudaEventRecord(ctx->ev[slot], ctx->stream), "event record");
@@ -1040,7 +1075,9 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     kw_ctx* c = ctx->children[i];
     ce = cudaStreamWaitEvent(c->stream, ev[n], 0);
     int64_t dummy = 0;
-    for (int it = 0; it < kChunk && ce == cudaSuccess; ++it) ce = iteration_launch(c->work, it & 1, nullptr, &dummy);
+    for (int it = 0; it < kChunk && ce == cudaSuccess; ++it)
+      ce = iteration_launch(c->work, it & 1, it == 0, nullptr, &dummy);
+    if (ce == cudaSuccess) ce = kw::join_streams(c->work);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[i], c->stream);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(bs, ev[i], 0);
     c->stats.launches += 0;
@@ -1075,7 +1112,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   if (ce != cudaSuccess) return cuda_fail(ctx, ce, "kw_solve_batched: graph launch");
   for (int64_t i = 0; i < n; ++i) {
     kw_ctx* c = ctx->children[i];
-    c->stats.launches += launches * kChunk * (c->work.full ? 4 : 3);
+    c->stats.launches += launches * kChunk * (c->work.full ? 4 : 3);   // per iteration: K2, K1, K3 (+K4)
     kw_status s = solve_end(c, inst[i].proj_out_host, info ? &info[i] : nullptr);
     if (s != KW_OK && result == KW_OK) {
       result = s;
@@ -1287,11 +1324,17 @@ kw_status kw_recalc(kw_ctx* ctx, int64_t n_iter, int64_t nproj, double thresh, c
   return st;
 }
 
+kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return KW_ERR_ARG;
+  ctx->overlap = on;
+  return KW_OK;
+}
+
 kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every) {
   if (!ctx || every < 0) return KW_ERR_ARG;
   if (every > 0 && !ctx->kev[0][0]) {
     for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 5; ++j) KW_CUDA(cudaEventCreate(&ctx->kev[i][j]), "kernel timing events");
+      for (int j = 0; j < 6; ++j) KW_CUDA(cudaEventCreate(&ctx->kev[i][j]), "kernel timing events");
   }
   ctx->timing_every = every;
   return KW_OK;
@@ -1335,7 +1378,7 @@ kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, k
   if (ts != KW_OK) return ts;
   ts = ensure_mv_buffers(ctx);
   if (ts != KW_OK) return ts;
-  KW_CUDA(ctx->part.ensure(part_doubles(ctx, 1) * 8), "alloc partials");
+  KW_CUDA(ctx->part_k1.ensure(part_doubles(ctx, 1) * 8), "alloc partials");
   KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "alloc state");
   KW_CUDA(ctx->tdot.ensure(16), "alloc dot");
   kw::Work w;

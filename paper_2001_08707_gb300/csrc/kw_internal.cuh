@@ -20,14 +20,22 @@ struct State {
   double2 c;         // alpha_n beta_{n-1} / alpha_{n-1}
   double2 beta;      // beta_n = rho_{n+1} / rho_n
   double2 t;         // r_n^T A r_n
+  double2 u;         // K1's r^T (z r - H r) for its seed zs_k1, before any pending seed switch
+  double2 zs_k1;     // the seed shift K1 uses: the one current when the previous K2 ended
+  float4 p_zs_k1;    // its FP32-pair image
+  // Scalars of Eq. 17 formed by K1's last block for the case that the seed is
+  // kept (K2 uses them unless a seed switch is pending)
+  double2 k1_alpha, k1_c, k1_inv_rho, k1_inv_rho_alpha, k1_t;
+  int k1_status;     // 0, KW_ERR_BREAKDOWN or KW_ERR_NONFINITE
+  int pad2;
   double2 inv_rho;   // 1 / rho_n
   double2 inv_rho_alpha;  // 1 / (rho_n alpha_n)
   double nu;         // ||r_{n+1}||_2^2
   double thresh;     // tol * ||b||
   double norm_b;
   // Lazy seed switch: the stored r_n / r_{n-1} are still in the old seed's
-  // normalisation; the next K1/K2 multiply them by these factors and K2 writes
-  // the rescaled r_n back.
+  // normalisation; the next K2 multiplies them by these factors, writes the
+  // rescaled r_n back and corrects K1's q and r^T q by linearity.
   double2 scale_rn, scale_rnm1;
   double2 inv_pj1, inv_pj0;  // 1/pi^j_{n+1}, 1/pi^j_n for the lazy pi rescale in K3
   // FP32-pair images (re.hi, re.lo, im.hi, im.lo) of the scalars the vector
@@ -129,16 +137,27 @@ struct Work {
   // Krylov log for recalculation (NULL = off): rows [log_max][KW_LOG_FIXED + nproj]
   double2* log = nullptr;
   long long log_max = 0;
-  // reduction scratch
+  // reduction scratch (part_k1: K1's own, since K1 overlaps K3)
   double* part;
+  double* part_k1 = nullptr;
+  // second stream for K3/K4 and the events that order the two streams
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr;
+  int overlap = 1;   // 0: K3/K4 on the work stream after K1(n+1), no events
   State* st;
   cudaStream_t stream;
   int num_sms;
 };
 
+// Make the work stream wait for the shift stream (end of a chunk of iterations).
+inline cudaError_t join_streams(Work& w) {
+  return w.overlap ? cudaStreamWaitEvent(w.stream, w.ev_k3, 0) : cudaSuccess;
+}
+
 // Launchers implemented per precision (kw_kernels_f64.cu / kw_kernels_c32.cu).
 template <int P> cudaError_t launch_init(Work& w);
-template <int P> cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* launches);
+// first: the first iteration after launch_init or after join_streams (no wait for K3).
+template <int P> cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, int64_t* launches);
 template <int P> cudaError_t launch_finish_x(Work& w);
 template <int P> cudaError_t launch_project_x(Work& w, double2* out);
 template <int P>

@@ -148,8 +148,8 @@ struct SpmvMode {
   double2* t_out;    // standalone: result
 };
 
-// End of K1 (both layouts): block sum of r^T q, then the last block computes
-// alpha_n and c_n (Eq. 17) or, standalone, returns t.
+// End of K1 (every layout): block sum of r^T q; the last block stores it for
+// the next K2, which forms alpha_n and c_n (Eq. 17), or returns it standalone.
 template <class A>
 __device__ __forceinline__ void spmv_finish(A c_re, A c_im, double t_re, double t_im, int lane, State* st,
                                             double* __restrict__ part, const SpmvMode& mode) {
@@ -172,29 +172,29 @@ __device__ __forceinline__ void spmv_finish(A c_re, A c_im, double t_re, double 
       *mode.t_out = t;
       return;
     }
-    st->t = t;
-    const double2 rho = st->rho, boa = st->boa;
-    // alpha_n = rho_n / (r_n^T A r_n - (beta_{n-1}/alpha_{n-1}) rho_n)   (Eq. 17)
-    const double2 denom = csub(t, cmul(boa, rho));
-    if ((rho.x == 0.0 && rho.y == 0.0) || (denom.x == 0.0 && denom.y == 0.0)) {
-      set_fail(st, KW_ERR_BREAKDOWN);
-      return;
+    st->u = t;
+    // alpha_{n+1} for the case that the concurrent K3 keeps the seed (the next
+    // K2 recomputes it after a switch): rho = rho_{n+1}, beta_n/alpha_n =
+    // rho_{n+1} / (rho_n alpha_n), both from the K2 that produced r_{n+1}
+    const double2 rho = st->rho1, boa = cmul(rho, st->inv_rho_alpha);
+    const double2 denom = csub(t, cmul(boa, rho));   // Eq. 17
+    int status = ((rho.x == 0.0 && rho.y == 0.0) || (denom.x == 0.0 && denom.y == 0.0)) ? KW_ERR_BREAKDOWN : 0;
+    double2 alpha = make_double2(0.0, 0.0), c = alpha, inv_rho = alpha;
+    if (!status) {
+      inv_rho = crecip(rho);
+      alpha = cmul(rho, crecip(denom));
+      c = cmul(alpha, boa);
+      if (!cfinite(alpha) || !cfinite(c)) status = KW_ERR_NONFINITE;
     }
-    const double2 inv_denom = crecip(denom), inv_rho = crecip(rho);
-    const double2 alpha = cmul(rho, inv_denom);
-    const double2 c = cmul(alpha, boa);
-    if (!cfinite(alpha) || !cfinite(c)) {
-      set_fail(st, KW_ERR_NONFINITE);
-      return;
-    }
-    st->alpha = alpha;
-    st->c = c;
-    st->inv_rho = inv_rho;                                    // beta_n = rho_{n+1} / rho_n in K2
-    st->inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));  // 1/(rho_n alpha_n): beta_n/alpha_n in K3
+    st->k1_status = status;
+    st->k1_alpha = alpha;
+    st->k1_c = c;
+    st->k1_inv_rho = inv_rho;
+    st->k1_inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));
+    st->k1_t = t;
     st->p_alpha = pair_of(alpha);
     st->p_c = pair_of(c);
     st->p_opc = pair_of(make_double2(1.0 + c.x, c.y));
-    st->n_list = 0;
   }
 }
 
@@ -205,15 +205,10 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
            typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::A A;
-  V zsv, scv = vzero<V>();
-  bool scaled = false;
+  V zsv;
   if (mode.solver) {
     if (st->done) return;
-    zsv = vscalar<V>(st->zs, st->p_zs);
-    if (st->vec_scale_pending) {
-      scv = vscalar<V>(st->scale_rn, st->p_s1);
-      scaled = true;
-    }
+    zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -252,10 +247,6 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       acc = normalize(acc);
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
-      if (scaled) {                           // lazy seed switch: r <- s r, q <- s q
-        qi = cmul(scv, qi);
-        ri = cmul(scv, ri);
-      }
       q[row] = qi;
       acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
@@ -281,15 +272,10 @@ k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restri
             double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::A A;
-  V zsv, scv = vzero<V>();
-  bool scaled = false;
+  V zsv;
   if (mode.solver) {
     if (st->done) return;
-    zsv = vscalar<V>(st->zs, st->p_zs);
-    if (st->vec_scale_pending) {
-      scv = vscalar<V>(st->scale_rn, st->p_s1);
-      scaled = true;
-    }
+    zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -320,10 +306,6 @@ k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restri
       acc = normalize(acc);
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
-      if (scaled) {
-        qi = cmul(scv, qi);
-        ri = cmul(scv, ri);
-      }
       q[row] = qi;
       acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
@@ -349,15 +331,10 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
          double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::A A;
-  V zsv, scv = vzero<V>();
-  bool scaled = false;
+  V zsv;
   if (mode.solver) {
     if (st->done) return;
-    zsv = vscalar<V>(st->zs, st->p_zs);
-    if (st->vec_scale_pending) {
-      scv = vscalar<V>(st->scale_rn, st->p_s1);
-      scaled = true;
-    }
+    zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -399,10 +376,6 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
       mac(hr, uv, sum);
       hr = normalize(hr);
       V qi = csub(cmul(zsv, ri), hr);         // z_s r - H r
-      if (scaled) {                           // lazy seed switch: r <- s r, q <- s q
-        qi = cmul(scv, qi);
-        ri = cmul(scv, ri);
-      }
       q[row] = qi;
       acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
@@ -417,31 +390,21 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
 }
 
 // Shared tail of the generated-operator K1 kernels: q = z_s r - H r for one
-// row, the lazy seed-switch scale, the store and the r^T q partial.
+// row, the store and the r^T q partial.
 template <class V, class A>
-__device__ __forceinline__ void k1_emit(int row, V ri, V hr, V zsv, bool scaled, V scv, V* __restrict__ q,
-                                        A& c_re, A& c_im) {
-  V qi = csub(cmul(zsv, ri), hr);
-  if (scaled) {
-    qi = cmul(scv, qi);
-    ri = cmul(scv, ri);
-  }
+__device__ __forceinline__ void k1_emit(int row, V ri, V hr, V zsv, V* __restrict__ q, A& c_re, A& c_im) {
+  const V qi = csub(cmul(zsv, ri), hr);
   q[row] = qi;
   acc_cplx(c_re, c_im, cmul(ri, qi));
 }
 
-// Seed shift and pending scale of K1 (inside the solve or standalone).
+// Seed shift of K1 (inside the solve: the one current when the previous K2
+// ended; standalone: the caller's).  False when the solve has stopped.
 template <class V>
-__device__ __forceinline__ bool k1_scalars(const State* st, const SpmvMode& mode, V& zsv, V& scv, bool& scaled) {
-  scaled = false;
-  scv = vzero<V>();
+__device__ __forceinline__ bool k1_seed(const State* st, const SpmvMode& mode, V& zsv) {
   if (mode.solver) {
     if (st->done) return false;
-    zsv = vscalar<V>(st->zs, st->p_zs);
-    if (st->vec_scale_pending) {
-      scv = vscalar<V>(st->scale_rn, st->p_s1);
-      scaled = true;
-    }
+    zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -475,9 +438,8 @@ k_spmv_spin(int m, const unsigned* __restrict__ basis, const int* __restrict__ b
     if constexpr (!UNI) bval[i] = val_g[i];
   }
   __syncthreads();
-  V zsv, scv;
-  bool scaled;
-  if (!k1_scalars<V>(st, mode, zsv, scv, scaled)) return;
+  V zsv;
+  if (!k1_seed<V>(st, mode, zsv)) return;
   const int lane = threadIdx.x & 31;
   A c_re = azero<A>(), c_im = azero<A>();
   double t_re = 0, t_im = 0;
@@ -510,7 +472,7 @@ k_spmv_spin(int m, const unsigned* __restrict__ basis, const int* __restrict__ b
       if constexpr (UNI) mac(hr, uv, normalize(sum));
       else vacc(hr, normalize(sum));
       hr = normalize(hr);
-      k1_emit(row, ri, hr, zsv, scaled, scv, q, c_re, c_im);
+      k1_emit(row, ri, hr, zsv, q, c_re, c_im);
     }
     if (++in_chunk == PT<P>::CHUNK) {
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -532,9 +494,8 @@ k_spmv_lattice(int m, int nx, int ny, int nz, const DV* __restrict__ eps, DV hop
                double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::A A;
-  V zsv, scv;
-  bool scaled;
-  if (!k1_scalars<V>(st, mode, zsv, scv, scaled)) return;
+  V zsv;
+  if (!k1_seed<V>(st, mode, zsv)) return;
   const int lane = threadIdx.x & 31;
   const int nxy = nx * ny;
   A c_re = azero<A>(), c_im = azero<A>();
@@ -560,7 +521,7 @@ k_spmv_lattice(int m, int nx, int ny, int nz, const DV* __restrict__ eps, DV hop
       mac(hr, eps[row], ri);
       mac(hr, hop, normalize(sum));
       hr = normalize(hr);
-      k1_emit(row, ri, hr, zsv, scaled, scv, q, c_re, c_im);
+      k1_emit(row, ri, hr, zsv, q, c_re, c_im);
     }
     if (++in_chunk == PT<P>::CHUNK) {
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -591,15 +552,10 @@ k_matvec_finish(int m, const typename PT<P>::V* r, const typename MvT<P>::H* hq,
                 double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::A A;
-  V zsv, scv = vzero<V>();
-  bool scaled = false;
+  V zsv;
   if (mode.solver) {
     if (st->done) return;
-    zsv = vscalar<V>(st->zs, st->p_zs);
-    if (st->vec_scale_pending) {
-      scv = vscalar<V>(st->scale_rn, st->p_s1);
-      scaled = true;
-    }
+    zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -614,10 +570,6 @@ k_matvec_finish(int m, const typename PT<P>::V* r, const typename MvT<P>::H* hq,
     if (row < m) {
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), mv_in(hq[row], (V*)nullptr));   // z_s r - H r
-      if (scaled) {
-        qi = cmul(scv, qi);
-        ri = cmul(scv, ri);
-      }
       q[row] = qi;
       acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
     }
@@ -720,11 +672,83 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
   constexpr int N = 3 + 2 * NP;
   constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
   if (st->done) return;
-  const int pend = st->vec_scale_pending;
-  const V s1 = vscalar<V>(st->scale_rn, st->p_s1), s0 = vscalar<V>(st->scale_rnm1, st->p_s0);
-  const double2 c = st->c;
-  const V opc = vscalar<V>(make_double2(1.0 + c.x, c.y), st->p_opc);
-  const V av = vscalar<V>(st->alpha, st->p_alpha), cv = vscalar<V>(c, st->p_c);
+  // Seed scalars of Eq. 17, formed by every block from K1's r^T q.  K1 ran
+  // concurrently with the previous K3, i.e. before any seed switch that K3
+  // decided (new seed z_j, r_n <- s1 r_n): by linearity the switched product
+  // is q' = s1 (q + dz r) and t' = s1^2 (u + dz rho_raw), dz = z_j - z_K1.
+  __shared__ double2 s_sc[6];   // alpha, c, s1, s0, dz, 1/rho_n
+  __shared__ float4 s_pp[6];    // their FP32-pair images and that of 1 + c
+  __shared__ int s_fail, s_pend;
+  if (threadIdx.x == 0) {
+    const int pend0 = st->vec_scale_pending;
+    const double2 s1d = st->scale_rn, zero = make_double2(0.0, 0.0);
+    double2 alpha, c, inv_rho, inv_rho_alpha, t, dz = zero;
+    float4 pa, pc, popc;
+    int fail = 0;
+    if (!pend0) {              // seed kept: K1's last block already formed the scalars
+      fail = st->k1_status;
+      alpha = st->k1_alpha;
+      c = st->k1_c;
+      inv_rho = st->k1_inv_rho;
+      inv_rho_alpha = st->k1_inv_rho_alpha;
+      t = st->k1_t;
+      pa = st->p_alpha;
+      pc = st->p_c;
+      popc = st->p_opc;
+    } else {
+      dz = csub(st->zs, st->zs_k1);
+      t = cmul(cmul(s1d, s1d), cadd(st->u, cmul(dz, st->rho1)));
+      const double2 rho = st->rho, boa = st->boa;
+      // alpha_n = rho_n / (r_n^T A r_n - (beta_{n-1}/alpha_{n-1}) rho_n)   (Eq. 17)
+      const double2 denom = csub(t, cmul(boa, rho));
+      alpha = c = inv_rho = inv_rho_alpha = zero;
+      if ((rho.x == 0.0 && rho.y == 0.0) || (denom.x == 0.0 && denom.y == 0.0)) {
+        fail = KW_ERR_BREAKDOWN;
+      } else {
+        inv_rho = crecip(rho);
+        alpha = cmul(rho, crecip(denom));
+        c = cmul(alpha, boa);
+        inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));
+        if (!cfinite(alpha) || !cfinite(c)) fail = KW_ERR_NONFINITE;
+      }
+      pa = pair_of(alpha);
+      pc = pair_of(c);
+      popc = pair_of(make_double2(1.0 + c.x, c.y));
+    }
+    s_sc[0] = alpha;
+    s_sc[1] = c;
+    s_sc[2] = s1d;
+    s_sc[3] = st->scale_rnm1;
+    s_sc[4] = dz;
+    s_sc[5] = inv_rho;
+    s_pp[0] = pa;
+    s_pp[1] = pc;
+    s_pp[2] = popc;
+    s_pp[3] = st->p_s1;
+    s_pp[4] = st->p_s0;
+    s_pp[5] = pend0 ? pair_of(dz) : make_float4(0.f, 0.f, 0.f, 0.f);
+    s_fail = fail;
+    s_pend = pend0;
+    if (blockIdx.x == 0) {
+      if (fail) {
+        set_fail(st, fail);
+      } else {
+        st->t = t;
+        st->alpha = alpha;
+        st->c = c;
+        st->inv_rho = inv_rho;                   // beta_n = rho_{n+1} / rho_n below
+        st->inv_rho_alpha = inv_rho_alpha;       // 1/(rho_n alpha_n): beta_n/alpha_n in K3 and the next K1
+        st->n_list = 0;
+      }
+    }
+  }
+  __syncthreads();
+  if (s_fail) return;
+  const int pend = s_pend;
+  const double2 c = s_sc[1];
+  const V s1 = vscalar<V>(s_sc[2], s_pp[3]), s0 = vscalar<V>(s_sc[3], s_pp[4]), dzv = vscalar<V>(s_sc[4], s_pp[5]);
+  const V opc = vscalar<V>(make_double2(1.0 + c.x, c.y), s_pp[2]);
+  const V av = vscalar<V>(s_sc[0], s_pp[0]), cv = vscalar<V>(c, s_pp[1]);
   const int n = 3 + 2 * np;
 
   A chunk[N], tot[N];
@@ -753,9 +777,10 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
       const int i = i0 + u * stride;
-      if (pend) {             // lazy seed switch: bring r_n, r_{n-1} to the new seed
+      if (pend) {             // lazy seed switch: bring r_n, r_{n-1} and q to the new seed
         rn[u] = cmul(s1, rn[u]);
         rm[u] = cmul(s0, rm[u]);
+        qv[u] = cadd(cmul(s1, qv[u]), cmul(dzv, rn[u]));
         if (has[u]) rn_buf[i] = rn[u];
       }
       const V r1 = csub(csub(cmul(opc, rn[u]), cmul(av, qv[u])), cmul(cv, rm[u]));   // zero when !has
@@ -791,8 +816,12 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
   if (threadIdx.x == 0) {
     st->cnt_seed = 0;
     st->vec_scale_pending = 0;
+    st->zs_k1 = st->zs;                                // the seed the next K1 uses
+    st->p_zs_k1 = st->p_zs;
     const double2 rho1 = make_double2(all[0], all[1]);
-    const double2 beta = cmul(rho1, st->inv_rho);      // beta_n = rho_{n+1} / rho_n
+    // beta_n = rho_{n+1} / rho_n, with this block's own 1/rho_n (block 0's copy in
+    // the state was written during this kernel and may not be visible here)
+    const double2 beta = cmul(rho1, s_sc[5]);
     st->rho1 = rho1;
     st->beta = beta;
     st->nu = all[2];
@@ -1271,6 +1300,8 @@ k_init_dots(int m, int np, const double* __restrict__ b, const double* __restric
   if (threadIdx.x == 0) {
     st->cnt_init = 0;
     st->rho = make_double2(all[0], 0.0);
+    st->rho1 = st->rho;             // the first K1 forms alpha_0 from rho1 and inv_rho_alpha = 0 (beta_{-1} = 0)
+    st->inv_rho_alpha = make_double2(0.0, 0.0);
     st->norm_b = sqrt(all[0]);
     st->thresh = tol * st->norm_b;
     if (np > 0) w0[0] = make_double2(all[0], 0.0);
@@ -1365,7 +1396,7 @@ static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   const int need = (int)((w.m * G + 255) / 256);   // no more blocks than rows need
   const int grid = std::max(1, std::min(nblk, need));
   k_spmv_dot<P, RV, G><<<grid, 256, 0, w.stream>>>((int)w.m, w.rowptr, w.col, (const RV*)w.val,
-                                                   (const V*)r, (V*)q, w.st, w.part, mode);
+                                                   (const V*)r, (V*)q, w.st, w.part_k1, mode);
   return cudaGetLastError();
 }
 
@@ -1378,7 +1409,7 @@ static cudaError_t sell_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   const int grid = std::max(1, std::min(nblk, (nslice + 7) / 8));
   k_spmv_sell<P, RV><<<grid, 256, 0, w.stream>>>((int)w.m, nslice, w.sell_perm, w.sell_len, w.sell_ptr,
                                                  w.sell_col, (const RV*)w.sell_val, (const V*)r, (V*)q, w.st,
-                                                 w.part, mode);
+                                                 w.part_k1, mode);
   return cudaGetLastError();
 }
 
@@ -1412,7 +1443,7 @@ static cudaError_t uniform_launch(Work& w, const void* r, void* q, SpmvMode mode
     uv.lo = (float)(w.u_v - (double)uv.hi);
   }
   k_spmv_u<P, DV, G><<<grid, 256, 0, w.stream>>>((int)w.m, w.u_rowptr, w.u_col, (const DV*)w.u_diag, uv,
-                                                 (const V*)r, (V*)q, w.st, w.part, mode);
+                                                 (const V*)r, (V*)q, w.st, w.part_k1, mode);
   return cudaGetLastError();
 }
 
@@ -1464,13 +1495,13 @@ static cudaError_t spin_launch(Work& w, const void* r, void* q, SpmvMode mode) {
     if (nblk == 0) nblk = resident_blocks(k_spmv_spin<P, DV, true>, 256, w.num_sms);
     k_spmv_spin<P, DV, true><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
         (int)w.m, w.sp_basis, w.sp_binom, w.sp_bond, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag,
-        dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part, mode);
+        dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part_k1, mode);
   } else {
     static int nblk = 0;
     if (nblk == 0) nblk = resident_blocks(k_spmv_spin<P, DV, false>, 256, w.num_sms);
     k_spmv_spin<P, DV, false><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
         (int)w.m, w.sp_basis, w.sp_binom, w.sp_bond, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag,
-        dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part, mode);
+        dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part_k1, mode);
   }
   return cudaGetLastError();
 }
@@ -1482,7 +1513,7 @@ static cudaError_t lattice_launch(Work& w, const void* r, void* q, SpmvMode mode
   if (nblk == 0) nblk = resident_blocks(k_spmv_lattice<P, DV>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   k_spmv_lattice<P, DV><<<grid, 256, 0, w.stream>>>((int)w.m, w.lx, w.ly, w.lz, (const DV*)w.u_diag,
-                                                   dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part,
+                                                   dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part_k1,
                                                    mode);
   return cudaGetLastError();
 }
@@ -1529,7 +1560,7 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
   static int nblk = 0;
   if (nblk == 0) nblk = resident_blocks(k_matvec_finish<P>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
-  k_matvec_finish<P><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)r, (const H*)hq, (V*)q, w.st, w.part, mode);
+  k_matvec_finish<P><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)r, (const H*)hq, (V*)q, w.st, w.part_k1, mode);
   return cudaGetLastError();
 }
 
@@ -1572,28 +1603,42 @@ static cudaError_t seed_dispatch(Work& w, void* rn, void* rm) {
   return seed_launch<P, KW_MAX_PROJ>(w, rn, rm);
 }
 
-// One iteration: K1..K4 on the work stream.  If ev is not NULL, ev[0..4] are
-// recorded before K1 and after each kernel (ev[4] after K3 in projected mode).
+// One iteration n on two streams (K1(n) was enqueued by the previous
+// iteration or by launch_init):
+//   stream:  [wait K3(n-1)] K2(n) [record ev_k2] K1(n+1)
+//   stream2: [wait ev_k2] K3(n) K4(n) [record ev_k3]
+// K1(n+1) needs only r_{n+1}; K3(n)/K4(n) need only K2(n)'s scalars and
+// r_{n+1}.  K2(n+1) waits for both; a seed switch decided by K3(n) reaches
+// K1(n+1)'s product through K2(n+1)'s correction.  If ev is not NULL, ev[0..5]
+// are recorded around K2 and K1 (stream) and K3 and K4 (stream2).
 template <int P>
-cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* launches) {
+cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, int64_t* launches) {
   typedef typename PT<P>::V V;
-  if (!w.st || !w.part || !w.rA || !w.rB || !w.q || !w.z || !w.list) return cudaErrorInvalidValue;
+  if (!w.st || !w.part || !w.part_k1 || !w.rA || !w.rB || !w.q || !w.z || !w.list || !w.stream2 || !w.ev_k2 ||
+      !w.ev_k3)
+    return cudaErrorInvalidValue;
   // parity 0: r_n in rA, r_{n-1} in rB; parity 1: swapped.  K2 writes r_{n+1} over r_{n-1}.
   void* rn = parity ? w.rB : w.rA;
   void* rm = parity ? w.rA : w.rB;
   cudaError_t e;
-#define KW_MARK(i) \
-  if (ev && (e = cudaEventRecord(ev[i], w.stream)) != cudaSuccess) return e;
-  KW_MARK(0);
+#define KW_MARK(i, s) \
+  if (ev && (e = cudaEventRecord(ev[i], s)) != cudaSuccess) return e;
+  cudaStream_t s2 = w.overlap ? w.stream2 : w.stream;
+  if (w.overlap && !first && (e = cudaStreamWaitEvent(w.stream, w.ev_k3, 0)) != cudaSuccess) return e;
+  KW_MARK(0, w.stream);
+  if ((e = seed_dispatch<P>(w, rn, rm)) != cudaSuccess) return e;
+  KW_MARK(1, w.stream);
+  if (w.overlap && (e = cudaEventRecord(w.ev_k2, w.stream)) != cudaSuccess) return e;
   SpmvMode mode;
   mode.solver = 1;
   mode.zs = make_double2(0.0, 0.0);
   mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);
   mode.t_out = nullptr;
-  if ((e = spmv_dispatch<P>(w, rn, w.q, mode)) != cudaSuccess) return e;
-  KW_MARK(1);
-  if ((e = seed_dispatch<P>(w, rn, rm)) != cudaSuccess) return e;
-  KW_MARK(2);
+  if ((e = spmv_dispatch<P>(w, rm, w.q, mode)) != cudaSuccess) return e;   // K1(n+1) on r_{n+1}
+  KW_MARK(2, w.stream);
+
+  if (w.overlap && (e = cudaStreamWaitEvent(s2, w.ev_k2, 0)) != cudaSuccess) return e;
+  KW_MARK(3, s2);
   ShiftArgs a;
   a.K = w.K;
   a.np = w.nproj;
@@ -1619,25 +1664,26 @@ cudaError_t launch_iteration(Work& w, int parity, cudaEvent_t* ev, int64_t* laun
   const int spw = 32 / lps;
   const int nb3 = (w.K + spw - 1) / spw;
   switch (lps) {
-    case 1: k_shift<1><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
-    case 2: k_shift<2><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
-    case 4: k_shift<4><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
-    case 8: k_shift<8><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
-    case 16: k_shift<16><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
-    default: k_shift<32><<<nb3, 32, 0, w.stream>>>(a, w.st); break;
+    case 1: k_shift<1><<<nb3, 32, 0, s2>>>(a, w.st); break;
+    case 2: k_shift<2><<<nb3, 32, 0, s2>>>(a, w.st); break;
+    case 4: k_shift<4><<<nb3, 32, 0, s2>>>(a, w.st); break;
+    case 8: k_shift<8><<<nb3, 32, 0, s2>>>(a, w.st); break;
+    case 16: k_shift<16><<<nb3, 32, 0, s2>>>(a, w.st); break;
+    default: k_shift<32><<<nb3, 32, 0, s2>>>(a, w.st); break;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  KW_MARK(3);
+  KW_MARK(4, s2);
   *launches += (w.mv_fn && P == PREC_DF) ? 4 : 3;
   if (w.full) {
     static int nblk_xp = 0;
     if (nblk_xp == 0) nblk_xp = resident_blocks(k_update_xp<P, 8>, 256, w.num_sms);
-    k_update_xp<P, 8><<<nblk_xp, 256, 0, w.stream>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
-                                                     (const V*)rm, w.st);
+    k_update_xp<P, 8><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
+                                                      (const V*)rm, w.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
   }
-  KW_MARK(4);
+  KW_MARK(5, s2);
+  if (w.overlap && (e = cudaEventRecord(w.ev_k3, s2)) != cudaSuccess) return e;
 #undef KW_MARK
   return cudaSuccess;
 }
@@ -1646,7 +1692,8 @@ template <int P>
 cudaError_t launch_init(Work& w) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
-  if (!w.st || !w.part || !w.rA || !w.rB || !w.b || !w.pi1 || !w.w0 || (w.full && (!w.X || !w.P)))
+  if (!w.st || !w.part || !w.part_k1 || !w.rA || !w.rB || !w.q || !w.b || !w.pi1 || !w.w0 ||
+      (w.full && (!w.X || !w.P)))
     return cudaErrorInvalidValue;
   const int nb = 4 * w.num_sms;
   k_init_vectors<P><<<nb, 256, 0, w.stream>>>((int)w.m, w.nproj, w.b, w.left, (V*)w.rA, (V*)w.rB,
@@ -1664,7 +1711,14 @@ cudaError_t launch_init(Work& w) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_init_shifts<<<(w.K + 127) / 128, 128, 0, w.stream>>>(w.K, w.nproj, w.pi1, w.pi0, w.active, w.conv_iter,
                                                         w.final_res, w.Y, w.U, w.w0);
-  return cudaGetLastError();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // K1(0) on r_0 (rA); every iteration then enqueues the next K1 after its K2
+  SpmvMode mode;
+  mode.solver = 1;
+  mode.zs = make_double2(0.0, 0.0);
+  mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);
+  mode.t_out = nullptr;
+  return spmv_dispatch<P>(w, w.rA, w.q, mode);
 }
 
 // Full-mode outputs: FP32-pair vectors are first converted to FP64 in place

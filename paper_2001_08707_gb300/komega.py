@@ -106,6 +106,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_spin_operator": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P]),
         "kw_set_lattice3d": (C.c_int, [P, I64, I64, I64, P, D]),
         "kw_set_krylov_log": (C.c_int, [P, I64]),
+        "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
         "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
         "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
     }
@@ -379,6 +380,13 @@ class Solver:
             raise self._err(st, "kw_set_lattice3d")
         self._keep = []
         self.m = int(nx) * int(ny) * int(nz)
+
+    def set_stream_overlap(self, on: bool):
+        """kw_set_stream_overlap: run the shift scalars of iteration n beside the
+        product of iteration n+1 (True, the default) or on one stream."""
+        st = self._lib.kw_set_stream_overlap(self._ctx, 1 if on else 0)
+        if st != KW_OK:
+            raise self._err(st, "kw_set_stream_overlap")
 
     def set_krylov_log(self, max_iters: int):
         """Record the Krylov log (at most max_iters rows) in the next solves; 0 = off."""

@@ -41,13 +41,16 @@ def _small_batch():
 
 @pytest.mark.parametrize("prec", ["f64", "df64", "c32"])
 def test_batched_equals_individual_solves(prec):
+    """Each instance of the batch ends exactly as its own solve.  (The FP32-vector
+    form stalls on some of these instances and may end in a reported breakdown
+    after thousands of iterations; the batch must then report the same.)"""
     batch = _small_batch()
     s = kw.Solver(prec, maxiter=20000)
-    res = s.solve_batched(batch)
+    res = s.solve_batched(batch, check=prec != "c32")
     for d, r in zip(batch, res):
         one = kw.Solver(prec, maxiter=20000, tol=d["tol"])
         one.set_csr(d["H"].rowptr, d["H"].col, d["H"].val)
-        g = one.solve(d["b"], d["z"], left=d.get("left"), full=d["full"])
+        g = one.solve(d["b"], d["z"], left=d.get("left"), full=d["full"], check=prec != "c32")
         assert r.iters == g.iters and r.status == g.status and r.n_seed_switch == g.n_seed_switch
         np.testing.assert_array_equal(r.proj, g.proj)
         if d["full"]:
