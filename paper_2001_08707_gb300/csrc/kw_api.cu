@@ -811,9 +811,8 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   s.zs_k1 = s.zs;
   s.p_zs_k1 = host_pair(z_host[0].re, z_host[0].im);
   s.boa = make_double2(0.0, 0.0);
-  s.scale_rn = s.scale_rnm1 = make_double2(1.0, 0.0);
+  s.bscale[0] = s.bscale[1] = make_double2(1.0, 0.0);
   s.p_zs = host_pair(z_host[0].re, z_host[0].im);
-  s.p_s1 = s.p_s0 = host_pair(1.0, 0.0);
   s.seed = 0;
   s.seed_switch = ctx->opt.seed_switch ? 1 : 0;
   s.status = KW_NOT_CONVERGED;

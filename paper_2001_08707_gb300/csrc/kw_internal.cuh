@@ -33,15 +33,15 @@ struct State {
   double nu;         // ||r_{n+1}||_2^2
   double thresh;     // tol * ||b||
   double norm_b;
-  // Lazy seed switch: the stored r_n / r_{n-1} are still in the old seed's
-  // normalisation; the next K2 multiplies them by these factors, writes the
-  // rescaled r_n back and corrects K1's q and r^T q by linearity.
-  double2 scale_rn, scale_rnm1;
+  // Seed switch without touching the vectors: bscale[b] is the pending factor
+  // of residual buffer b (0: rA, 1: rB) that K2 folds into its coefficients;
+  // switched: the last K3 switched the seed (K2 then re-forms alpha_n).
+  double2 bscale[2];
   double2 inv_pj1, inv_pj0;  // 1/pi^j_{n+1}, 1/pi^j_n for the lazy pi rescale in K3
   // FP32-pair images (re.hi, re.lo, im.hi, im.lo) of the scalars the vector
   // kernels use, written next to their FP64 values; the FP32 form uses the .hi parts.
-  float4 p_zs, p_alpha, p_c, p_opc, p_s1, p_s0;
-  int vec_scale_pending;
+  float4 p_zs, p_alpha, p_c, p_opc;
+  int switched;
   int pi_rescale_pending;
   int new_seed;
   int seed;

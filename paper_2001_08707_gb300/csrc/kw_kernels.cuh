@@ -106,6 +106,30 @@ __device__ __forceinline__ void block_sum(const T (&v)[N], int n, double* out) {
   __syncthreads();
 }
 
+// FP32-pair form: the same block sum kept in pairs (FP32 pipe) across the
+// warps; out[i] receives the pair.  Converting to FP64 once per value at the
+// very end keeps the FP64 pipe, 1/64 of the FP32 rate on this GPU, out of the
+// reduction.
+template <int N>
+__device__ __forceinline__ void block_sum_df(const df (&v)[N], int n, df* out) {
+  __shared__ df sh[32][N > 0 ? N : 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    if (i < n) {
+      const df s = warp_sum(anorm(v[i]));
+      if (lane == 0) sh[warp][i] = s;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    df s = sh[0][i];
+    for (int k = 1; k < nw; ++k) s = df_add(s, sh[k][i]);
+    out[i] = s;
+  }
+  __syncthreads();
+}
+
 // Arrival counter: true in the one block that finishes last.  Every block's
 // partials are fenced before it arrives, so the last block sees all of them.
 __device__ __forceinline__ bool arrive_last(unsigned int* cnt) {
@@ -663,41 +687,44 @@ __global__ void k_sell_fill(int m, int nslice, const int* __restrict__ perm, con
 // Values per block: [rho.re, rho.im, nu, w_0.re, w_0.im, ..., w_{np-1}.re, w_{np-1}.im]
 template <int P, int NP>
 __global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5) ? 3 : 1)
-k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
+k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
               typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int np,
-              State* st, double* __restrict__ part, double2* __restrict__ w_out) {
+              int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   typedef typename PT<P>::A A;
   constexpr int N = 3 + 2 * NP;
   constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
   if (st->done) return;
-  // Seed scalars of Eq. 17, formed by every block from K1's r^T q.  K1 ran
-  // concurrently with the previous K3, i.e. before any seed switch that K3
-  // decided (new seed z_j, r_n <- s1 r_n): by linearity the switched product
-  // is q' = s1 (q + dz r) and t' = s1^2 (u + dz rho_raw), dz = z_j - z_K1.
-  __shared__ double2 s_sc[6];   // alpha, c, s1, s0, dz, 1/rho_n
-  __shared__ float4 s_pp[6];    // their FP32-pair images and that of 1 + c
-  __shared__ int s_fail, s_pend;
+  // Seed scalars of Eq. 17 and the three coefficients of Eq. 16.  The two
+  // residual buffers carry pending scales (bscale) from seed switches
+  // (Sec. 2.2.4: r_{n+1} <- r_{n+1}/pi^j_{n+1}, r_n <- r_n/pi^j_n), and K1 ran
+  // concurrently with the last K3, i.e. with the seed before its switch
+  // (q_raw = z_K1 r_raw - H r_raw).  With s_n, s_{n-1} the buffers' scales and
+  // dz = z_s - z_K1, by linearity r_n = s_n r_raw, q = s_n (q_raw + dz r_raw),
+  // r_n^T A r_n = s_n^2 (u + dz rho_raw), so that
+  //   r_{n+1} = [s_n (1 + c - alpha dz)] r_raw - [alpha s_n] q_raw - [c s_{n-1}] r_{n-1,raw}:
+  // a switch changes the coefficients, not the per-element work.
+  __shared__ double2 s_sc[2];   // c_n, 1/rho_n
+  __shared__ double2 s_cf[3];   // the three coefficients in FP64
+  __shared__ float4 s_pp[3];    // FP32-pair images of the three coefficients
+  __shared__ int s_fail;
   if (threadIdx.x == 0) {
-    const int pend0 = st->vec_scale_pending;
-    const double2 s1d = st->scale_rn, zero = make_double2(0.0, 0.0);
+    const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
+    const double2 sn = st->bscale[parity], sm = st->bscale[1 - parity];
+    const int switched = st->switched;
     double2 alpha, c, inv_rho, inv_rho_alpha, t, dz = zero;
-    float4 pa, pc, popc;
     int fail = 0;
-    if (!pend0) {              // seed kept: K1's last block already formed the scalars
+    if (!switched) {           // seed kept: K1's last block already formed the scalars
       fail = st->k1_status;
       alpha = st->k1_alpha;
       c = st->k1_c;
       inv_rho = st->k1_inv_rho;
       inv_rho_alpha = st->k1_inv_rho_alpha;
       t = st->k1_t;
-      pa = st->p_alpha;
-      pc = st->p_c;
-      popc = st->p_opc;
     } else {
       dz = csub(st->zs, st->zs_k1);
-      t = cmul(cmul(s1d, s1d), cadd(st->u, cmul(dz, st->rho1)));
+      t = cmul(cmul(sn, sn), cadd(st->u, cmul(dz, st->rho1)));
       const double2 rho = st->rho, boa = st->boa;
       // alpha_n = rho_n / (r_n^T A r_n - (beta_{n-1}/alpha_{n-1}) rho_n)   (Eq. 17)
       const double2 denom = csub(t, cmul(boa, rho));
@@ -711,24 +738,20 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
         inv_rho_alpha = cmul(denom, cmul(inv_rho, inv_rho));
         if (!cfinite(alpha) || !cfinite(c)) fail = KW_ERR_NONFINITE;
       }
-      pa = pair_of(alpha);
-      pc = pair_of(c);
-      popc = pair_of(make_double2(1.0 + c.x, c.y));
     }
-    s_sc[0] = alpha;
-    s_sc[1] = c;
-    s_sc[2] = s1d;
-    s_sc[3] = st->scale_rnm1;
-    s_sc[4] = dz;
-    s_sc[5] = inv_rho;
-    s_pp[0] = pa;
-    s_pp[1] = pc;
-    s_pp[2] = popc;
-    s_pp[3] = st->p_s1;
-    s_pp[4] = st->p_s0;
-    s_pp[5] = pend0 ? pair_of(dz) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool plain = !switched && sn.x == 1.0 && sn.y == 0.0 && sm.x == 1.0 && sm.y == 0.0;
+    if (plain) {               // 1 + c, alpha, c as K1 converted them
+      s_pp[0] = st->p_opc;
+      s_pp[1] = st->p_alpha;
+      s_pp[2] = st->p_c;
+    } else {
+      s_pp[0] = pair_of(cmul(sn, csub(make_double2(1.0 + c.x, c.y), cmul(alpha, dz))));
+      s_pp[1] = pair_of(cmul(alpha, sn));
+      s_pp[2] = pair_of(cmul(c, sm));
+    }
+    s_sc[0] = c;
+    s_sc[1] = inv_rho;
     s_fail = fail;
-    s_pend = pend0;
     if (blockIdx.x == 0) {
       if (fail) {
         set_fail(st, fail);
@@ -741,14 +764,16 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
         st->n_list = 0;
       }
     }
+    // FP64 form: the coefficients themselves (the pair images carry them otherwise)
+    s_cf[0] = plain ? make_double2(1.0 + c.x, c.y) : cmul(sn, csub(make_double2(1.0 + c.x, c.y), cmul(alpha, dz)));
+    s_cf[1] = plain ? alpha : cmul(alpha, sn);
+    s_cf[2] = plain ? c : cmul(c, sm);
   }
   __syncthreads();
   if (s_fail) return;
-  const int pend = s_pend;
-  const double2 c = s_sc[1];
-  const V s1 = vscalar<V>(s_sc[2], s_pp[3]), s0 = vscalar<V>(s_sc[3], s_pp[4]), dzv = vscalar<V>(s_sc[4], s_pp[5]);
-  const V opc = vscalar<V>(make_double2(1.0 + c.x, c.y), s_pp[2]);
-  const V av = vscalar<V>(s_sc[0], s_pp[0]), cv = vscalar<V>(c, s_pp[1]);
+  // the coefficients are re-read from shared memory at each element (the pair
+  // form would otherwise hold 12 more registers through the loop)
+  const volatile float4* vpp = s_pp;
   const int n = 3 + 2 * np;
 
   A chunk[N], tot[N];
@@ -777,13 +802,18 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
 #pragma unroll
     for (int u = 0; u < ILP; ++u) {
       const int i = i0 + u * stride;
-      if (pend) {             // lazy seed switch: bring r_n, r_{n-1} and q to the new seed
-        rn[u] = cmul(s1, rn[u]);
-        rm[u] = cmul(s0, rm[u]);
-        qv[u] = cadd(cmul(s1, qv[u]), cmul(dzv, rn[u]));
-        if (has[u]) rn_buf[i] = rn[u];
+      float4 pa, pb, pc;
+      if constexpr (P == PREC_DF) {
+        pa = make_float4(vpp[0].x, vpp[0].y, vpp[0].z, vpp[0].w);
+        pb = make_float4(vpp[1].x, vpp[1].y, vpp[1].z, vpp[1].w);
+        pc = make_float4(vpp[2].x, vpp[2].y, vpp[2].z, vpp[2].w);
+      } else {
+        pa = s_pp[0];
+        pb = s_pp[1];
+        pc = s_pp[2];
       }
-      const V r1 = csub(csub(cmul(opc, rn[u]), cmul(av, qv[u])), cmul(cv, rm[u]));   // zero when !has
+      const V ca = vscalar<V>(s_cf[0], pa), cb = vscalar<V>(s_cf[1], pb), cc = vscalar<V>(s_cf[2], pc);
+      const V r1 = csub(csub(cmul(ca, rn[u]), cmul(cb, qv[u])), cmul(cc, rm[u]));   // Eq. 16; zero when !has
       if (has[u]) rm_buf[i] = r1;
       acc_rho_nrm(chunk[0], chunk[1], chunk[2], r1);
 #pragma unroll
@@ -805,23 +835,46 @@ k_seed_update(int m, typename PT<P>::V* __restrict__ rn_buf, const typename PT<P
     else tot[k] = chunk[k];
   }
 
-  __shared__ double red[N];
-  block_sum<N, A>(tot, n, red);
-  for (int k = threadIdx.x; k < n; k += blockDim.x) part[(size_t)blockIdx.x * n + k] = red[k];
-  if (!arrive_last(&st->cnt_seed)) return;
-
   __shared__ double all[N];
-  reduce_partials<N>(part, gridDim.x, n, n, all);
+  if constexpr (P == PREC_DF) {
+    // block and grid sums in FP32 pairs (part holds one pair per value)
+    __shared__ df red[N];
+    block_sum_df<N>(tot, n, red);
+    df* partd = reinterpret_cast<df*>(part);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) partd[(size_t)blockIdx.x * n + k] = red[k];
+    if (!arrive_last(&st->cnt_seed)) return;
+    df acc[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) acc[i] = azero<df>();
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i < n) {
+          const float2 v = __ldcg(reinterpret_cast<const float2*>(partd + (size_t)b * n + i));
+          acc[i] = df_add(acc[i], df{v.x, v.y});
+        }
+    }
+    block_sum_df<N>(acc, n, red);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) all[k] = df_to_double(red[k]);
+    __syncthreads();
+  } else {
+    __shared__ double red[N];
+    block_sum<N, A>(tot, n, red);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) part[(size_t)blockIdx.x * n + k] = red[k];
+    if (!arrive_last(&st->cnt_seed)) return;
+    reduce_partials<N>(part, gridDim.x, n, n, all);
+  }
   for (int l = threadIdx.x; l < np; l += blockDim.x) w_out[l] = make_double2(all[3 + 2 * l], all[4 + 2 * l]);
   if (threadIdx.x == 0) {
     st->cnt_seed = 0;
-    st->vec_scale_pending = 0;
+    st->bscale[1 - parity] = make_double2(1.0, 0.0);   // r_{n+1} was just written
+    st->switched = 0;
     st->zs_k1 = st->zs;                                // the seed the next K1 uses
     st->p_zs_k1 = st->p_zs;
     const double2 rho1 = make_double2(all[0], all[1]);
     // beta_n = rho_{n+1} / rho_n, with this block's own 1/rho_n (block 0's copy in
     // the state was written during this kernel and may not be visible here)
-    const double2 beta = cmul(rho1, s_sc[5]);
+    const double2 beta = cmul(rho1, s_sc[1]);
     st->rho1 = rho1;
     st->beta = beta;
     st->nu = all[2];
@@ -1018,12 +1071,13 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   double2 boa = cmul(rho1_in, st->inv_rho_alpha);       // beta_n / alpha_n
   if (do_switch) {                                      // Sec. 2.2.4
     const double2 ii1 = ipj1, ii0 = crecip(pj0);
-    st->scale_rn = ii1;                  // r_{n+1} <- r_{n+1} / pi^j_{n+1}
-    st->scale_rnm1 = ii0;                // r_n     <- r_n / pi^j_n
-    st->p_s1 = pair_of(ii1);
-    st->p_s0 = pair_of(ii0);
+    // r_{n+1} <- r_{n+1} / pi^j_{n+1}, r_n <- r_n / pi^j_n, pending on their
+    // buffers: iteration n (parity n & 1) wrote r_{n+1} into buffer 1 - (n & 1)
+    const int par = (int)(iter & 1);
+    st->bscale[1 - par] = cmul(st->bscale[1 - par], ii1);
+    st->bscale[par] = cmul(st->bscale[par], ii0);
     st->p_zs = pair_of(zj);
-    st->vec_scale_pending = 1;
+    st->switched = 1;
     rho1 = cmul(rho1, cmul(ii1, ii1));   // rho_{n+1} of the rescaled residual
     boa = cmul(boa, cmul(pj0, ii1));     // beta^j_n / alpha^j_n
     st->inv_pj1 = ii1;
@@ -1581,26 +1635,26 @@ static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode)
 }
 
 template <int P, int NP>
-static cudaError_t seed_launch(Work& w, void* rn, void* rm) {
+static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   static int nblk = 0;
   if (nblk == 0) nblk = resident_blocks(k_seed_update<P, NP>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
-  k_seed_update<P, NP><<<grid, 256, 0, w.stream>>>((int)w.m, (V*)rn, (const V*)w.q, (V*)rm,
-                                                   (const R*)w.proj_rows, w.nproj, w.st, w.part, w.w);
+  k_seed_update<P, NP><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)rn, (const V*)w.q, (V*)rm,
+                                                   (const R*)w.proj_rows, w.nproj, parity, w.st, w.part, w.w);
   return cudaGetLastError();
 }
 
 template <int P>
-static cudaError_t seed_dispatch(Work& w, void* rn, void* rm) {
+static cudaError_t seed_dispatch(Work& w, void* rn, void* rm, int parity) {
   const int np = w.nproj;
-  if (np == 0) return seed_launch<P, 0>(w, rn, rm);
-  if (np <= 2) return seed_launch<P, 2>(w, rn, rm);
-  if (np <= 5) return seed_launch<P, 5>(w, rn, rm);
-  if (np <= 9) return seed_launch<P, 9>(w, rn, rm);
-  if (np <= 17) return seed_launch<P, 17>(w, rn, rm);
-  return seed_launch<P, KW_MAX_PROJ>(w, rn, rm);
+  if (np == 0) return seed_launch<P, 0>(w, rn, rm, parity);
+  if (np <= 2) return seed_launch<P, 2>(w, rn, rm, parity);
+  if (np <= 5) return seed_launch<P, 5>(w, rn, rm, parity);
+  if (np <= 9) return seed_launch<P, 9>(w, rn, rm, parity);
+  if (np <= 17) return seed_launch<P, 17>(w, rn, rm, parity);
+  return seed_launch<P, KW_MAX_PROJ>(w, rn, rm, parity);
 }
 
 // One iteration n on two streams (K1(n) was enqueued by the previous
@@ -1626,7 +1680,7 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   cudaStream_t s2 = w.overlap ? w.stream2 : w.stream;
   if (w.overlap && !first && (e = cudaStreamWaitEvent(w.stream, w.ev_k3, 0)) != cudaSuccess) return e;
   KW_MARK(0, w.stream);
-  if ((e = seed_dispatch<P>(w, rn, rm)) != cudaSuccess) return e;
+  if ((e = seed_dispatch<P>(w, rn, rm, parity)) != cudaSuccess) return e;
   KW_MARK(1, w.stream);
   if (w.overlap && (e = cudaEventRecord(w.ev_k2, w.stream)) != cudaSuccess) return e;
   SpmvMode mode;
