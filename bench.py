@@ -395,6 +395,8 @@ def run_ours(args):
                 "spmv_config": list(cfg)}
 
     kernels = {HEADLINE: kern(HEADLINE, h_cfg, h_stats, h_res.iters, t_max)}
+    kernels[HEADLINE]["seed_update_traffic"] = recorded_traffic(f"k_seed_update<{HEADLINE}>:heisenberg_N24")
+    kernels[HEADLINE]["seed_update_bytes"] = seed_bytes(m, PREC_BYTES[HEADLINE][0], PREC_BYTES[HEADLINE][1], nproj)
     A_h = -np.imag(h_res.proj[:, 0]) / np.pi
 
     def compare(res):
