@@ -8,6 +8,8 @@ the Komega paper (arXiv:2001.08707):
 * ``shifted_cocg``: the shifted COCG iteration step by step (Sec. 2.2,
   Appendix A), full and projected modes, seed switching; with ``log=True`` it
   also keeps the per-iteration record used for recalculation.
+* ``shifted_bicg``: the other solvers of Table 1 (Appendix B): shifted BiCG
+  with a shadow residual, and shifted CG for Hermitian A with real shifts.
 * ``recalc``: projections at new shifts replayed from that record without
   matrix-vector products (Sec. 3.3 (iv); Eqs. 20-22, 25-26).
 * ``adjoint``: the gradient of the spectrum with respect to the Hamiltonian's
