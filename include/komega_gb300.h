@@ -123,6 +123,12 @@ kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
 kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev,
                      const int32_t* col_dev, const double* val_dev);
 
+/* Solvers of Table 1: COCG (the default) for complex symmetric A + sigma I
+ * (real symmetric or complex symmetric H, complex shifts); CG for Hermitian
+ * A + sigma I (real symmetric or Hermitian H, real shifts); BiCG otherwise
+ * (Appendix B: a shadow residual driven by A^dagger). */
+typedef enum { KW_METHOD_COCG = 0, KW_METHOD_CG = 1, KW_METHOD_BICG = 2 } kw_method;
+
 /* Element types of the vectors handed to a matrix-vector callback. */
 #define KW_ELEM_C128 0   /* kw_c128 */
 #define KW_ELEM_C64 1    /* complex FP32: {float re, im} */
@@ -324,6 +330,29 @@ typedef struct {
 /* Bracket the kernels of one iteration in every `every` with CUDA events on
  * the context stream (0 turns it off; the default).  Errors: KW_ERR_ARG. */
 kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
+
+/* Select the solver of Table 1 for the next solves of ctx (kw_solve,
+ * kw_solve_host, kw_solve_batched):
+ *   KW_METHOD_COCG (default): unconjugated inner products (Appendix A).
+ *   KW_METHOD_CG: conjugated inner products, rho = ||r||^2; for Hermitian
+ *     A + sigma I, i.e. a real symmetric or Hermitian H (Hermitian through
+ *     kw_set_matvec) and real shifts (a complex shift fails with KW_ERR_ARG).
+ *   KW_METHOD_BICG: Appendix B; a shadow residual r~ (start btilde_dev, real
+ *     [m] device vector, or NULL for b; kw_solve_batched always uses b) is
+ *     advanced with A^dagger and the conjugated coefficients, rho = r~^dagger r.
+ *     A^dagger r~ = conj(z_s) r~ - H^dagger r~, with H^dagger = H for the CSR and
+ *     generated operators (real symmetric) and, for a callback, the adjoint
+ *     callback (kw_set_matvec_adjoint) or the same callback when none is set.
+ *     Each iteration then makes two products and one more pass over r~ and q.
+ * The shifted recurrences (Eqs. 20-26), seed switching and outputs are those of
+ * COCG for every method.  btilde_dev is borrowed until the next kw_set_method.
+ * Errors: KW_ERR_ARG (unknown method, btilde_dev with a method other than BiCG). */
+kw_status kw_set_method(kw_ctx* ctx, int method, const double* btilde_dev);
+
+/* Adjoint product q = H^dagger r for BiCG with a callback operator that is not
+ * Hermitian (same calling rules as kw_matvec_fn; NULL: H is Hermitian).  A later
+ * kw_set_matvec or kw_set_csr clears it.  Errors: KW_ERR_ARG (no callback set). */
+kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user);
 
 /* Schedule of an iteration.  on = 1 (the default): the shift scalars of
  * iteration n (and the full-mode x/p update) run on a second stream while the

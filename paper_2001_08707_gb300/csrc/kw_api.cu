@@ -75,7 +75,13 @@ struct kw_ctx {
   // operator as a caller's callback (kw_set_matvec); the FP32-pair form hands it kw_c128 copies
   kw_matvec_fn mv_fn = nullptr;
   void* mv_user = nullptr;
+  kw_matvec_fn mv_fn_adj = nullptr;   // adjoint product for BiCG (NULL: Hermitian)
+  void* mv_user_adj = nullptr;
   DBuf mv_r, mv_q;
+  // solver of Table 1 (kw_set_method) and the BiCG shadow vectors
+  int method = KW_METHOD_COCG;
+  const double* btilde = nullptr;
+  DBuf rtA, rtB, qt;
   DBuf val32;
   DBuf valpair;               // FP32-pair copy of the values (KW_DF64, values not exact in FP32)
   DBuf inexact;
@@ -214,7 +220,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->part_k1, &ctx->st, &ctx->projx, &ctx->tdot,
-                  &ctx->mv_r, &ctx->mv_q, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
+                  &ctx->mv_r, &ctx->mv_q, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag};
@@ -252,6 +258,8 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
     return fail(ctx, KW_ERR_ARG, "kw_set_csr: need 1 <= m < 2^31, 0 <= nnz < 2^31 and non-NULL arrays");
   ctx->mv_fn = nullptr;
   ctx->mv_user = nullptr;
+  ctx->mv_fn_adj = nullptr;
+  ctx->mv_user_adj = nullptr;
   ctx->op = kw::OP_CSR;
   ctx->m = m;
   ctx->nnz = nnz;
@@ -317,6 +325,8 @@ static void become_generated(kw_ctx* ctx, int op, int64_t m) {
   ctx->val = nullptr;
   ctx->mv_fn = nullptr;
   ctx->mv_user = nullptr;
+  ctx->mv_fn_adj = nullptr;
+  ctx->mv_user_adj = nullptr;
   ctx->val32_exact = false;
   ctx->spmv_lanes = 1;
   ctx->spmv_val_f32 = 0;
@@ -412,6 +422,8 @@ kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user) {
   if (m < 1 || m > 0x7fffffffLL || !fn) return fail(ctx, KW_ERR_ARG, "kw_set_matvec: need 1 <= m < 2^31 and fn");
   ctx->mv_fn = fn;
   ctx->mv_user = user;
+  ctx->mv_fn_adj = nullptr;
+  ctx->mv_user_adj = nullptr;
   ctx->op = kw::OP_CALLBACK;
   ctx->m = m;
   ctx->nnz = 0;
@@ -471,6 +483,8 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.part_k1 = (double*)ctx->part_k1.p;
   w.mv_fn = ctx->mv_fn;
   w.mv_user = ctx->mv_user;
+  w.mv_fn_adj = ctx->mv_fn_adj;
+  w.mv_user_adj = ctx->mv_user_adj;
   w.mv_r = ctx->mv_r.p;
   w.mv_q = ctx->mv_q.p;
   if (lanes == kw::KW_SPMV_SELL) {
@@ -762,6 +776,17 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->projx, Ks * w.nout * 16},
   };
   for (auto& pl : plan) KW_CUDA(pl.b->ensure(pl.bytes), "workspace allocation");
+  w.method = ctx->method;
+  w.btilde = ctx->method == KW_METHOD_BICG ? ctx->btilde : nullptr;
+  w.rtA = w.rtB = w.qt = nullptr;
+  if (ctx->method == KW_METHOD_BICG) {
+    KW_CUDA(ctx->rtA.ensure(Ms * vs), "workspace allocation");
+    KW_CUDA(ctx->rtB.ensure(Ms * vs), "workspace allocation");
+    KW_CUDA(ctx->qt.ensure(Ms * vs), "workspace allocation");
+    w.rtA = ctx->rtA.p;
+    w.rtB = ctx->rtB.p;
+    w.qt = ctx->qt.p;
+  }
   w.log = nullptr;
   w.log_max = 0;
   if (ctx->log_max > 0) {
@@ -865,6 +890,10 @@ static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, c
   for (int64_t k = 0; k < nshift; ++k)
     if (!isfinite(z_host[k].re) || !isfinite(z_host[k].im))
       return fail(ctx, KW_ERR_ARG, "kw_solve: shift %lld is not finite", (long long)k);
+  if (ctx->method == KW_METHOD_CG)
+    for (int64_t k = 0; k < nshift; ++k)
+      if (z_host[k].im != 0.0)
+        return fail(ctx, KW_ERR_ARG, "kw_solve: the CG solver needs real shifts (shift %lld is complex)", (long long)k);
   memset(&ctx->stats, 0, sizeof(ctx->stats));
   kw_status s = tune_spmv(ctx);
   if (s != KW_OK) return s;
@@ -1042,6 +1071,9 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   for (int64_t i = 0; i < n; ++i) {
     kw_ctx* c = ctx->children[i];
     c->opt = ctx->opt;
+    c->method = ctx->method;   // BiCG instances start their shadow from b
+    c->btilde = nullptr;
+    c->overlap = ctx->overlap;
     if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
     KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
     kw_status s = kw_set_csr(c, inst[i].m, inst[i].nnz, inst[i].rowptr_dev, inst[i].col_dev, inst[i].val_dev);
@@ -1321,6 +1353,25 @@ kw_status kw_recalc(kw_ctx* ctx, int64_t n_iter, int64_t nproj, double thresh, c
     fail(ctx, st, "kw_recalc: %lld of %lld shifts did not freeze within %lld rows", (long long)(nshift - nc),
          (long long)nshift, (long long)rows);
   return st;
+}
+
+kw_status kw_set_method(kw_ctx* ctx, int method, const double* btilde_dev) {
+  if (!ctx) return KW_ERR_ARG;
+  if (method != KW_METHOD_COCG && method != KW_METHOD_CG && method != KW_METHOD_BICG)
+    return fail(ctx, KW_ERR_ARG, "kw_set_method: unknown method %d", method);
+  if (btilde_dev && method != KW_METHOD_BICG)
+    return fail(ctx, KW_ERR_ARG, "kw_set_method: a shadow start vector is for BiCG only");
+  ctx->method = method;
+  ctx->btilde = btilde_dev;
+  return KW_OK;
+}
+
+kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user) {
+  if (!ctx) return KW_ERR_ARG;
+  if (!ctx->mv_fn) return fail(ctx, KW_ERR_ARG, "kw_set_matvec_adjoint: set the product with kw_set_matvec first");
+  ctx->mv_fn_adj = fn;
+  ctx->mv_user_adj = fn ? user : nullptr;
+  return KW_OK;
 }
 
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {

@@ -98,6 +98,10 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ dfc csub(dfc a, dfc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
 
+__device__ __forceinline__ double2 vconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ float2 vconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ dfc vconj(dfc a) { return {a.re, df_neg(a.im)}; }
+
 template <class V> __device__ __forceinline__ V vzero();
 template <> __device__ __forceinline__ double2 vzero<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float2 vzero<float2>() { return make_float2(0.f, 0.f); }
@@ -226,6 +230,28 @@ __device__ __forceinline__ void acc_rho_nrm(df& re, df& im, df& n, dfc r) {
   acc_prod(re, mim, r.im);
   const df x2 = {2.f * r.re.hi, 2.f * r.re.lo};
   acc_prod(im, x2, r.im);
+  acc_prod(n, r.re, r.re);
+  acc_prod(n, r.im, r.im);
+}
+// (re, im) += x^dagger y (one element): re += x.re y.re + x.im y.im, im += x.re y.im - x.im y.re
+__device__ __forceinline__ void acc_cdot(double& re, double& im, double2 x, double2 y) {
+  re += x.x * y.x + x.y * y.y;
+  im += x.x * y.y - x.y * y.x;
+}
+__device__ __forceinline__ void acc_cdot(float& re, float& im, float2 x, float2 y) {
+  re += x.x * y.x + x.y * y.y;
+  im += x.x * y.y - x.y * y.x;
+}
+__device__ __forceinline__ void acc_cdot(df& re, df& im, dfc x, dfc y) {
+  acc_prod(re, x.re, y.re);
+  acc_prod(re, x.im, y.im);
+  acc_prod(im, x.re, y.im);
+  acc_prod(im, df_neg(x.im), y.re);
+}
+// nrm += |r|^2
+__device__ __forceinline__ void acc_nrm(double& n, double2 r) { n += r.x * r.x + r.y * r.y; }
+__device__ __forceinline__ void acc_nrm(float& n, float2 r) { n += r.x * r.x + r.y * r.y; }
+__device__ __forceinline__ void acc_nrm(df& n, dfc r) {
   acc_prod(n, r.re, r.re);
   acc_prod(n, r.im, r.im);
 }

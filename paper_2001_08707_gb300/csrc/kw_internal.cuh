@@ -128,9 +128,18 @@ struct Work {
   int sp_uniform = 0;                   // every J_b equal: one value u_v
   // lattice operator (kw_set_lattice3d): eps in u_diag/u_kind, hopping in u_v
   int lx = 0, ly = 0, lz = 0;
+  // solver of Table 1 and the BiCG shadow vectors (rotating like rA/rB) and A^dagger r~
+  int method = KW_METHOD_COCG;
+  void* rtA = nullptr;
+  void* rtB = nullptr;
+  void* qt = nullptr;
+  const double* btilde = nullptr;   // BiCG r~_0 (NULL: b)
   // operator given as a callback (kw_set_matvec) instead of the CSR arrays
   kw_matvec_fn mv_fn = nullptr;
   void* mv_user = nullptr;
+  kw_matvec_fn mv_fn_adj = nullptr;   // q = H^dagger r (BiCG; NULL: H Hermitian)
+  void* mv_user_adj = nullptr;
+  int mv_adjoint = 0;                 // set while K1 forms the adjoint product
   void* mv_r = nullptr;   // FP32-pair form: kw_c128 copy of r handed to the callback
   void* mv_q = nullptr;   // FP32-pair form: the callback's H r (kw_c128)
   int mv_failed = 0;      // set when the callback returned nonzero

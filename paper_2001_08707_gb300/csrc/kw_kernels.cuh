@@ -166,10 +166,13 @@ __device__ __forceinline__ void set_fail(State* st, int status) {
 
 // ================================================================ K1: SpMV + first dot
 struct SpmvMode {
-  int solver;        // 1: inside the solve (reads z_s, pending scale, computes alpha)
+  int solver;        // 1: inside the solve (reads z_s, computes alpha)
   double2 zs;        // standalone: seed shift
   float4 zs_pair;    // standalone: its FP32-pair image
   double2* t_out;    // standalone: result
+  int conj_zs = 0;   // use the conjugate seed shift (BiCG: the adjoint product A^dagger r~ for real H)
+  int conj_dot = 0;  // r^dagger q instead of r^T q (CG)
+  int dot = 1;       // 0: only q, no r^T q and no K1 tail (BiCG forms its dot separately)
 };
 
 // End of K1 (every layout): block sum of r^T q; the last block stores it for
@@ -177,6 +180,7 @@ struct SpmvMode {
 template <class A>
 __device__ __forceinline__ void spmv_finish(A c_re, A c_im, double t_re, double t_im, int lane, State* st,
                                             double* __restrict__ part, const SpmvMode& mode) {
+  if (!mode.dot) return;   // uniform: no block takes part, the counter is untouched
   t_re += ato_double(warp_sum(anorm(c_re)));
   t_im += ato_double(warp_sum(anorm(c_im)));
   __shared__ double red[2];
@@ -233,6 +237,7 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
   if (mode.solver) {
     if (st->done) return;
     zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
+    if (mode.conj_zs) zsv = vconj(zsv);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -272,7 +277,7 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
       q[row] = qi;
-      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
+      acc_cplx(c_re, c_im, cmul(mode.conj_dot ? vconj(ri) : ri, qi));   // r^T q (COCG) or r^dagger q (CG)
     }
     if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -300,6 +305,7 @@ k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restri
   if (mode.solver) {
     if (st->done) return;
     zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
+    if (mode.conj_zs) zsv = vconj(zsv);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -331,7 +337,7 @@ k_spmv_sell(int m, int nslice, const int* __restrict__ perm, const int* __restri
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), acc);        // z_s r - H r
       q[row] = qi;
-      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
+      acc_cplx(c_re, c_im, cmul(mode.conj_dot ? vconj(ri) : ri, qi));   // r^T q (COCG) or r^dagger q (CG)
     }
     if (++in_chunk == PT<P>::CHUNK) {
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -359,6 +365,7 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
   if (mode.solver) {
     if (st->done) return;
     zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
+    if (mode.conj_zs) zsv = vconj(zsv);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -401,7 +408,7 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
       hr = normalize(hr);
       V qi = csub(cmul(zsv, ri), hr);         // z_s r - H r
       q[row] = qi;
-      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
+      acc_cplx(c_re, c_im, cmul(mode.conj_dot ? vconj(ri) : ri, qi));   // r^T q (COCG) or r^dagger q (CG)
     }
     if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -416,10 +423,11 @@ k_spmv_u(int m, const int* __restrict__ rowptr, const int* __restrict__ col, con
 // Shared tail of the generated-operator K1 kernels: q = z_s r - H r for one
 // row, the store and the r^T q partial.
 template <class V, class A>
-__device__ __forceinline__ void k1_emit(int row, V ri, V hr, V zsv, V* __restrict__ q, A& c_re, A& c_im) {
+__device__ __forceinline__ void k1_emit(int row, V ri, V hr, V zsv, V* __restrict__ q, A& c_re, A& c_im,
+                                        int conj_dot) {
   const V qi = csub(cmul(zsv, ri), hr);
   q[row] = qi;
-  acc_cplx(c_re, c_im, cmul(ri, qi));
+  acc_cplx(c_re, c_im, cmul(conj_dot ? vconj(ri) : ri, qi));
 }
 
 // Seed shift of K1 (inside the solve: the one current when the previous K2
@@ -429,6 +437,7 @@ __device__ __forceinline__ bool k1_seed(const State* st, const SpmvMode& mode, V
   if (mode.solver) {
     if (st->done) return false;
     zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
+    if (mode.conj_zs) zsv = vconj(zsv);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -496,7 +505,7 @@ k_spmv_spin(int m, const unsigned* __restrict__ basis, const int* __restrict__ b
       if constexpr (UNI) mac(hr, uv, normalize(sum));
       else vacc(hr, normalize(sum));
       hr = normalize(hr);
-      k1_emit(row, ri, hr, zsv, q, c_re, c_im);
+      k1_emit(row, ri, hr, zsv, q, c_re, c_im, mode.conj_dot);
     }
     if (++in_chunk == PT<P>::CHUNK) {
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -545,7 +554,7 @@ k_spmv_lattice(int m, int nx, int ny, int nz, const DV* __restrict__ eps, DV hop
       mac(hr, eps[row], ri);
       mac(hr, hop, normalize(sum));
       hr = normalize(hr);
-      k1_emit(row, ri, hr, zsv, q, c_re, c_im);
+      k1_emit(row, ri, hr, zsv, q, c_re, c_im, mode.conj_dot);
     }
     if (++in_chunk == PT<P>::CHUNK) {
       t_re += ato_double(warp_sum(anorm(c_re)));
@@ -580,6 +589,7 @@ k_matvec_finish(int m, const typename PT<P>::V* r, const typename MvT<P>::H* hq,
   if (mode.solver) {
     if (st->done) return;
     zsv = vscalar<V>(st->zs_k1, st->p_zs_k1);
+    if (mode.conj_zs) zsv = vconj(zsv);
   } else {
     zsv = vscalar<V>(mode.zs, mode.zs_pair);
   }
@@ -595,8 +605,36 @@ k_matvec_finish(int m, const typename PT<P>::V* r, const typename MvT<P>::H* hq,
       V ri = r[row];
       V qi = csub(cmul(zsv, ri), mv_in(hq[row], (V*)nullptr));   // z_s r - H r
       q[row] = qi;
-      acc_cplx(c_re, c_im, cmul(ri, qi));     // r^T q, unconjugated
+      acc_cplx(c_re, c_im, cmul(mode.conj_dot ? vconj(ri) : ri, qi));   // r^T q (COCG) or r^dagger q (CG)
     }
+    if (++in_chunk == PT<P>::CHUNK) {
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
+// BiCG's first dot, r~_n^dagger (A r_n), over the two vectors K1 left (r~ and
+// q), followed by the same K1 tail (the seed scalars of Eq. 17 for the case
+// that the seed is kept).
+template <int P>
+__global__ void __launch_bounds__(256)
+k_dot_tail(int m, const typename PT<P>::V* __restrict__ x, const typename PT<P>::V* __restrict__ y, State* st,
+           double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  if (st->done) return;
+  const int lane = threadIdx.x & 31;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < m; base += stride) {
+    const int i = base + (int)threadIdx.x;
+    if (i < m) acc_cplx(c_re, c_im, cmul(vconj(x[i]), y[i]));
     if (++in_chunk == PT<P>::CHUNK) {
       t_re += ato_double(warp_sum(anorm(c_re)));
       t_im += ato_double(warp_sum(anorm(c_im)));
@@ -685,11 +723,16 @@ __global__ void k_sell_fill(int m, int nslice, const int* __restrict__ perm, con
 
 // ================================================================ K2: three-term update + dots
 // Values per block: [rho.re, rho.im, nu, w_0.re, w_0.im, ..., w_{np-1}.re, w_{np-1}.im]
-template <int P, int NP>
-__global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5) ? 3 : 1)
+// METHOD (Table 1): COCG rho = r^T r; CG rho = r^dagger r = nu; BiCG also
+// advances the shadow residual (Appendix B: conjugated coefficients, A^dagger)
+// and rho = r~^dagger r.
+template <int P, int NP, int METHOD>
+__global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5 && METHOD != KW_METHOD_BICG) ? 3 : 1)
 k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
               typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int np,
-              int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out) {
+              int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out,
+              const typename PT<P>::V* __restrict__ rtn_buf, const typename PT<P>::V* __restrict__ qt,
+              typename PT<P>::V* __restrict__ rtm_buf) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   typedef typename PT<P>::A A;
@@ -815,7 +858,17 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
       const V ca = vscalar<V>(s_cf[0], pa), cb = vscalar<V>(s_cf[1], pb), cc = vscalar<V>(s_cf[2], pc);
       const V r1 = csub(csub(cmul(ca, rn[u]), cmul(cb, qv[u])), cmul(cc, rm[u]));   // Eq. 16; zero when !has
       if (has[u]) rm_buf[i] = r1;
-      acc_rho_nrm(chunk[0], chunk[1], chunk[2], r1);
+      if constexpr (METHOD == KW_METHOD_BICG) {
+        // shadow: the conjugated coefficients (their folded scales are the conjugate ones)
+        const V rtn = has[u] ? rtn_buf[i] : vzero<V>(), rtm = has[u] ? rtm_buf[i] : vzero<V>();
+        const V qtv = has[u] ? qt[i] : vzero<V>();
+        const V rt1 = csub(csub(cmul(vconj(ca), rtn), cmul(vconj(cb), qtv)), cmul(vconj(cc), rtm));
+        if (has[u]) rtm_buf[i] = rt1;
+        acc_cdot(chunk[0], chunk[1], rt1, r1);
+        acc_nrm(chunk[2], r1);
+      } else {
+        acc_rho_nrm(chunk[0], chunk[1], chunk[2], r1);
+      }
 #pragma unroll
       for (int l = 0; l < NP; ++l)
         if (l < np) acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a[u][l], r1);
@@ -871,7 +924,8 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
     st->switched = 0;
     st->zs_k1 = st->zs;                                // the seed the next K1 uses
     st->p_zs_k1 = st->p_zs;
-    const double2 rho1 = make_double2(all[0], all[1]);
+    // rho_{n+1}: r^T r (COCG), ||r||^2 (CG), r~^dagger r (BiCG)
+    const double2 rho1 = METHOD == KW_METHOD_CG ? make_double2(all[2], 0.0) : make_double2(all[0], all[1]);
     // beta_n = rho_{n+1} / rho_n, with this block's own 1/rho_n (block 0's copy in
     // the state was written during this kernel and may not be visible here)
     const double2 beta = cmul(rho1, s_sc[1]);
@@ -1364,6 +1418,35 @@ k_init_dots(int m, int np, const double* __restrict__ b, const double* __restric
   }
 }
 
+// BiCG start: r~_0 = b~, r~_{-1} = 0, and rho_0 = b~^T b (b, b~ real) by the last block.
+template <int P>
+__global__ void __launch_bounds__(256) k_init_shadow(int m, const double* __restrict__ bt, const double* __restrict__ b,
+                                                     typename PT<P>::V* rt0, typename PT<P>::V* rtm, State* st,
+                                                     double* __restrict__ part) {
+  typedef typename PT<P>::V V;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    rt0[i] = vreal<V>(bt[i]);
+    rtm[i] = vzero<V>();
+    acc = fma(bt[i], b[i], acc);
+  }
+  __shared__ double red[1];
+  {
+    double v1[1] = {acc};
+    block_sum<1, double>(v1, 1, red);
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+  if (!arrive_last(&st->cnt_init)) return;
+  __shared__ double tot[1];
+  reduce_partials<1>(part, gridDim.x, 1, 1, tot);
+  if (threadIdx.x == 0) {
+    st->cnt_init = 0;
+    st->rho = make_double2(tot[0], 0.0);
+    st->rho1 = st->rho;
+    if (tot[0] == 0.0) set_fail(st, KW_ERR_BREAKDOWN);
+  }
+}
+
 static __global__ void k_init_shifts(int K, int np, double2* pi1, double2* pi0, int* active, long long* conv_iter,
                                      double* final_res, double2* Y, double2* U, const double2* w0) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1607,7 +1690,9 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
     rin = w.mv_r;
     hq = w.mv_q;
   }
-  if (w.mv_fn(w.mv_user, rin, hq, w.m, P == PREC_C32 ? KW_ELEM_C64 : KW_ELEM_C128, (void*)w.stream) != 0) {
+  kw_matvec_fn fn = (w.mv_adjoint && w.mv_fn_adj) ? w.mv_fn_adj : w.mv_fn;
+  void* user = (w.mv_adjoint && w.mv_fn_adj) ? w.mv_user_adj : w.mv_user;
+  if (fn(user, rin, hq, w.m, P == PREC_C32 ? KW_ELEM_C64 : KW_ELEM_C128, (void*)w.stream) != 0) {
     w.mv_failed = 1;
     return cudaErrorUnknown;
   }
@@ -1634,27 +1719,75 @@ static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode)
   }
 }
 
-template <int P, int NP>
+template <int P, int NP, int METHOD>
 static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_seed_update<P, NP>, 256, w.num_sms);
+  if (nblk == 0) nblk = resident_blocks(k_seed_update<P, NP, METHOD>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
-  k_seed_update<P, NP><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)rn, (const V*)w.q, (V*)rm,
-                                                   (const R*)w.proj_rows, w.nproj, parity, w.st, w.part, w.w);
+  // shadow buffers rotate like the residual buffers (parity 0: r~_n in rtA)
+  const void* rtn = parity ? w.rtB : w.rtA;
+  void* rtm = parity ? w.rtA : w.rtB;
+  k_seed_update<P, NP, METHOD><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)rn, (const V*)w.q, (V*)rm,
+                                                           (const R*)w.proj_rows, w.nproj, parity, w.st, w.part,
+                                                           w.w, (const V*)rtn, (const V*)w.qt, (V*)rtm);
   return cudaGetLastError();
+}
+
+template <int P, int METHOD>
+static cudaError_t seed_dispatch_m(Work& w, void* rn, void* rm, int parity) {
+  const int np = w.nproj;
+  if (np == 0) return seed_launch<P, 0, METHOD>(w, rn, rm, parity);
+  if (np <= 2) return seed_launch<P, 2, METHOD>(w, rn, rm, parity);
+  if (np <= 5) return seed_launch<P, 5, METHOD>(w, rn, rm, parity);
+  if (np <= 9) return seed_launch<P, 9, METHOD>(w, rn, rm, parity);
+  if (np <= 17) return seed_launch<P, 17, METHOD>(w, rn, rm, parity);
+  return seed_launch<P, KW_MAX_PROJ, METHOD>(w, rn, rm, parity);
 }
 
 template <int P>
 static cudaError_t seed_dispatch(Work& w, void* rn, void* rm, int parity) {
-  const int np = w.nproj;
-  if (np == 0) return seed_launch<P, 0>(w, rn, rm, parity);
-  if (np <= 2) return seed_launch<P, 2>(w, rn, rm, parity);
-  if (np <= 5) return seed_launch<P, 5>(w, rn, rm, parity);
-  if (np <= 9) return seed_launch<P, 9>(w, rn, rm, parity);
-  if (np <= 17) return seed_launch<P, 17>(w, rn, rm, parity);
-  return seed_launch<P, KW_MAX_PROJ>(w, rn, rm, parity);
+  if (w.method == KW_METHOD_BICG) {
+    if (!w.rtA || !w.rtB || !w.qt) return cudaErrorInvalidValue;
+    return seed_dispatch_m<P, KW_METHOD_BICG>(w, rn, rm, parity);
+  }
+  if (w.method == KW_METHOD_CG) return seed_dispatch_m<P, KW_METHOD_CG>(w, rn, rm, parity);
+  return seed_dispatch_m<P, KW_METHOD_COCG>(w, rn, rm, parity);
+}
+
+// K1 of iteration n+1 for the solver of Table 1 on r (and r~ for BiCG):
+// COCG r^T q, CG r^dagger q; BiCG the product on r, the adjoint product on r~
+// (conjugate seed shift; the adjoint callback when given) and r~^dagger q.
+template <int P>
+static cudaError_t k1_dispatch(Work& w, void* r, void* rt) {
+  typedef typename PT<P>::V V;
+  SpmvMode mode;
+  mode.solver = 1;
+  mode.zs = make_double2(0.0, 0.0);
+  mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);
+  mode.t_out = nullptr;
+  if (w.method != KW_METHOD_BICG) {
+    mode.conj_dot = w.method == KW_METHOD_CG;
+    return spmv_dispatch<P>(w, r, w.q, mode);
+  }
+  if (!rt || !w.qt) return cudaErrorInvalidValue;
+  mode.dot = 0;
+  cudaError_t e = spmv_dispatch<P>(w, r, w.q, mode);
+  if (e != cudaSuccess) return e;
+  SpmvMode ms = mode;
+  ms.conj_zs = 1;
+  w.mv_adjoint = 1;   // the callback path takes the adjoint callback for this product
+  e = spmv_dispatch<P>(w, rt, w.qt, ms);
+  w.mv_adjoint = 0;
+  if (e != cudaSuccess) return e;
+  SpmvMode md = mode;
+  md.dot = 1;
+  static int nblk = 0;
+  if (nblk == 0) nblk = resident_blocks(k_dot_tail<P>, 256, w.num_sms);
+  const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
+  k_dot_tail<P><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)rt, (const V*)w.q, w.st, w.part_k1, md);
+  return cudaGetLastError();
 }
 
 // One iteration n on two streams (K1(n) was enqueued by the previous
@@ -1683,12 +1816,8 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   if ((e = seed_dispatch<P>(w, rn, rm, parity)) != cudaSuccess) return e;
   KW_MARK(1, w.stream);
   if (w.overlap && (e = cudaEventRecord(w.ev_k2, w.stream)) != cudaSuccess) return e;
-  SpmvMode mode;
-  mode.solver = 1;
-  mode.zs = make_double2(0.0, 0.0);
-  mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);
-  mode.t_out = nullptr;
-  if ((e = spmv_dispatch<P>(w, rm, w.q, mode)) != cudaSuccess) return e;   // K1(n+1) on r_{n+1}
+  // K1(n+1) on r_{n+1} (and r~_{n+1}, which K2 wrote over r~_{n-1})
+  if ((e = k1_dispatch<P>(w, rm, parity ? w.rtA : w.rtB)) != cudaSuccess) return e;
   KW_MARK(2, w.stream);
 
   if (w.overlap && (e = cudaStreamWaitEvent(s2, w.ev_k2, 0)) != cudaSuccess) return e;
@@ -1766,13 +1895,14 @@ cudaError_t launch_init(Work& w) {
   k_init_shifts<<<(w.K + 127) / 128, 128, 0, w.stream>>>(w.K, w.nproj, w.pi1, w.pi0, w.active, w.conv_iter,
                                                         w.final_res, w.Y, w.U, w.w0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (w.method == KW_METHOD_BICG) {   // r~_0 = b~ (default b), r~_{-1} = 0, rho_0 = b~^T b
+    if (!w.rtA || !w.rtB || !w.qt) return cudaErrorInvalidValue;
+    k_init_shadow<P><<<nb, 256, 0, w.stream>>>((int)w.m, w.btilde ? w.btilde : w.b, w.b, (V*)w.rtA, (V*)w.rtB,
+                                               w.st, w.part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // K1(0) on r_0 (rA); every iteration then enqueues the next K1 after its K2
-  SpmvMode mode;
-  mode.solver = 1;
-  mode.zs = make_double2(0.0, 0.0);
-  mode.zs_pair = make_float4(0.f, 0.f, 0.f, 0.f);
-  mode.t_out = nullptr;
-  return spmv_dispatch<P>(w, w.rA, w.q, mode);
+  return k1_dispatch<P>(w, w.rA, w.rtA);
 }
 
 // Full-mode outputs: FP32-pair vectors are first converted to FP64 in place

@@ -62,6 +62,7 @@ _lib = None
 # kw_matvec_fn: (user, r_dev, q_dev, m, elem, cuda_stream) -> int
 MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_void_p)
 KW_ELEM_C128, KW_ELEM_C64 = 0, 1
+METHODS = {"cocg": 0, "cg": 1, "bicg": 2}
 
 
 class _DeviceVector:
@@ -107,6 +108,8 @@ def load_library(path: str = LIB_PATH):
         "kw_set_lattice3d": (C.c_int, [P, I64, I64, I64, P, D]),
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
+        "kw_set_method": (C.c_int, [P, C.c_int, P]),
+        "kw_set_matvec_adjoint": (C.c_int, [P, MATVEC_FN, P]),
         "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
         "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
     }
@@ -193,7 +196,7 @@ class Solver:
     """A solver context (kw_ctx) on the current CUDA device and stream."""
 
     def __init__(self, prec: str = "f64", tol: float = 1e-10, maxiter: int = 100000, seed_switch: bool = True,
-                 hist_stride: int = 0, hist_max: int = 0, stream=None):
+                 hist_stride: int = 0, hist_max: int = 0, stream=None, method: str = "cocg"):
         import torch
 
         self._torch = torch
@@ -212,6 +215,8 @@ class Solver:
         self._ctx = ctx
         self._keep = []
         self.m = None
+        if method != "cocg":
+            self.set_method(method)
         self.vec_dtype = torch.complex64 if self.prec == KW_C32V_F64S else torch.complex128
 
     # ------------------------------------------------------------------ helpers
@@ -324,11 +329,12 @@ class Solver:
                 raise self._err(st, "kw_get_residual_history")
         return h
 
-    def set_matvec(self, fn, m: int):
+    def set_matvec(self, fn, m: int, fn_adj=None):
         """kw_set_matvec: use ``fn(r, q)`` as the operator, where r and q are
         borrowed complex CUDA tensors of length m (complex64 in the FP32 form,
         complex128 otherwise) and fn must write H r into q with torch work on
-        the current stream (the solver's).  kw_set_csr ends it."""
+        the current stream (the solver's).  fn_adj(r, q), if given, writes
+        H^dagger r (kw_set_matvec_adjoint, for BiCG).  kw_set_csr ends it."""
         torch = self._torch
         self._mv_error = None
 
@@ -351,6 +357,25 @@ class Solver:
         if st != KW_OK:
             raise self._err(st, "kw_set_matvec")
         self._mv_cb = cb                          # the library keeps the pointer
+        if fn_adj is not None:
+            def trampoline_adj(user, r, q, mm, elem, stream):
+                try:
+                    ts = "<f8" if elem == KW_ELEM_C128 else "<f4"
+                    rt = torch.view_as_complex(torch.as_tensor(_DeviceVector(r, mm, ts), device="cuda"))
+                    qt = torch.view_as_complex(torch.as_tensor(_DeviceVector(q, mm, ts), device="cuda"))
+                    cs = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+                    with torch.cuda.stream(cs):
+                        fn_adj(rt, qt)
+                    return 0
+                except BaseException as exc:          # reported as KW_ERR_CALLBACK
+                    self._mv_error = exc
+                    return 1
+
+            cba = MATVEC_FN(trampoline_adj)
+            st = self._lib.kw_set_matvec_adjoint(self._ctx, cba, None)
+            if st != KW_OK:
+                raise self._err(st, "kw_set_matvec_adjoint")
+            self._mv_cb_adj = cba
         self._keep = []
         self.m = int(m)
 
@@ -380,6 +405,15 @@ class Solver:
             raise self._err(st, "kw_set_lattice3d")
         self._keep = []
         self.m = int(nx) * int(ny) * int(nz)
+
+    def set_method(self, method: str, btilde=None):
+        """kw_set_method: 'cocg' (default), 'cg' (Hermitian A, real shifts) or
+        'bicg' (shadow residual; btilde = its real start vector, default b)."""
+        bt = None if btilde is None else self._dev(btilde, self._torch.float64)
+        st = self._lib.kw_set_method(self._ctx, METHODS[method], None if bt is None else C.c_void_p(bt.data_ptr()))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_method")
+        self._btilde = bt                          # borrowed by the context
 
     def set_stream_overlap(self, on: bool):
         """kw_set_stream_overlap: run the shift scalars of iteration n beside the
