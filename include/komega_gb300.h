@@ -237,6 +237,21 @@ typedef struct {
     double tol;                    /* > 0 overrides the context's tolerance for this problem */
 } kw_instance;
 
+/* Continue the last kw_solve of ctx for up to more_iters further iterations
+ * (the "restart" mode of Sec. 3.3: a solve stopped by its iteration cap goes on
+ * from where it stopped, on the device state the context kept).  Valid only
+ * when that solve ended with KW_NOT_CONVERGED and nothing has since changed
+ * the context's operator, method or workspace (kw_set_csr, kw_set_matvec, the
+ * generated operators, kw_set_method, kw_spmv_dot, kw_solve_batched and other
+ * solves end it).  b, the shifts, the left vectors and, in full mode, the
+ * caller's x buffer must still be valid: they are read and updated in place.
+ * The result is the one a single solve with the larger cap would give (the
+ * pair form's x is converted back from kw_c128 to pairs first, which keeps
+ * its value).  proj_out_host and info as for kw_solve (iteration counts are
+ * totals); the same residual history and Krylov log continue.  Errors:
+ * KW_ERR_ARG (more_iters < 1, nothing to resume), the kw_solve errors. */
+kw_status kw_resume(kw_ctx* ctx, int64_t more_iters, kw_c128* proj_out_host, kw_solve_info* info);
+
 /* Solve n independent problems (uneven sizes and shift counts) together.
  * Each instance runs the kw_solve iteration on its own stream and workspace,
  * owned by the context and reused by later calls; one CUDA graph holds a chunk

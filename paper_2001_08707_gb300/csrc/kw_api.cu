@@ -125,6 +125,8 @@ struct kw_ctx {
   DBuf child_states, done_count;
   int* done_host = nullptr;   // pinned
   // last solve
+  bool resumable = false;     // the last kw_solve stopped at maxiter and its workspace is intact
+  int64_t run_maxiter = 0;    // iteration cap of the running solve
   int64_t last_K = 0;
   int64_t last_nrec = 0;
   // Krylov log (kw_set_krylov_log) and the last solve's record of it
@@ -261,6 +263,7 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   ctx->mv_fn_adj = nullptr;
   ctx->mv_user_adj = nullptr;
   ctx->op = kw::OP_CSR;
+  ctx->resumable = false;
   ctx->m = m;
   ctx->nnz = nnz;
   ctx->rowptr = rowptr_dev;
@@ -318,6 +321,7 @@ static kw_status generated_diag(kw_ctx* ctx, int64_t m, bool offdiag_exact32) {
 // The context's operator becomes a generated one: forget the CSR and callback.
 static void become_generated(kw_ctx* ctx, int op, int64_t m) {
   ctx->op = op;
+  ctx->resumable = false;
   ctx->m = m;
   ctx->nnz = 0;
   ctx->rowptr = nullptr;
@@ -425,6 +429,7 @@ kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user) {
   ctx->mv_fn_adj = nullptr;
   ctx->mv_user_adj = nullptr;
   ctx->op = kw::OP_CALLBACK;
+  ctx->resumable = false;
   ctx->m = m;
   ctx->nnz = 0;
   ctx->rowptr = nullptr;
@@ -895,6 +900,8 @@ static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, c
       if (z_host[k].im != 0.0)
         return fail(ctx, KW_ERR_ARG, "kw_solve: the CG solver needs real shifts (shift %lld is complex)", (long long)k);
   memset(&ctx->stats, 0, sizeof(ctx->stats));
+  ctx->resumable = false;
+  ctx->run_maxiter = ctx->opt.maxiter;
   kw_status s = tune_spmv(ctx);
   if (s != KW_OK) return s;
   s = ensure_mv_buffers(ctx);
@@ -918,10 +925,10 @@ static const int kChunk = 16;   // iterations per chunk (even: buffer parity rep
 
 // Phase 2 for one context: enqueue chunks and poll the device stop flag one
 // chunk behind; returns after the stream has drained.
-static kw_status run_loop(kw_ctx* ctx) {
+static kw_status run_loop(kw_ctx* ctx, int64_t start = 0) {
   kw::Work& w = ctx->work;
   const bool timing = ctx->timing_every > 0;
-  int64_t launched = 0;
+  int64_t launched = start;   // iteration number of the next launch (its parity selects the buffers)
   int slot = 0;
   bool have_prev = false;
   int64_t sampled_at[2] = {-1, -1};
@@ -955,7 +962,7 @@ static kw_status run_loop(kw_ctx* ctx) {
     }
     have_prev = true;
     slot ^= 1;
-    if (launched > ctx->opt.maxiter + 2 * kChunk) break;   // the device stops at maxiter; never loop forever
+    if (launched > ctx->run_maxiter + 2 * kChunk) break;   // the device stops at maxiter; never loop forever
   }
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
   return KW_OK;
@@ -973,6 +980,7 @@ static kw_status solve_end(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* i
   const kw::State& st = *ctx->st_host;
   ctx->last_K = nshift;
   ctx->last_nrec = st.n_rec;
+  ctx->resumable = st.status == KW_NOT_CONVERGED;
   ctx->last_run = st.iter;
   ctx->last_log_rows = w.log ? std::min<int64_t>(st.iter, w.log_max) : -1;
   ctx->last_log_np = w.nproj;
@@ -1029,6 +1037,47 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
   return solve_end(ctx, proj_out_host, info);
 }
 
+kw_status kw_resume(kw_ctx* ctx, int64_t more_iters, kw_c128* proj_out_host, kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  if (more_iters < 1) return fail(ctx, KW_ERR_ARG, "kw_resume: more_iters < 1");
+  if (!ctx->resumable)
+    return fail(ctx, KW_ERR_ARG, "kw_resume: the last kw_solve of this context did not stop at maxiter, or its "
+                                 "operator, method or workspace has changed since");
+  kw::Work& w = ctx->work;
+  const kw::State& sh = *ctx->st_host;   // read back by the last solve_end
+  const int64_t it = sh.iter;
+  ctx->resumable = false;
+  ctx->run_maxiter = it + more_iters;
+  memset(&ctx->stats, 0, sizeof(ctx->stats));
+  if (w.full && w.prec == kw::PREC_DF) {   // x was handed out as kw_c128: back to FP32 pairs
+    KW_CUDA(kw::launch_unfinish_x<kw::PREC_DF>(w), "kw_resume: x to pairs");
+  }
+  // restart the device loop: new cap, stop flag cleared, K1 counter reset
+  long long maxit = (long long)ctx->run_maxiter;
+  const int zero = 0, notconv = KW_NOT_CONVERGED;
+  const unsigned int uzero = 0;
+  KW_CUDA(cudaMemcpyAsync(&w.st->maxiter, &maxit, sizeof(maxit), cudaMemcpyHostToDevice, ctx->stream), "kw_resume");
+  KW_CUDA(cudaMemcpyAsync(&w.st->done, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "kw_resume");
+  KW_CUDA(cudaMemcpyAsync(&w.st->status, &notconv, sizeof(int), cudaMemcpyHostToDevice, ctx->stream), "kw_resume");
+  KW_CUDA(cudaMemcpyAsync(&w.st->cnt_spmv, &uzero, sizeof(uzero), cudaMemcpyHostToDevice, ctx->stream), "kw_resume");
+  // K1 of iteration `it` again: the one queued after the last K2 may have seen the stop flag
+  void* rn = (it & 1) ? w.rB : w.rA;
+  void* rtn = (it & 1) ? w.rtB : w.rtA;
+  cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_k1<kw::PREC_C32>(w, rn, rtn)
+                  : w.prec == kw::PREC_DF ? kw::launch_k1<kw::PREC_DF>(w, rn, rtn)
+                                          : kw::launch_k1<kw::PREC_F64>(w, rn, rtn);
+  if (e != cudaSuccess) {
+    if (w.mv_failed) {
+      cudaStreamSynchronize(ctx->stream);
+      return fail(ctx, KW_ERR_CALLBACK, "kw_resume: the matrix-vector callback returned nonzero");
+    }
+    return cuda_fail(ctx, e, "kw_resume: first product");
+  }
+  kw_status s = run_loop(ctx, it);
+  if (s != KW_OK) return s;
+  return solve_end(ctx, proj_out_host, info);
+}
+
 kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_solve_info* info) {
   if (!ctx) return KW_ERR_ARG;
   if (n < 1 || n > 65536 || !inst) return fail(ctx, KW_ERR_ARG, "kw_solve_batched: need 1 <= n <= 65536 instances");
@@ -1038,6 +1087,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     KW_CUDA(cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking), "kw_solve_batched: stream");
   cudaStream_t bs = ctx->batch_stream;
   ctx->last_log_rows = -1;   // the instances run on child contexts, which keep no log
+  ctx->resumable = false;
   {
     cudaEvent_t e0;
     KW_CUDA(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming), "kw_solve_batched: event");
@@ -1075,6 +1125,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     c->btilde = nullptr;
     c->overlap = ctx->overlap;
     if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
+    c->run_maxiter = c->opt.maxiter;
     KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
     kw_status s = kw_set_csr(c, inst[i].m, inst[i].nnz, inst[i].rowptr_dev, inst[i].col_dev, inst[i].val_dev);
     if (s == KW_OK)
@@ -1190,6 +1241,7 @@ kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowp
   if (st != KW_OK) return st;
   st = kw_solve(ctx, (const double*)ctx->h_b.p, nshift, z_host, nleft, nleft > 0 ? (const double*)ctx->h_left.p : nullptr,
                 x_out_host ? ctx->h_x.p : nullptr, proj_out_host, info);
+  ctx->resumable = false;   // its outputs went to host memory: kw_resume is for kw_solve
   if (x_out_host && (st == KW_OK || st == KW_NOT_CONVERGED || st == KW_ERR_BREAKDOWN || st == KW_ERR_NONFINITE))
     KW_CUDA(cudaMemcpy(x_out_host, ctx->h_x.p, (size_t)nshift * m * vs, cudaMemcpyDeviceToHost), "copy x");
   return st;
@@ -1363,6 +1415,7 @@ kw_status kw_set_method(kw_ctx* ctx, int method, const double* btilde_dev) {
     return fail(ctx, KW_ERR_ARG, "kw_set_method: a shadow start vector is for BiCG only");
   ctx->method = method;
   ctx->btilde = btilde_dev;
+  ctx->resumable = false;
   return KW_OK;
 }
 
@@ -1431,6 +1484,7 @@ kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, k
   KW_CUDA(ctx->part_k1.ensure(part_doubles(ctx, 1) * 8), "alloc partials");
   KW_CUDA(ctx->st.ensure(sizeof(kw::State)), "alloc state");
   KW_CUDA(ctx->tdot.ensure(16), "alloc dot");
+  ctx->resumable = false;   // shares the solve's state buffer
   kw::Work w;
   spmv_work(ctx, w, ctx->spmv_lanes, ctx->spmv_val_f32);
   KW_CUDA(cudaMemsetAsync(&w.st->cnt_spmv, 0, sizeof(unsigned int), ctx->stream), "reset counter");

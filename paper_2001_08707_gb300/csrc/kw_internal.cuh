@@ -168,6 +168,8 @@ template <int P> cudaError_t launch_init(Work& w);
 // first: the first iteration after launch_init or after join_streams (no wait for K3).
 template <int P> cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, int64_t* launches);
 template <int P> cudaError_t launch_finish_x(Work& w);
+template <int P> cudaError_t launch_unfinish_x(Work& w);
+template <int P> cudaError_t launch_k1(Work& w, void* r, void* rt);
 template <int P> cudaError_t launch_project_x(Work& w, double2* out);
 template <int P>
 cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, float4 zs_pair, double2* t_dev);

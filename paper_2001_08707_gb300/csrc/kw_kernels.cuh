@@ -1490,6 +1490,15 @@ k_project_x(int m, int np, const double* __restrict__ b, const double* __restric
 
 // In-place conversion of FP32-pair complex vectors to FP64 complex (same 16 bytes):
 // hi + lo is exact in FP64.
+// In place: kw_c128 back to FP32 pairs (a resumed pair-form solve continues
+// from the x that the previous solve converted for the caller).
+static __global__ void k_double_to_pairs(dfc* x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 d = reinterpret_cast<const double2*>(x)[i];
+    x[i] = {df_from_double(d.x), df_from_double(d.y)};
+  }
+}
+
 static __global__ void k_pairs_to_double(dfc* x, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const dfc v = x[i];
@@ -1871,6 +1880,13 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   return cudaSuccess;
 }
 
+// K1 on r (and r~ for BiCG) outside the iteration, as launch_init ends: used
+// when a stopped solve is resumed.
+template <int P>
+cudaError_t launch_k1(Work& w, void* r, void* rt) {
+  return k1_dispatch<P>(w, r, rt);
+}
+
 template <int P>
 cudaError_t launch_init(Work& w) {
   typedef typename PT<P>::V V;
@@ -1903,6 +1919,16 @@ cudaError_t launch_init(Work& w) {
   }
   // K1(0) on r_0 (rA); every iteration then enqueues the next K1 after its K2
   return k1_dispatch<P>(w, w.rA, w.rtA);
+}
+
+template <int P>
+cudaError_t launch_unfinish_x(Work& w) {
+  if constexpr (P == PREC_DF) {
+    k_double_to_pairs<<<8 * w.num_sms, 256, 0, w.stream>>>((dfc*)w.X, (long long)w.K * w.m);
+    return cudaGetLastError();
+  } else {
+    return cudaSuccess;
+  }
 }
 
 // Full-mode outputs: FP32-pair vectors are first converted to FP64 in place

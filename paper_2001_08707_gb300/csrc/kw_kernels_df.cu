@@ -7,6 +7,8 @@ namespace kw {
 template cudaError_t launch_init<PREC_DF>(Work&);
 template cudaError_t launch_iteration<PREC_DF>(Work&, int, int, cudaEvent_t*, int64_t*);
 template cudaError_t launch_finish_x<PREC_DF>(Work&);
+template cudaError_t launch_unfinish_x<PREC_DF>(Work&);
+template cudaError_t launch_k1<PREC_DF>(Work&, void*, void*);
 template cudaError_t launch_project_x<PREC_DF>(Work&, double2*);
 template cudaError_t launch_spmv_dot<PREC_DF>(Work&, const void*, void*, double2, float4, double2*);
 

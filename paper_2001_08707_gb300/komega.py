@@ -109,6 +109,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
+        "kw_resume": (C.c_int, [P, I64, P, C.POINTER(kw_solve_info)]),
         "kw_set_matvec_adjoint": (C.c_int, [P, MATVEC_FN, P]),
         "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
         "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
@@ -279,8 +280,24 @@ class Solver:
         info = kw_solve_info()
         st = self._lib.kw_solve(self._ctx, C.c_void_p(bd.data_ptr()), K, zp, nleft, lp, xp,
                                 proj.ctypes.data_as(C.c_void_p), C.byref(info))
+        self._last_solve = (bd, zz, ld, x, proj.shape)   # kept alive for kw_resume
         if check and st not in (KW_OK, KW_NOT_CONVERGED):
             raise self._err(st, "kw_solve") from getattr(self, "_mv_error", None)
+        return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
+                           info.seed, STATUS.get(st, str(st)))
+
+    def resume(self, more_iters: int, check: bool = True) -> SolveResult:
+        """kw_resume: continue the last solve (stopped at its iteration cap) for up
+        to more_iters further iterations; x (full mode) is the same tensor."""
+        last = getattr(self, "_last_solve", None)
+        if last is None:
+            raise KomegaError(KW_ERR_ARG, "resume: no solve to continue")
+        _, _, _, x, shape = last
+        proj = np.zeros(shape, dtype=np.complex128)
+        info = kw_solve_info()
+        st = self._lib.kw_resume(self._ctx, int(more_iters), proj.ctypes.data_as(C.c_void_p), C.byref(info))
+        if check and st not in (KW_OK, KW_NOT_CONVERGED):
+            raise self._err(st, "kw_resume")
         return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
                            info.seed, STATUS.get(st, str(st)))
 
