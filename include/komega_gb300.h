@@ -237,6 +237,43 @@ typedef struct {
     double tol;                    /* > 0 overrides the context's tolerance for this problem */
 } kw_instance;
 
+/* ---------------------------------------------------------------------------
+ * Reverse communication (Sec. 3.1 (iii), Algorithm 1): the caller computes
+ * every product itself, between calls, as the paper's *_init / *_update /
+ * *_getresidual / *_finalize flow does.  Each kw_rci_update runs one iteration
+ * synchronously (no host run-ahead, one stream), so it is slower than
+ * kw_set_matvec, which it otherwise matches bit for bit.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+    const void* r;   /* device [m]: the vector to multiply (elem type below) */
+    void* q;         /* device [m]: where the caller writes H r */
+    const void* rt;  /* BiCG: the shadow vector r~ (else NULL) */
+    void* qt;        /* BiCG: where the caller writes H^dagger r~ (else NULL) */
+    int elem;        /* KW_ELEM_C128, or KW_ELEM_C64 in the KW_C32V_F64S form */
+} kw_rci_io;
+
+/* Start a solve of (z_k I - H) x_k = b of size m (arguments as kw_solve) with
+ * the caller as the operator: any CSR matrix, callback or generated operator of
+ * ctx is dropped.  *io receives the first vectors.  The solver of
+ * kw_set_method is used (COCG by default).  Errors: those of kw_solve. */
+kw_status kw_rci_init(kw_ctx* ctx, int64_t m, const double* b_dev, int64_t nshift, const kw_c128* z_host,
+                      int64_t nleft, const double* left_dev, void* x_out_dev, kw_rci_io* io);
+
+/* After the caller has written q = H r (and, for BiCG, qt = H^dagger rt) for
+ * the vectors of the last *io: finish the iteration; *done = 1 when every
+ * shift has converged or the iteration cap or a breakdown was reached, else 0
+ * with the next vectors in *io (their addresses change between iterations).
+ * The vectors may still carry a pending seed-switch scale, which the library
+ * applies by linearity.  Errors: KW_ERR_ARG (no kw_rci_init), KW_ERR_CUDA. */
+kw_status kw_rci_update(kw_ctx* ctx, int* done, kw_rci_io* io);
+
+/* Current residual estimate ||r_n||/|pi_n^k| of every shift (host, [nshift]). */
+kw_status kw_rci_get_residual(kw_ctx* ctx, double* res_host);
+
+/* End the solve: outputs and status as kw_solve returns them.  ctx then has no
+ * operator until the next kw_set_csr, kw_set_matvec or generated operator. */
+kw_status kw_rci_finalize(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* info);
+
 /* Continue the last kw_solve of ctx for up to more_iters further iterations
  * (the "restart" mode of Sec. 3.3: a solve stopped by its iteration cap goes on
  * from where it stopped, on the device state the context kept).  Valid only

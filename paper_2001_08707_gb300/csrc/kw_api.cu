@@ -77,7 +77,10 @@ struct kw_ctx {
   void* mv_user = nullptr;
   kw_matvec_fn mv_fn_adj = nullptr;   // adjoint product for BiCG (NULL: Hermitian)
   void* mv_user_adj = nullptr;
-  DBuf mv_r, mv_q;
+  DBuf mv_r, mv_q, mv_r2, mv_q2;
+  // reverse communication (kw_rci_*)
+  bool rci_active = false;
+  int64_t rci_iter = 0;
   // solver of Table 1 (kw_set_method) and the BiCG shadow vectors
   int method = KW_METHOD_COCG;
   const double* btilde = nullptr;
@@ -222,7 +225,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->part_k1, &ctx->st, &ctx->projx, &ctx->tdot,
-                  &ctx->mv_r, &ctx->mv_q, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
+                  &ctx->mv_r, &ctx->mv_q, &ctx->mv_r2, &ctx->mv_q2, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag};
@@ -492,6 +495,10 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
   w.mv_user_adj = ctx->mv_user_adj;
   w.mv_r = ctx->mv_r.p;
   w.mv_q = ctx->mv_q.p;
+  w.mv_r2 = ctx->mv_r2.p;
+  w.mv_q2 = ctx->mv_q2.p;
+  w.rci = ctx->rci_active ? 1 : 0;
+  w.rci_phase = ctx->rci_active ? 1 : 0;
   if (lanes == kw::KW_SPMV_SELL) {
     if (p == KW_F64) w.val_f32 = 0;       // the SELL copy keeps FP64 values in the FP64 form
     w.sell_perm = (const int*)ctx->sell_perm.p;
@@ -634,7 +641,9 @@ static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 
 // and the pick would be noise); they use one thread per row and FP64 values.
 static const int64_t kTuneMinNnz = 1 << 20;
 
-static bool has_operator(const kw_ctx* ctx) { return ctx->rowptr || ctx->mv_fn || ctx->op >= kw::OP_SPIN; }
+static bool has_operator(const kw_ctx* ctx) {
+  return ctx->rowptr || ctx->mv_fn || ctx->rci_active || ctx->op >= kw::OP_SPIN;
+}
 
 static kw_status tune_spmv(kw_ctx* ctx) {
   if (ctx->op != kw::OP_CSR) {   // callback or generated operator: nothing to tune
@@ -832,7 +841,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.stream2 = ctx->stream2;
   w.ev_k2 = ctx->ev_k2;
   w.ev_k3 = ctx->ev_k3;
-  w.overlap = ctx->overlap;
+  w.overlap = ctx->rci_active ? 0 : ctx->overlap;   // one step per call under reverse communication
 
   KW_CUDA(cudaMemcpyAsync(w.z, z_host, K * 16, cudaMemcpyHostToDevice, ctx->stream), "upload shifts");
   kw::State& s = *ctx->st_host;
@@ -888,6 +897,8 @@ static cudaError_t iteration_launch(kw::Work& w, int parity, int first, cudaEven
 static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
                              const double* left_dev, void* x_out_dev) {
   if (!has_operator(ctx)) return fail(ctx, KW_ERR_ARG, "kw_solve: no operator has been set");
+  if (ctx->rci_active && ctx->rci_iter > 0)
+    return fail(ctx, KW_ERR_ARG, "kw_solve: a reverse-communication solve is in progress (kw_rci_finalize first)");
   if (!b_dev || !z_host || nshift < 1 || nshift > 0x7fffffffLL)
     return fail(ctx, KW_ERR_ARG, "kw_solve: need b, z and 1 <= nshift < 2^31");
   if (nleft < 0 || nleft >= KW_MAX_PROJ || (nleft > 0 && !left_dev))
@@ -1035,6 +1046,98 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
   s = run_loop(ctx);
   if (s != KW_OK) return s;
   return solve_end(ctx, proj_out_host, info);
+}
+
+static void rci_io(kw_ctx* ctx, kw_rci_io* io) {
+  if (!io) return;
+  const kw::Work& w = ctx->work;
+  io->r = w.rci_r;
+  io->q = w.rci_q;
+  io->rt = w.method == KW_METHOD_BICG ? w.rci_rt : nullptr;
+  io->qt = w.method == KW_METHOD_BICG ? w.rci_qt : nullptr;
+  io->elem = ctx->opt.prec == KW_C32V_F64S ? KW_ELEM_C64 : KW_ELEM_C128;
+}
+
+kw_status kw_rci_init(kw_ctx* ctx, int64_t m, const double* b_dev, int64_t nshift, const kw_c128* z_host,
+                      int64_t nleft, const double* left_dev, void* x_out_dev, kw_rci_io* io) {
+  if (!ctx) return KW_ERR_ARG;
+  if (m < 1 || m > 0x7fffffffLL || !io) return fail(ctx, KW_ERR_ARG, "kw_rci_init: need 1 <= m < 2^31 and io");
+  // the caller is the operator from now on
+  ctx->op = kw::OP_CALLBACK;
+  ctx->m = m;
+  ctx->nnz = 0;
+  ctx->rowptr = nullptr;
+  ctx->col = nullptr;
+  ctx->val = nullptr;
+  ctx->mv_fn = nullptr;
+  ctx->mv_user = nullptr;
+  ctx->mv_fn_adj = nullptr;
+  ctx->mv_user_adj = nullptr;
+  ctx->spmv_lanes = 1;
+  ctx->u_state = 0;
+  ctx->sell_built = false;
+  ctx->resumable = false;
+  ctx->rci_active = true;
+  if (ctx->opt.prec == KW_DF64) {
+    KW_CUDA(ctx->mv_r.ensure((size_t)m * 16), "kw_rci_init: staging");
+    KW_CUDA(ctx->mv_q.ensure((size_t)m * 16), "kw_rci_init: staging");
+    if (ctx->method == KW_METHOD_BICG) {
+      KW_CUDA(ctx->mv_r2.ensure((size_t)m * 16), "kw_rci_init: staging");
+      KW_CUDA(ctx->mv_q2.ensure((size_t)m * 16), "kw_rci_init: staging");
+    }
+  }
+  kw_status s = solve_begin(ctx, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
+  if (s != KW_OK) {
+    ctx->rci_active = false;
+    return s;
+  }
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_rci_init: sync");
+  ctx->rci_iter = 0;
+  rci_io(ctx, io);
+  return KW_OK;
+}
+
+kw_status kw_rci_update(kw_ctx* ctx, int* done, kw_rci_io* io) {
+  if (!ctx || !done) return KW_ERR_ARG;
+  if (!ctx->rci_active) return fail(ctx, KW_ERR_ARG, "kw_rci_update: no kw_rci_init");
+  kw::Work& w = ctx->work;
+  const int64_t n = ctx->rci_iter;
+  // finish iteration n's products (the caller wrote them), then K2, K3, K4 and the staging of r_{n+1}
+  w.rci_phase = 2;
+  void* rn = (n & 1) ? w.rB : w.rA;
+  void* rtn = (n & 1) ? w.rtB : w.rtA;
+  cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_k1<kw::PREC_C32>(w, rn, rtn)
+                  : w.prec == kw::PREC_DF ? kw::launch_k1<kw::PREC_DF>(w, rn, rtn)
+                                          : kw::launch_k1<kw::PREC_F64>(w, rn, rtn);
+  w.rci_phase = 1;
+  KW_CUDA(e, "kw_rci_update: products");
+  KW_CUDA(iteration_launch(w, (int)(n & 1), 1, nullptr, &ctx->stats.launches), "kw_rci_update: iteration");
+  int d = 0;
+  KW_CUDA(cudaMemcpyAsync(&d, &w.st->done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "kw_rci_update");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_rci_update: sync");
+  ctx->rci_iter = n + 1;
+  *done = d;
+  rci_io(ctx, io);
+  return KW_OK;
+}
+
+kw_status kw_rci_get_residual(kw_ctx* ctx, double* res_host) {
+  if (!ctx || !res_host) return KW_ERR_ARG;
+  if (!ctx->rci_active) return fail(ctx, KW_ERR_ARG, "kw_rci_get_residual: no kw_rci_init");
+  KW_CUDA(cudaMemcpy(res_host, ctx->work.final_res, (size_t)ctx->work_K * 8, cudaMemcpyDeviceToHost),
+          "kw_rci_get_residual");
+  return KW_OK;
+}
+
+kw_status kw_rci_finalize(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* info) {
+  if (!ctx) return KW_ERR_ARG;
+  if (!ctx->rci_active) return fail(ctx, KW_ERR_ARG, "kw_rci_finalize: no kw_rci_init");
+  ctx->rci_active = false;
+  kw_status s = solve_end(ctx, proj_out_host, info);
+  ctx->resumable = false;
+  ctx->op = kw::OP_CSR;   // no operator until the next kw_set_*
+  ctx->m = 0;
+  return s;
 }
 
 kw_status kw_resume(kw_ctx* ctx, int64_t more_iters, kw_c128* proj_out_host, kw_solve_info* info) {

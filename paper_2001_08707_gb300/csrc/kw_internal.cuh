@@ -140,6 +140,16 @@ struct Work {
   kw_matvec_fn mv_fn_adj = nullptr;   // q = H^dagger r (BiCG; NULL: H Hermitian)
   void* mv_user_adj = nullptr;
   int mv_adjoint = 0;                 // set while K1 forms the adjoint product
+  void* mv_r2 = nullptr;              // FP32-pair form, BiCG under reverse communication:
+  void* mv_q2 = nullptr;              // staging of the shadow product (both are outstanding)
+  // reverse communication (kw_rci_*): the caller computes the products between calls.
+  // rci_phase 1: stage the vectors and record them (no product); 2: finish the products
+  int rci = 0;
+  int rci_phase = 0;
+  const void* rci_r = nullptr;
+  void* rci_q = nullptr;
+  const void* rci_rt = nullptr;
+  void* rci_qt = nullptr;
   void* mv_r = nullptr;   // FP32-pair form: kw_c128 copy of r handed to the callback
   void* mv_q = nullptr;   // FP32-pair form: the callback's H r (kw_c128)
   int mv_failed = 0;      // set when the callback returned nonzero

@@ -1684,6 +1684,9 @@ static cudaError_t generated_dispatch(Work& w, const void* r, void* q, SpmvMode 
 }
 
 // K1 through the caller's matrix-vector callback.
+// Under reverse communication the same path is cut in two: phase 1 stages r
+// (and records where the caller finds r and puts H r), phase 2 finishes after
+// the caller's product.
 template <int P>
 static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
@@ -1691,19 +1694,35 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
   const void* rin = r;
   void* hq = q;
   if constexpr (P == PREC_DF) {
-    if (!w.mv_r || !w.mv_q) return cudaErrorInvalidValue;
-    k_pairs_to_c128<<<4 * w.num_sms, 256, 0, w.stream>>>((int)w.m, (const dfc*)r, (double2*)w.mv_r, w.st,
-                                                        mode.solver);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    rin = w.mv_r;
-    hq = w.mv_q;
+    void* sr = (w.rci && w.mv_adjoint) ? w.mv_r2 : w.mv_r;
+    void* sq = (w.rci && w.mv_adjoint) ? w.mv_q2 : w.mv_q;
+    if (!sr || !sq) return cudaErrorInvalidValue;
+    if (w.rci_phase != 2) {
+      k_pairs_to_c128<<<4 * w.num_sms, 256, 0, w.stream>>>((int)w.m, (const dfc*)r, (double2*)sr, w.st,
+                                                          mode.solver);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    rin = sr;
+    hq = sq;
   }
-  kw_matvec_fn fn = (w.mv_adjoint && w.mv_fn_adj) ? w.mv_fn_adj : w.mv_fn;
-  void* user = (w.mv_adjoint && w.mv_fn_adj) ? w.mv_user_adj : w.mv_user;
-  if (fn(user, rin, hq, w.m, P == PREC_C32 ? KW_ELEM_C64 : KW_ELEM_C128, (void*)w.stream) != 0) {
-    w.mv_failed = 1;
-    return cudaErrorUnknown;
+  if (w.rci_phase == 1) {     // the caller computes H r between the calls
+    if (w.mv_adjoint) {
+      w.rci_rt = rin;
+      w.rci_qt = hq;
+    } else {
+      w.rci_r = rin;
+      w.rci_q = hq;
+    }
+    return cudaSuccess;
+  }
+  if (w.rci_phase != 2) {
+    kw_matvec_fn fn = (w.mv_adjoint && w.mv_fn_adj) ? w.mv_fn_adj : w.mv_fn;
+    void* user = (w.mv_adjoint && w.mv_fn_adj) ? w.mv_user_adj : w.mv_user;
+    if (fn(user, rin, hq, w.m, P == PREC_C32 ? KW_ELEM_C64 : KW_ELEM_C128, (void*)w.stream) != 0) {
+      w.mv_failed = 1;
+      return cudaErrorUnknown;
+    }
   }
   static int nblk = 0;
   if (nblk == 0) nblk = resident_blocks(k_matvec_finish<P>, 256, w.num_sms);
@@ -1714,7 +1733,7 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
 
 template <int P>
 static cudaError_t spmv_dispatch(Work& w, const void* r, void* q, SpmvMode mode) {
-  if (w.mv_fn) return matvec_dispatch<P>(w, r, q, mode);
+  if (w.mv_fn || w.rci) return matvec_dispatch<P>(w, r, q, mode);
   if (w.op == OP_SPIN || w.op == OP_LATTICE) return generated_dispatch<P>(w, r, q, mode);
   if (w.spmv_lanes > KW_SPMV_UNIFORM) return uniform_dispatch<P>(w, r, q, mode);
   if constexpr (P == PREC_F64) {
@@ -1790,6 +1809,7 @@ static cudaError_t k1_dispatch(Work& w, void* r, void* rt) {
   e = spmv_dispatch<P>(w, rt, w.qt, ms);
   w.mv_adjoint = 0;
   if (e != cudaSuccess) return e;
+  if (w.rci_phase == 1) return cudaSuccess;   // the products are the caller's to make first
   SpmvMode md = mode;
   md.dot = 1;
   static int nblk = 0;

@@ -52,6 +52,10 @@ class kw_instance(C.Structure):
                 ("proj_out_host", C.c_void_p), ("tol", C.c_double)]
 
 
+class kw_rci_io(C.Structure):
+    _fields_ = [("r", C.c_void_p), ("q", C.c_void_p), ("rt", C.c_void_p), ("qt", C.c_void_p), ("elem", C.c_int)]
+
+
 class kw_stats(C.Structure):
     _fields_ = [("launches", C.c_int64), ("timed_iters", C.c_int64), ("kernel_ms", C.c_double * 4)]
 
@@ -110,6 +114,10 @@ def load_library(path: str = LIB_PATH):
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
         "kw_resume": (C.c_int, [P, I64, P, C.POINTER(kw_solve_info)]),
+        "kw_rci_init": (C.c_int, [P, I64, P, I64, P, I64, P, P, C.POINTER(kw_rci_io)]),
+        "kw_rci_update": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(kw_rci_io)]),
+        "kw_rci_get_residual": (C.c_int, [P, P]),
+        "kw_rci_finalize": (C.c_int, [P, P, C.POINTER(kw_solve_info)]),
         "kw_set_matvec_adjoint": (C.c_int, [P, MATVEC_FN, P]),
         "kw_get_krylov_log": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64), C.POINTER(D), P, P]),
         "kw_recalc": (C.c_int, [P, I64, I64, D, P, P, I64, P, P, P, P, C.POINTER(kw_solve_info)]),
@@ -283,6 +291,61 @@ class Solver:
         self._last_solve = (bd, zz, ld, x, proj.shape)   # kept alive for kw_resume
         if check and st not in (KW_OK, KW_NOT_CONVERGED):
             raise self._err(st, "kw_solve") from getattr(self, "_mv_error", None)
+        return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
+                           info.seed, STATUS.get(st, str(st)))
+
+    # ------------------------------------------------------------------ reverse communication
+    def _rci_views(self, io):
+        torch = self._torch
+        ts = "<f8" if io.elem == KW_ELEM_C128 else "<f4"
+        view = lambda ptr: None if not ptr else torch.view_as_complex(
+            torch.as_tensor(_DeviceVector(ptr, self.m, ts), device="cuda"))
+        return view(io.r), view(io.q), view(io.rt), view(io.qt)
+
+    def rci_init(self, b, z, left=None, full: bool = False):
+        """kw_rci_init: start a solve whose products the caller makes.  Returns
+        (r, q, rt, qt) tensor views: write H r into q (and H^dagger rt into qt
+        for BiCG), then call rci_update."""
+        t = self._torch
+        bd = self._dev(b, t.float64)
+        zz, zp = _z_array(z)
+        ld = None if left is None else self._dev(np.atleast_2d(left), t.float64)
+        nleft = 0 if ld is None else ld.shape[0]
+        self.m = bd.numel()
+        x = t.empty((zz.size, self.m), dtype=self.vec_dtype, device="cuda") if full else None
+        io = kw_rci_io()
+        st = self._lib.kw_rci_init(self._ctx, self.m, C.c_void_p(bd.data_ptr()), zz.size, zp, nleft,
+                                   None if ld is None else C.c_void_p(ld.data_ptr()),
+                                   None if x is None else C.c_void_p(x.data_ptr()), C.byref(io))
+        if st != KW_OK:
+            raise self._err(st, "kw_rci_init")
+        self._rci = (bd, zz, ld, x, (zz.size, nleft + 1))
+        return self._rci_views(io)
+
+    def rci_update(self):
+        """kw_rci_update: finish the iteration; returns (done, (r, q, rt, qt))."""
+        d = C.c_int()
+        io = kw_rci_io()
+        st = self._lib.kw_rci_update(self._ctx, C.byref(d), C.byref(io))
+        if st != KW_OK:
+            raise self._err(st, "kw_rci_update")
+        return bool(d.value), self._rci_views(io)
+
+    def rci_residual(self):
+        K = self._rci[1].size
+        res = np.zeros(K)
+        st = self._lib.kw_rci_get_residual(self._ctx, res.ctypes.data_as(C.c_void_p))
+        if st != KW_OK:
+            raise self._err(st, "kw_rci_get_residual")
+        return res
+
+    def rci_finalize(self, check: bool = True) -> SolveResult:
+        _, _, _, x, shape = self._rci
+        proj = np.zeros(shape, dtype=np.complex128)
+        info = kw_solve_info()
+        st = self._lib.kw_rci_finalize(self._ctx, proj.ctypes.data_as(C.c_void_p), C.byref(info))
+        if check and st not in (KW_OK, KW_NOT_CONVERGED):
+            raise self._err(st, "kw_rci_finalize")
         return SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch, info.updates,
                            info.seed, STATUS.get(st, str(st)))
 
