@@ -51,6 +51,27 @@ struct DBuf {
   }
 };
 
+// Events destroyed when the holder goes out of scope (every return path).
+struct ScopedEvents {
+  std::vector<cudaEvent_t> ev;
+  cudaError_t create(size_t n, unsigned flags) {
+    ev.assign(n, nullptr);
+    for (auto& e : ev) {
+      cudaError_t r = cudaEventCreateWithFlags(&e, flags);
+      if (r != cudaSuccess) {
+        e = nullptr;
+        return r;
+      }
+    }
+    return cudaSuccess;
+  }
+  cudaEvent_t operator[](size_t i) const { return ev[i]; }
+  ~ScopedEvents() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace
 
 struct kw_ctx {
@@ -689,9 +710,9 @@ static kw_status tune_spmv(kw_ctx* ctx) {
     vals[0] = (ctx->force_val && ctx->val32_exact) ? 1 : 0;
     nvals = 1;
   }
-  cudaEvent_t e0, e1;
-  KW_CUDA(cudaEventCreate(&e0), "tune event");
-  KW_CUDA(cudaEventCreate(&e1), "tune event");
+  ScopedEvents tev;
+  KW_CUDA(tev.create(2, cudaEventDefault), "tune events");
+  cudaEvent_t e0 = tev[0], e1 = tev[1];
   float best = 1e30f;
   int best_l = 4, best_v = vals[0];
   // Candidates are visited in a fixed order; a later one replaces the current
@@ -727,8 +748,6 @@ static kw_status tune_spmv(kw_ctx* ctx) {
       }
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   KW_CUDA(cudaGetLastError(), "tune launches");
   ctx->spmv_lanes = best_l;
   ctx->spmv_val_f32 = best_l == kw::KW_SPMV_SELL ? (p == KW_F64 ? 0 : best_v) : best_v;
@@ -1213,13 +1232,10 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     ctx->children.push_back(c);
   }
   // begin every instance on its own stream; the batch stream waits for all initialisations
-  std::vector<cudaEvent_t> ev(n + 1, nullptr);
-  for (int64_t i = 0; i <= n; ++i) KW_CUDA(cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming), "batch events");
+  ScopedEvents ev;
+  KW_CUDA(ev.create((size_t)n + 1, cudaEventDisableTiming), "batch events");
   kw_status result = KW_OK;
-  auto cleanup = [&]() {
-    for (cudaEvent_t e : ev)
-      if (e) cudaEventDestroy(e);
-  };
+  auto cleanup = [&]() {};   // the events are released by their holder
   KW_CUDA(cudaEventRecord(ev[n], bs), "batch event");   // instances start after the caller's work
   for (int64_t i = 0; i < n; ++i) {
     kw_ctx* c = ctx->children[i];

@@ -1526,19 +1526,23 @@ static __global__ void k_f64_to_pair(const double* __restrict__ in, df* __restri
 
 // ================================================================ launchers
 // Blocks that fit on the device at once for a kernel with the given block size.
+// per_sm caches the occupancy of the kernel (a property of the kernel and the
+// architecture); the SM count is the current context's.
 template <class F>
-static int resident_blocks(F kernel, int threads, int num_sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
+static int resident_blocks(int& per_sm, F kernel, int threads, int num_sms) {
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) b = 1;
+    per_sm = b;
+  }
   return per_sm * num_sms;
 }
 
 template <int P, class RV, int G>
 static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_spmv_dot<P, RV, G>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_spmv_dot<P, RV, G>, 256, w.num_sms);
   const int need = (int)((w.m * G + 255) / 256);   // no more blocks than rows need
   const int grid = std::max(1, std::min(nblk, need));
   k_spmv_dot<P, RV, G><<<grid, 256, 0, w.stream>>>((int)w.m, w.rowptr, w.col, (const RV*)w.val,
@@ -1549,8 +1553,8 @@ static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
 template <int P, class RV>
 static cudaError_t sell_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_spmv_sell<P, RV>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_spmv_sell<P, RV>, 256, w.num_sms);
   const int nslice = (int)((w.m + 31) / 32);
   const int grid = std::max(1, std::min(nblk, (nslice + 7) / 8));
   k_spmv_sell<P, RV><<<grid, 256, 0, w.stream>>>((int)w.m, nslice, w.sell_perm, w.sell_len, w.sell_ptr,
@@ -1577,8 +1581,8 @@ static cudaError_t spmv_dispatch_v(Work& w, const void* r, void* q, SpmvMode mod
 template <int P, class DV, int G>
 static cudaError_t uniform_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_spmv_u<P, DV, G>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_spmv_u<P, DV, G>, 256, w.num_sms);
   const int need = (int)((w.m * G + 255) / 256);
   const int grid = std::max(1, std::min(nblk, need));
   DV uv;
@@ -1637,14 +1641,14 @@ static cudaError_t spin_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
   const int need = (int)((w.m + 255) / 256);
   if (w.sp_uniform) {
-    static int nblk = 0;
-    if (nblk == 0) nblk = resident_blocks(k_spmv_spin<P, DV, true>, 256, w.num_sms);
+    static int nblk_per_sm = 0;
+    const int nblk = resident_blocks(nblk_per_sm, k_spmv_spin<P, DV, true>, 256, w.num_sms);
     k_spmv_spin<P, DV, true><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
         (int)w.m, w.sp_basis, w.sp_binom, w.sp_bond, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag,
         dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part_k1, mode);
   } else {
-    static int nblk = 0;
-    if (nblk == 0) nblk = resident_blocks(k_spmv_spin<P, DV, false>, 256, w.num_sms);
+    static int nblk_per_sm = 0;
+    const int nblk = resident_blocks(nblk_per_sm, k_spmv_spin<P, DV, false>, 256, w.num_sms);
     k_spmv_spin<P, DV, false><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
         (int)w.m, w.sp_basis, w.sp_binom, w.sp_bond, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag,
         dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part_k1, mode);
@@ -1655,8 +1659,8 @@ static cudaError_t spin_launch(Work& w, const void* r, void* q, SpmvMode mode) {
 template <int P, class DV>
 static cudaError_t lattice_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_spmv_lattice<P, DV>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_spmv_lattice<P, DV>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   k_spmv_lattice<P, DV><<<grid, 256, 0, w.stream>>>((int)w.m, w.lx, w.ly, w.lz, (const DV*)w.u_diag,
                                                    dv_from_double<DV>(w.u_v), (const V*)r, (V*)q, w.st, w.part_k1,
@@ -1724,8 +1728,8 @@ static cudaError_t matvec_dispatch(Work& w, const void* r, void* q, SpmvMode mod
       return cudaErrorUnknown;
     }
   }
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_matvec_finish<P>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_matvec_finish<P>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   k_matvec_finish<P><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)r, (const H*)hq, (V*)q, w.st, w.part_k1, mode);
   return cudaGetLastError();
@@ -1751,8 +1755,8 @@ template <int P, int NP, int METHOD>
 static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_seed_update<P, NP, METHOD>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_seed_update<P, NP, METHOD>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   // shadow buffers rotate like the residual buffers (parity 0: r~_n in rtA)
   const void* rtn = parity ? w.rtB : w.rtA;
@@ -1812,8 +1816,8 @@ static cudaError_t k1_dispatch(Work& w, void* r, void* rt) {
   if (w.rci_phase == 1) return cudaSuccess;   // the products are the caller's to make first
   SpmvMode md = mode;
   md.dot = 1;
-  static int nblk = 0;
-  if (nblk == 0) nblk = resident_blocks(k_dot_tail<P>, 256, w.num_sms);
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_dot_tail<P>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   k_dot_tail<P><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)rt, (const V*)w.q, w.st, w.part_k1, md);
   return cudaGetLastError();
@@ -1887,8 +1891,8 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   KW_MARK(4, s2);
   *launches += (w.mv_fn && P == PREC_DF) ? 4 : 3;
   if (w.full) {
-    static int nblk_xp = 0;
-    if (nblk_xp == 0) nblk_xp = resident_blocks(k_update_xp<P, 8>, 256, w.num_sms);
+    static int nblk_xp_per_sm = 0;
+    const int nblk_xp = resident_blocks(nblk_xp_per_sm, k_update_xp<P, 8>, 256, w.num_sms);
     k_update_xp<P, 8><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
                                                       (const V*)rm, w.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
