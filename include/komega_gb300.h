@@ -181,6 +181,15 @@ kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user);
 kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const int32_t* bonds_host,
                                const double* J_host, const double* h_host);
 
+/* Spin operator storage.  on = 0 (default): every product regenerates the
+ * exchanged words' rows from the combinatorial number system (4 + 4 bytes per
+ * row: basis word and diagonal).  on = 1: the context also keeps an exchange
+ * table of nbond * M int32 (the row of each bond's exchanged word, -1 for
+ * parallel spins), stored bond by bond so that a warp's rows read each bond
+ * together, and the product only gathers.  Applies to the current spin
+ * operator at once and to later ones.  Errors: KW_ERR_ARG, KW_ERR_OOM. */
+kw_status kw_set_spin_table(kw_ctx* ctx, int on);
+
 /* Set the operator H to a tight-binding model on a periodic nx x ny x nz
  * lattice, generated on the fly: H_ii = eps_i, H_ij = hopping for the six
  * nearest neighbours j of site i = x + nx (y + ny z) (the Anderson model of

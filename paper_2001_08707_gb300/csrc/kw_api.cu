@@ -87,8 +87,9 @@ struct kw_ctx {
   const double* val = nullptr;
   // operator generated on the fly (kw_set_spin_operator, kw_set_lattice3d)
   int op = kw::OP_CSR;
-  DBuf sp_binom, sp_basis, sp_bond, sp_J, sp_h, sp_val;
+  DBuf sp_binom, sp_basis, sp_bond, sp_J, sp_h, sp_val, sp_table;
   int sp_nbond = 0, sp_uniform = 0;
+  bool sp_table_on = false, sp_table_built = false;
   int lx = 0, ly = 0, lz = 0;
   DBuf g_diag64, g_diag32, g_diagpair;   // diagonal (spin) or on-site energies (lattice)
   int g_kind = 0;                        // storage read by the form (kw::Work::u_kind)
@@ -247,7 +248,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->part_k1, &ctx->st, &ctx->projx, &ctx->tdot,
                   &ctx->mv_r, &ctx->mv_q, &ctx->mv_r2, &ctx->mv_q2, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
-                  &ctx->sp_h, &ctx->sp_val, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
+                  &ctx->sp_h, &ctx->sp_val, &ctx->sp_table, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag};
   for (DBuf* b : bufs) b->release();
@@ -402,6 +403,14 @@ kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const
                                 (unsigned*)ctx->sp_basis.p, (double*)ctx->g_diag64.p, ctx->stream),
           "kw_set_spin_operator: set-up");
   become_generated(ctx, kw::OP_SPIN, m);
+  ctx->sp_table_built = false;
+  if (ctx->sp_table_on) {
+    KW_CUDA(ctx->sp_table.ensure((size_t)nbond * m * 4), "kw_set_spin_operator: exchange table");
+    KW_CUDA(kw::launch_spin_table((int)m, nbond, (const int*)ctx->sp_bond.p, (const int*)ctx->sp_binom.p,
+                                  (const unsigned*)ctx->sp_basis.p, (int*)ctx->sp_table.p, ctx->stream),
+            "kw_set_spin_operator: exchange table");
+    ctx->sp_table_built = true;
+  }
   kw_status st = generated_diag(ctx, m, exact32);
   if (st != KW_OK) return st;
   ctx->sp_nbond = nbond;
@@ -424,6 +433,27 @@ kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const
     }
   }
   KW_CUDA(cudaMemcpy(ctx->sp_val.p, vals.data(), vals.size(), cudaMemcpyHostToDevice), "operator upload");
+  return KW_OK;
+}
+
+kw_status kw_set_spin_table(kw_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return KW_ERR_ARG;
+  ctx->sp_table_on = on == 1;
+  if (ctx->op != kw::OP_SPIN) return KW_OK;   // takes effect at the next kw_set_spin_operator
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_set_spin_table: sync");
+  if (!on) {
+    ctx->sp_table.release();
+    ctx->sp_table_built = false;
+    return KW_OK;
+  }
+  if (!ctx->sp_table_built) {
+    KW_CUDA(ctx->sp_table.ensure((size_t)ctx->sp_nbond * ctx->m * 4), "kw_set_spin_table: allocation");
+    KW_CUDA(kw::launch_spin_table((int)ctx->m, ctx->sp_nbond, (const int*)ctx->sp_bond.p, (const int*)ctx->sp_binom.p,
+                                  (const unsigned*)ctx->sp_basis.p, (int*)ctx->sp_table.p, ctx->stream),
+            "kw_set_spin_table: build");
+    KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_set_spin_table: sync");
+    ctx->sp_table_built = true;
+  }
   return KW_OK;
 }
 
@@ -505,6 +535,7 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
     w.sp_val = ctx->sp_val.p;
     w.sp_nbond = ctx->sp_nbond;
     w.sp_uniform = ctx->sp_uniform;
+    w.sp_table = (ctx->op == kw::OP_SPIN && ctx->sp_table_built) ? (const int*)ctx->sp_table.p : nullptr;
     w.lx = ctx->lx;
     w.ly = ctx->ly;
     w.lz = ctx->lz;

@@ -126,6 +126,7 @@ struct Work {
   const void* sp_val = nullptr;         // [nbond] J_b/2 in the diagonal's storage (when not uniform)
   int sp_nbond = 0;
   int sp_uniform = 0;                   // every J_b equal: one value u_v
+  const int* sp_table = nullptr;        // optional [nbond][m] exchange columns (-1: parallel spins)
   // lattice operator (kw_set_lattice3d): eps in u_diag/u_kind, hopping in u_v
   int lx = 0, ly = 0, lz = 0;
   // solver of Table 1 and the BiCG shadow vectors (rotating like rA/rB) and A^dagger r~
@@ -209,6 +210,10 @@ cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int6
 // nup set), and the FP64 diagonal (bond terms +-J/4, field terms +-h/2).
 cudaError_t launch_spin_setup(int m, int nsite, int nup, int nbond, const int* bond, const double* J, const double* h,
                               int* binom, unsigned* basis, double* diag, cudaStream_t s);
+// Exchange table of a spin operator: table[b*m + row] = the row of the word with
+// bond b's spins exchanged, or -1 when they are parallel.
+cudaError_t launch_spin_table(int m, int nbond, const int* bond, const int* binom, const unsigned* basis, int* table,
+                              cudaStream_t s);
 
 // Batched solves: count of instances whose solve has stopped (written to *out).
 cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_t s);

@@ -444,6 +444,88 @@ __device__ __forceinline__ bool k1_seed(const State* st, const SpmvMode& mode, V
   return true;
 }
 
+// Row of the word sw (row `row`) with the spins of bond (a, c), a < c, exchanged
+// (they differ): the combinatorial-number-system rank change described below.
+__device__ __forceinline__ int spin_exchange_row(unsigned sw, int row, int a, int c, const int* binom) {
+  const int t = __popc(sw & ((1u << a) - 1u));
+  unsigned mid = sw & ((1u << c) - 1u) & ~((2u << a) - 1u);   // set bits strictly between a and c
+  const int mc = __popc(mid);
+  int d = binom[c * KW_BINOM_K + t + mc + 1] - binom[a * KW_BINOM_K + t + 1];
+  for (int u = 1; mid; ++u) {
+    const int qb = __ffs(mid) - 1;
+    d += binom[qb * KW_BINOM_K + t + u] - binom[qb * KW_BINOM_K + t + u + 1];
+    mid &= mid - 1u;
+  }
+  return ((sw >> a) & 1u) ? row + d : row - d;
+}
+
+// K1 for a spin operator with a precomputed exchange table (slot-major: the
+// rows of a warp read slot b together, coalesced, and gather bond b's
+// exchanged words together, which lie close to each other).
+template <int P, class DV, bool UNI>
+__global__ void __launch_bounds__(256)
+k_spmv_spin_tab(int m, const int* __restrict__ table, const DV* __restrict__ val_g, int nbond,
+                const DV* __restrict__ diag, DV uv, const typename PT<P>::V* __restrict__ r,
+                typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  __shared__ DV bval[UNI ? 1 : KW_SPIN_MAX_BONDS];
+  if constexpr (!UNI) {
+    for (int i = threadIdx.x; i < nbond; i += blockDim.x) bval[i] = val_g[i];
+    __syncthreads();
+  }
+  V zsv;
+  if (!k1_seed<V>(st, mode, zsv)) return;
+  const int lane = threadIdx.x & 31;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = blockIdx.x * blockDim.x; base < m; base += stride) {   // uniform trip count per warp
+    const int row = base + (int)threadIdx.x;
+    if (row < m) {
+      V sum = vzero<V>();
+      int b = 0;
+      for (; b + 3 < nbond; b += 4) {        // four slots' columns, then their gathers
+        const int c0 = table[(size_t)b * m + row], c1 = table[(size_t)(b + 1) * m + row];
+        const int c2 = table[(size_t)(b + 2) * m + row], c3 = table[(size_t)(b + 3) * m + row];
+        if constexpr (UNI) {
+          if (c0 >= 0) vacc(sum, r[c0]);
+          if (c1 >= 0) vacc(sum, r[c1]);
+          if (c2 >= 0) vacc(sum, r[c2]);
+          if (c3 >= 0) vacc(sum, r[c3]);
+        } else {
+          if (c0 >= 0) mac(sum, bval[b], r[c0]);
+          if (c1 >= 0) mac(sum, bval[b + 1], r[c1]);
+          if (c2 >= 0) mac(sum, bval[b + 2], r[c2]);
+          if (c3 >= 0) mac(sum, bval[b + 3], r[c3]);
+        }
+      }
+      for (; b < nbond; ++b) {
+        const int cb = table[(size_t)b * m + row];
+        if (cb >= 0) {
+          if constexpr (UNI) vacc(sum, r[cb]);
+          else mac(sum, bval[b], r[cb]);
+        }
+      }
+      V hr = vzero<V>();
+      const V ri = r[row];
+      mac(hr, diag[row], ri);
+      if constexpr (UNI) mac(hr, uv, normalize(sum));
+      else vacc(hr, normalize(sum));
+      hr = normalize(hr);
+      k1_emit(row, ri, hr, zsv, q, c_re, c_im, mode.conj_dot);
+    }
+    if (++in_chunk == PT<P>::CHUNK) {
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
 // K1 for a spin-1/2 operator generated on the fly (kw_set_spin_operator).  One
 // thread per basis word s (row = its rank).  For every bond (a, c), a < c, whose
 // spins differ, the exchanged word s' is s with the up spin moved across the
@@ -486,16 +568,7 @@ k_spmv_spin(int m, const unsigned* __restrict__ basis, const int* __restrict__ b
       for (int b = 0; b < nbond; ++b) {
         const int a = bond[b] & 255, c = bond[b] >> 8;
         if ((((sw >> a) ^ (sw >> c)) & 1u) == 0) continue;   // parallel spins: no exchange
-        const int t = __popc(sw & ((1u << a) - 1u));
-        unsigned mid = sw & ((1u << c) - 1u) & ~((2u << a) - 1u);   // set bits strictly between a and c
-        const int mc = __popc(mid);
-        int d = binom[c * KW_BINOM_K + t + mc + 1] - binom[a * KW_BINOM_K + t + 1];
-        for (int u = 1; mid; ++u) {
-          const int qb = __ffs(mid) - 1;
-          d += binom[qb * KW_BINOM_K + t + u] - binom[qb * KW_BINOM_K + t + u + 1];
-          mid &= mid - 1u;
-        }
-        const int colx = ((sw >> a) & 1u) ? row + d : row - d;
+        const int colx = spin_exchange_row(sw, row, a, c, binom);
         if constexpr (UNI) vacc(sum, r[colx]);
         else mac(sum, bval[b], r[colx]);
       }
@@ -1640,6 +1713,22 @@ template <int P, class DV>
 static cudaError_t spin_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   typedef typename PT<P>::V V;
   const int need = (int)((w.m + 255) / 256);
+  if (w.sp_table) {
+    if (w.sp_uniform) {
+      static int per_sm = 0;
+      const int nblk = resident_blocks(per_sm, k_spmv_spin_tab<P, DV, true>, 256, w.num_sms);
+      k_spmv_spin_tab<P, DV, true><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
+          (int)w.m, w.sp_table, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag, dv_from_double<DV>(w.u_v),
+          (const V*)r, (V*)q, w.st, w.part_k1, mode);
+    } else {
+      static int per_sm = 0;
+      const int nblk = resident_blocks(per_sm, k_spmv_spin_tab<P, DV, false>, 256, w.num_sms);
+      k_spmv_spin_tab<P, DV, false><<<std::max(1, std::min(nblk, need)), 256, 0, w.stream>>>(
+          (int)w.m, w.sp_table, (const DV*)w.sp_val, w.sp_nbond, (const DV*)w.u_diag, dv_from_double<DV>(w.u_v),
+          (const V*)r, (V*)q, w.st, w.part_k1, mode);
+    }
+    return cudaGetLastError();
+  }
   if (w.sp_uniform) {
     static int nblk_per_sm = 0;
     const int nblk = resident_blocks(nblk_per_sm, k_spmv_spin<P, DV, true>, 256, w.num_sms);

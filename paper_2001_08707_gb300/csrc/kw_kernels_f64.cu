@@ -262,6 +262,27 @@ static __global__ void k_spin_diag(int m, int nsite, int nbond, const int* __res
   }
 }
 
+static __global__ void k_spin_table(int m, int nbond, const int* __restrict__ bond, const int* __restrict__ binom_g,
+                                    const unsigned* __restrict__ basis, int* __restrict__ table) {
+  __shared__ int binom[KW_BINOM_N * KW_BINOM_K];
+  for (int i = threadIdx.x; i < KW_BINOM_N * KW_BINOM_K; i += blockDim.x) binom[i] = binom_g[i];
+  __syncthreads();
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < m; row += gridDim.x * blockDim.x) {
+    const unsigned sw = basis[row];
+    for (int b = 0; b < nbond; ++b) {
+      const int a = bond[b] & 255, c = bond[b] >> 8;
+      table[(size_t)b * m + row] = (((sw >> a) ^ (sw >> c)) & 1u) ? spin_exchange_row(sw, row, a, c, binom) : -1;
+    }
+  }
+}
+
+cudaError_t launch_spin_table(int m, int nbond, const int* bond, const int* binom, const unsigned* basis, int* table,
+                              cudaStream_t s) {
+  const int grid = std::max(1, std::min(8192, (m + 255) / 256));
+  k_spin_table<<<grid, 256, 0, s>>>(m, nbond, bond, binom, basis, table);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spin_setup(int m, int nsite, int nup, int nbond, const int* bond, const double* J, const double* h,
                               int* binom, unsigned* basis, double* diag, cudaStream_t s) {
   k_binom<<<1, 1, 0, s>>>(binom);

@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_matvec": (C.c_int, [P, I64, MATVEC_FN, P]),
         "kw_set_spin_operator": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P]),
         "kw_set_lattice3d": (C.c_int, [P, I64, I64, I64, P, D]),
+        "kw_set_spin_table": (C.c_int, [P, C.c_int]),
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
@@ -474,6 +475,13 @@ class Solver:
 
         self._keep = []
         self.m = comb(int(nsite), int(nup))
+
+    def set_spin_table(self, on: bool):
+        """kw_set_spin_table: keep an exchange table for the spin operator (True)
+        or regenerate the exchanged rows in every product (False, default)."""
+        st = self._lib.kw_set_spin_table(self._ctx, 1 if on else 0)
+        if st != KW_OK:
+            raise self._err(st, "kw_set_spin_table")
 
     def set_lattice3d(self, nx: int, ny: int, nz: int, eps, hopping: float = -1.0):
         """kw_set_lattice3d: periodic nearest-neighbour lattice, H_ii = eps_i,

@@ -160,10 +160,12 @@ def _check_step(s, Hs, prec):
     assert abs(t - np.dot(rr, q_ref)) <= (1e-12 if prec == "f64" else 1e-5) * np.sum(np.abs(rr * q_ref))
 
 
+@pytest.mark.parametrize("table", [False, True])
 @pytest.mark.parametrize("prec", ["f64", "c32", "df64"])
 @pytest.mark.parametrize("case", SPIN)
-def test_spin_operator_step(case, prec):
+def test_spin_operator_step(case, prec, table):
     s = kw.Solver(prec)
+    s.set_spin_table(table)
     Hs = _set_spin(s, case)
     assert s.m == Hs.shape[0]
     _check_step(s, Hs, prec)
@@ -178,9 +180,12 @@ def test_lattice_operator_step(case, prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "df64"])
-@pytest.mark.parametrize("case", ["heisenberg_N14", "j1j2_N12", "anderson_L10"])
+@pytest.mark.parametrize("case", ["heisenberg_N14", "j1j2_N12", "anderson_L10", "j1j2_N12_table"])
 def test_generated_operator_converged_solve(case, prec):
     s = kw.Solver(prec, tol=1e-10, maxiter=20000)
+    if case.endswith("_table"):
+        s.set_spin_table(True)
+        case = case[: -len("_table")]
     Hs = _set_lattice(s, case) if case.startswith("anderson") else _set_spin(s, case)
     m = Hs.shape[0]
     b = w.gaussian_unit(m, 31)
@@ -195,6 +200,22 @@ def test_generated_operator_converged_solve(case, prec):
     scale = np.abs(ro.proj).max(axis=0)
     norms = np.linalg.norm(np.vstack([b, left]), axis=1)
     assert np.all(np.abs(r.proj - ro.proj) <= 1e-10 * scale[None, :] + 2e-10 * norms[None, :] / dist[:, None])
+
+
+def test_spin_table_switch_on_existing_operator():
+    """Turning the table on and off for the current operator gives the same product."""
+    s = kw.Solver("f64")
+    Hs = _set_spin(s, "j1j2_N12")
+    rng = np.random.default_rng(3)
+    r = torch.as_tensor(rng.standard_normal(Hs.shape[0]) + 1j * rng.standard_normal(Hs.shape[0]), device="cuda")
+    qa, qb, qc = torch.empty_like(r), torch.empty_like(r), torch.empty_like(r)
+    ta = s.spmv_dot(0.2 + 0.3j, r, qa)
+    s.set_spin_table(True)
+    tb = s.spmv_dot(0.2 + 0.3j, r, qb)
+    s.set_spin_table(False)
+    tc = s.spmv_dot(0.2 + 0.3j, r, qc)
+    assert (qa - qb).abs().max().item() <= 1e-14 * qa.abs().max().item()
+    assert torch.equal(qa, qc) and ta == tc and abs(ta - tb) <= 1e-13 * abs(ta)
 
 
 def test_generated_operator_argument_errors():
