@@ -69,6 +69,17 @@ def test_gradient_matches_oracle(prec):
     assert np.abs(g - grad_o).max() <= 1e-8 * np.abs(grad_o).max(), (g, grad_o)
 
 
+def test_gradcheck_tiny_chain():
+    """torch.autograd.gradcheck of the spectrum A(theta) (every output, every
+    parameter) on a J1-J2 chain N=8 (M=70, 10 parameters), 6 shifts: the
+    hand-written backward against torch's central differences of the forward
+    solves (converged to 1e-13, so the difference noise is ~1e-13/eps)."""
+    j, z, b, _ = _problem(8, 6)
+    model = adjoint.GreenSpectrum(j.terms, b, z, prec="f64", tol=1e-13)
+    theta = torch.tensor(j.theta, dtype=torch.float64, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda th: model(th), (theta,), eps=1e-6, atol=1e-6, rtol=1e-5)
+
+
 def test_fullsize_gradient_vs_central_differences():
     """J1-J2 N=20 with 22 parameters, K=256 shifts: adjoint gradient of the
     quadratic spectrum loss against central differences (step 1e-5) of the GPU's
