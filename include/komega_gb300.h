@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define KW_ABI_VERSION 1
+#define KW_ABI_VERSION 2
 /* Largest number of projection rows (b plus left vectors) in projected mode. */
 #define KW_MAX_PROJ 32
 
@@ -77,6 +77,13 @@ typedef struct {
     int seed_switch;     /* 1: switch the seed after every update (Sec. 2.2.4); 0: fixed seed z_0 */
     int64_t hist_stride; /* record the per-shift residual every hist_stride iterations (0 = never) */
     int64_t hist_max;    /* records kept at most */
+    int use_graph;       /* 0: the host enqueues the iterations in chunks and polls the stop flag;
+                            1: the iterations loop on the device in one CUDA graph (a WHILE node whose
+                            body runs a chunk of iterations and then tests the stop flag), with no host
+                            work per chunk; n >= 2: the same with n iterations per body (rounded up to
+                            even).  The graph is kept and relaunched while the solve's descriptor is
+                            unchanged.  Solves with a matrix-vector callback, or with kernel timing on
+                            (kw_set_kernel_timing), use the host loop whatever this says. */
 } kw_options;
 
 typedef struct {
@@ -93,7 +100,7 @@ typedef struct {
 int kw_abi_version(void);
 
 /* Fill *opt with defaults: KW_F64, tol 1e-10, maxiter 100000, seed_switch 1,
- * hist_stride 0, hist_max 0. */
+ * hist_stride 0, hist_max 0, use_graph 1. */
 void kw_default_options(kw_options* opt);
 
 /* Human-readable name of a status code (static string, never NULL). */

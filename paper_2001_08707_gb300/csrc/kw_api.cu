@@ -149,6 +149,17 @@ struct kw_ctx {
   bool owns_stream = false;
   DBuf child_states, done_count;
   int* done_host = nullptr;   // pinned
+  // device-side iteration loop (opt.use_graph): a graph whose WHILE node runs
+  // chunks of iterations until the stop flag is raised; kept while the
+  // descriptor it was captured from is unchanged
+  cudaStream_t cap_stream = nullptr;   // capture stream (the caller's may be the legacy stream)
+  DBuf loop;                           // device [trips, trip cap]
+  unsigned* loop_host = nullptr;       // pinned [2]
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  kw::Work loop_work;                  // descriptor of the captured iterations
+  int loop_parity = -1, loop_chunk = 0;
+  int64_t loop_launches = 0;           // kernel launches per trip
   // last solve
   bool resumable = false;     // the last kw_solve stopped at maxiter and its workspace is intact
   int64_t run_maxiter = 0;    // iteration cap of the running solve
@@ -198,6 +209,7 @@ void kw_default_options(kw_options* opt) {
   opt->seed_switch = 1;
   opt->hist_stride = 0;
   opt->hist_max = 0;
+  opt->use_graph = 1;
 }
 
 const char* kw_status_string(kw_status s) {
@@ -256,6 +268,11 @@ void kw_destroy(kw_ctx* ctx) {
   if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
   ctx->child_states.release();
   ctx->done_count.release();
+  ctx->loop.release();
+  if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+  if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->loop_host) cudaFreeHost(ctx->loop_host);
   if (ctx->done_host) cudaFreeHost(ctx->done_host);
   if (ctx->owns_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->st_host) cudaFreeHost(ctx->st_host);
@@ -1029,6 +1046,114 @@ static kw_status run_loop(kw_ctx* ctx, int64_t start = 0) {
   return KW_OK;
 }
 
+static const int kGraphChunk = 8;   // iterations per trip of the device-side loop (even)
+
+// Iterations per trip of the device-side loop: 0 when the host loop runs (the
+// option is off, kernel timing samples events per chunk, or a callback's work
+// may not be capturable).
+static int graph_chunk(const kw_ctx* ctx) {
+  if (ctx->opt.use_graph <= 0 || ctx->timing_every > 0 || ctx->work.op == kw::OP_CALLBACK || ctx->work.mv_fn)
+    return 0;
+  const int n = ctx->opt.use_graph == 1 ? kGraphChunk : std::min(ctx->opt.use_graph, 1 << 12);
+  return (n + 1) & ~1;
+}
+
+// Capture one trip of the device-side loop into the body of a WHILE node:
+// `chunk` iterations from parity `parity`, the join of the two streams, and
+// the loop condition (stop flag clear, trip cap not reached).
+static cudaError_t capture_loop(kw_ctx* ctx, int parity, int chunk, cudaGraph_t* out, int64_t* launches) {
+  kw::Work& w = ctx->work;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  cudaGraphConditionalHandle h;
+  e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  const cudaStream_t user = w.stream;
+  w.stream = ctx->cap_stream;
+  e = cudaStreamBeginCaptureToGraph(w.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    int64_t n = 0;
+    for (int i = 0; i < chunk && e == cudaSuccess; ++i) e = iteration_launch(w, (parity + i) & 1, i == 0, nullptr, &n);
+    if (e == cudaSuccess) e = kw::join_streams(w);
+    if (e == cudaSuccess) e = kw::launch_loop_cond(&w.st->done, 1, (unsigned*)ctx->loop.p, h, w.stream);
+    *launches = n + 1;
+    cudaGraph_t captured = nullptr;   // the body graph itself, owned by the node
+    const cudaError_t ee = cudaStreamEndCapture(w.stream, &captured);
+    if (e == cudaSuccess) e = ee;
+  }
+  w.stream = user;
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  *out = g;
+  return cudaSuccess;
+}
+
+// Phase 2 on the device: one launch of the loop graph (captured again only
+// when the descriptor, the starting parity or the chunk changed); returns
+// after the stream has drained.
+static kw_status run_graph_loop(kw_ctx* ctx, int64_t start, int chunk) {
+  kw::Work& w = ctx->work;
+  const int parity = (int)(start & 1);
+  if (!ctx->cap_stream) KW_CUDA(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking), "loop stream");
+  if (!ctx->loop_host) KW_CUDA(cudaMallocHost((void**)&ctx->loop_host, 2 * sizeof(unsigned)), "loop alloc");
+  if (!ctx->loop.p) {
+    KW_CUDA(ctx->loop.ensure(2 * sizeof(unsigned)), "loop alloc");
+    if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);   // captured with another counter
+    ctx->loop_exec = nullptr;
+  }
+  const bool same = ctx->loop_exec && ctx->loop_parity == parity && ctx->loop_chunk == chunk &&
+                    memcmp(&ctx->loop_work, &w, sizeof(kw::Work)) == 0;
+  if (!same) {
+    if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);
+    if (ctx->loop_graph) cudaGraphDestroy(ctx->loop_graph);
+    ctx->loop_exec = nullptr;
+    ctx->loop_graph = nullptr;
+    int64_t per_trip = 0;
+    KW_CUDA(capture_loop(ctx, parity, chunk, &ctx->loop_graph, &per_trip), "loop graph capture");
+    cudaError_t e = cudaGraphInstantiate(&ctx->loop_exec, ctx->loop_graph, 0);
+    if (e != cudaSuccess) {
+      ctx->loop_exec = nullptr;
+      return cuda_fail(ctx, e, "loop graph instantiate");
+    }
+    memcpy(&ctx->loop_work, &w, sizeof(kw::Work));
+    ctx->loop_parity = parity;
+    ctx->loop_chunk = chunk;
+    ctx->loop_launches = per_trip;
+  }
+  // trip cap: the device stops at run_maxiter; two trips of slack
+  const int64_t left = std::max<int64_t>(ctx->run_maxiter - start, 0);
+  ctx->loop_host[0] = 0;
+  ctx->loop_host[1] = (unsigned)std::min<int64_t>(left / chunk + 3, 0x7fffffff);
+  KW_CUDA(cudaMemcpyAsync(ctx->loop.p, ctx->loop_host, 2 * sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream),
+          "loop counter");
+  KW_CUDA(cudaGraphLaunch(ctx->loop_exec, ctx->stream), "loop graph launch");
+  KW_CUDA(cudaMemcpyAsync(ctx->loop_host, ctx->loop.p, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream),
+          "loop counter");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "solve sync");
+  ctx->stats.launches += (int64_t)ctx->loop_host[0] * ctx->loop_launches;
+  return KW_OK;
+}
+
+// Phase 2: the device-side loop when it applies, else the host loop.
+static kw_status run_iterations(kw_ctx* ctx, int64_t start = 0) {
+  const int chunk = graph_chunk(ctx);
+  return chunk ? run_graph_loop(ctx, start, chunk) : run_loop(ctx, start);
+}
+
 // Phase 3 (the context's stream has drained): outputs and summary.
 static kw_status solve_end(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* info) {
   kw::Work& w = ctx->work;
@@ -1093,7 +1218,7 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
   if (!ctx) return KW_ERR_ARG;
   kw_status s = solve_begin(ctx, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
   if (s != KW_OK) return s;
-  s = run_loop(ctx);
+  s = run_iterations(ctx);
   if (s != KW_OK) return s;
   return solve_end(ctx, proj_out_host, info);
 }
@@ -1226,7 +1351,7 @@ kw_status kw_resume(kw_ctx* ctx, int64_t more_iters, kw_c128* proj_out_host, kw_
     }
     return cuda_fail(ctx, e, "kw_resume: first product");
   }
-  kw_status s = run_loop(ctx, it);
+  kw_status s = run_iterations(ctx, it);
   if (s != KW_OK) return s;
   return solve_end(ctx, proj_out_host, info);
 }
@@ -1297,46 +1422,95 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   KW_CUDA(cudaMemcpyAsync(ctx->child_states.p, sts.data(), (size_t)n * sizeof(void*), cudaMemcpyHostToDevice,
                           bs), "batch upload");
   KW_CUDA(cudaStreamSynchronize(bs), "batch sync");
-  // one graph: a chunk of iterations of every instance (fork/join over the
-  // instance streams), then the count of finished instances
+  // One graph: a chunk of iterations of every instance (fork/join over the
+  // instance streams), then the count of finished instances.  With the
+  // device-side loop the chunk is the body of a WHILE node that repeats until
+  // every instance has stopped; otherwise the host relaunches it per chunk.
+  const int gchunk = graph_chunk(ctx);
+  const int chunk = gchunk ? gchunk : kChunk;
+  int64_t maxit = ctx->opt.maxiter;
+  for (int64_t i = 0; i < n; ++i) maxit = std::max<int64_t>(maxit, ctx->children[i]->opt.maxiter);
+  if (gchunk) {
+    if (!ctx->loop_host) KW_CUDA(cudaMallocHost((void**)&ctx->loop_host, 2 * sizeof(unsigned)), "loop alloc");
+    if (!ctx->loop.p) {
+      KW_CUDA(ctx->loop.ensure(2 * sizeof(unsigned)), "loop alloc");
+      if (ctx->loop_exec) cudaGraphExecDestroy(ctx->loop_exec);   // captured with another counter
+      ctx->loop_exec = nullptr;
+    }
+  }
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  KW_CUDA(cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed), "batch capture");
-  cudaError_t ce = cudaEventRecord(ev[n], bs);
+  cudaGraph_t body = nullptr;
+  cudaGraphConditionalHandle h = 0;
+  cudaError_t ce = cudaSuccess;
+  if (gchunk) {
+    ce = cudaGraphCreate(&graph, 0);
+    if (ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (ce == cudaSuccess) body = np.conditional.phGraph_out[0];
+    if (ce == cudaSuccess) ce = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  } else {
+    ce = cudaStreamBeginCapture(bs, cudaStreamCaptureModeRelaxed);
+  }
+  if (ce != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(ctx, ce, "kw_solve_batched: graph capture");
+  }
+  ce = cudaEventRecord(ev[n], bs);
+  int64_t per_trip = 0;
   for (int64_t i = 0; i < n && ce == cudaSuccess; ++i) {
     kw_ctx* c = ctx->children[i];
     ce = cudaStreamWaitEvent(c->stream, ev[n], 0);
-    int64_t dummy = 0;
-    for (int it = 0; it < kChunk && ce == cudaSuccess; ++it)
-      ce = iteration_launch(c->work, it & 1, it == 0, nullptr, &dummy);
+    for (int it = 0; it < chunk && ce == cudaSuccess; ++it)
+      ce = iteration_launch(c->work, it & 1, it == 0, nullptr, &per_trip);
     if (ce == cudaSuccess) ce = kw::join_streams(c->work);
     if (ce == cudaSuccess) ce = cudaEventRecord(ev[i], c->stream);
     if (ce == cudaSuccess) ce = cudaStreamWaitEvent(bs, ev[i], 0);
-    c->stats.launches += 0;
   }
   if (ce == cudaSuccess) ce = kw::launch_count_done((int)n, (kw::State* const*)ctx->child_states.p,
                                                    (int*)ctx->done_count.p, bs);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(ctx->done_host, ctx->done_count.p, sizeof(int), cudaMemcpyDeviceToHost, bs);
-  cudaError_t ee = cudaStreamEndCapture(bs, &graph);
-  if (ce == cudaSuccess) ce = ee;
+  if (gchunk) {
+    if (ce == cudaSuccess) ce = kw::launch_loop_cond((const int*)ctx->done_count.p, (int)n, (unsigned*)ctx->loop.p, h, bs);
+    cudaGraph_t captured = nullptr;   // the body graph itself, owned by the node
+    const cudaError_t ee = cudaStreamEndCapture(bs, &captured);
+    if (ce == cudaSuccess) ce = ee;
+  } else {
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(ctx->done_host, ctx->done_count.p, sizeof(int), cudaMemcpyDeviceToHost, bs);
+    const cudaError_t ee = cudaStreamEndCapture(bs, &graph);
+    if (ce == cudaSuccess) ce = ee;
+  }
   if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
   if (ce != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
-    cleanup();
     return cuda_fail(ctx, ce, "kw_solve_batched: graph capture");
   }
-  int64_t maxit = ctx->opt.maxiter;
-  for (int64_t i = 0; i < n; ++i) maxit = std::max<int64_t>(maxit, ctx->children[i]->opt.maxiter);
-  int64_t launches = 0;
-  for (;;) {
-    ce = cudaGraphLaunch(exec, bs);
-    if (ce != cudaSuccess) break;
-    ++launches;
-    ce = cudaStreamSynchronize(bs);   // one chunk of the whole batch per graph launch
-    if (ce != cudaSuccess) break;
-    if (*(volatile int*)ctx->done_host >= n) break;
-    if (launches * kChunk > maxit + 2 * kChunk) break;   // every instance stops at its maxiter
+  int64_t trips = 0;
+  if (gchunk) {   // one launch; the trip cap stops the loop even if an instance never raises its flag
+    ctx->loop_host[0] = 0;
+    ctx->loop_host[1] = (unsigned)std::min<int64_t>(maxit / chunk + 3, 0x7fffffff);
+    ce = cudaMemcpyAsync(ctx->loop.p, ctx->loop_host, 2 * sizeof(unsigned), cudaMemcpyHostToDevice, bs);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, bs);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(ctx->loop_host, ctx->loop.p, sizeof(unsigned), cudaMemcpyDeviceToHost, bs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(bs);
+    if (ce == cudaSuccess) trips = ctx->loop_host[0];
+  } else {
+    for (;;) {
+      ce = cudaGraphLaunch(exec, bs);
+      if (ce != cudaSuccess) break;
+      ++trips;
+      ce = cudaStreamSynchronize(bs);   // one chunk of the whole batch per graph launch
+      if (ce != cudaSuccess) break;
+      if (*(volatile int*)ctx->done_host >= n) break;
+      if (trips * chunk > maxit + 2 * chunk) break;   // every instance stops at its maxiter
+    }
   }
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
@@ -1344,14 +1518,14 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   if (ce != cudaSuccess) return cuda_fail(ctx, ce, "kw_solve_batched: graph launch");
   for (int64_t i = 0; i < n; ++i) {
     kw_ctx* c = ctx->children[i];
-    c->stats.launches += launches * kChunk * (c->work.full ? 4 : 3);   // per iteration: K2, K1, K3 (+K4)
+    c->stats.launches += trips * chunk * (c->work.full ? 4 : 3);   // per iteration: K2, K1, K3 (+K4)
     kw_status s = solve_end(c, inst[i].proj_out_host, info ? &info[i] : nullptr);
     if (s != KW_OK && result == KW_OK) {
       result = s;
       fail(ctx, s, "kw_solve_batched: instance %lld: %s", (long long)i, c->err);
     }
   }
-  ctx->stats.launches = launches;
+  ctx->stats.launches = trips * (per_trip + (gchunk ? 2 : 1));   // every instance's kernels, the count (+ condition)
   {   // the caller's stream is ordered after the batch
     cudaEvent_t e1;
     KW_CUDA(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming), "kw_solve_batched: event");

@@ -217,6 +217,10 @@ cudaError_t launch_spin_table(int m, int nbond, const int* bond, const int* bino
 
 // Batched solves: count of instances whose solve has stopped (written to *out).
 cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_t s);
+// Loop condition of a CUDA graph WHILE node: continue while *count < target and
+// loop[0] (trips so far, incremented here) < loop[1].
+cudaError_t launch_loop_cond(const int* count, int target, unsigned* loop, cudaGraphConditionalHandle h,
+                             cudaStream_t s);
 
 // Adjoint bilinear forms (kw_bilinear): shifts per tile and the launcher.
 constexpr int kBilinearTile = 8;

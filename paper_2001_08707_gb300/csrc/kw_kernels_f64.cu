@@ -68,6 +68,21 @@ cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_
   return cudaGetLastError();
 }
 
+// Last node of a device-side loop body: one more trip while *count < target
+// and fewer than loop[1] trips have run (loop[0] counts them, so the loop ends
+// even if the stop flag is never raised).
+static __global__ void k_loop_cond(const int* count, int target, unsigned* loop, cudaGraphConditionalHandle h) {
+  const unsigned trips = loop[0] + 1;
+  loop[0] = trips;
+  cudaGraphSetConditional(h, (*count < target && trips < loop[1]) ? 1u : 0u);
+}
+
+cudaError_t launch_loop_cond(const int* count, int target, unsigned* loop, cudaGraphConditionalHandle h,
+                             cudaStream_t s) {
+  k_loop_cond<<<1, 1, 0, s>>>(count, target, loop, h);
+  return cudaGetLastError();
+}
+
 // Bilinear forms y_k^T H x_k of one term for every shift; partials need
 // kBilinearTile * nblk * ceil(K / kBilinearTile) double2.
 cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,

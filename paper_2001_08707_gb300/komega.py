@@ -29,7 +29,9 @@ MAX_PROJ = 32
 
 class kw_options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int64), ("seed_switch", C.c_int),
-                ("hist_stride", C.c_int64), ("hist_max", C.c_int64)]
+                ("hist_stride", C.c_int64), ("hist_max", C.c_int64), ("use_graph", C.c_int)]
+
+ABI_VERSION = 2   # KW_ABI_VERSION of the header these structures mirror
 
 
 class kw_c128(C.Structure):
@@ -86,6 +88,10 @@ def load_library(path: str = LIB_PATH):
         raise RuntimeError(f"{path} is missing: build it with `python -m paper_2001_08707_gb300.build` "
                            "(or __graft_entry__.build()); there is no CPU fallback")
     lib = C.CDLL(path)
+    lib.kw_abi_version.restype = C.c_int
+    if lib.kw_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{path} has ABI version {lib.kw_abi_version()}, the binding expects {ABI_VERSION}: "
+                           "rebuild it")
     P, I64, D = C.c_void_p, C.c_int64, C.c_double
     sig = {
         "kw_abi_version": (C.c_int, []),
@@ -203,10 +209,16 @@ def _z_array(z):
 
 
 class Solver:
-    """A solver context (kw_ctx) on the current CUDA device and stream."""
+    """A solver context (kw_ctx) on the current CUDA device and stream.
+
+    use_graph: 1 (default) runs the iterations as a device-side loop in one CUDA
+    graph; 0 has the host enqueue them in chunks; n >= 2 sets the iterations per
+    trip of the device-side loop (kw_options.use_graph).
+    """
 
     def __init__(self, prec: str = "f64", tol: float = 1e-10, maxiter: int = 100000, seed_switch: bool = True,
-                 hist_stride: int = 0, hist_max: int = 0, stream=None, method: str = "cocg"):
+                 hist_stride: int = 0, hist_max: int = 0, stream=None, method: str = "cocg",
+                 use_graph: int = 1):
         import torch
 
         self._torch = torch
@@ -215,7 +227,7 @@ class Solver:
         lib = load_library()
         self._lib = lib
         self.prec = PRECISIONS[prec]
-        opt = kw_options(self.prec, tol, maxiter, 1 if seed_switch else 0, hist_stride, hist_max)
+        opt = kw_options(self.prec, tol, maxiter, 1 if seed_switch else 0, hist_stride, hist_max, int(use_graph))
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         ctx = C.c_void_p()

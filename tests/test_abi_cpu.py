@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 import shutil
+import subprocess
 
 import pytest
 
@@ -41,7 +42,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_strings(lib):
-    assert lib.kw_abi_version() == 1
+    assert lib.kw_abi_version() == kw.ABI_VERSION == 2
     assert lib.kw_status_string(0) == b"KW_OK"
     assert lib.kw_status_string(4) == b"KW_ERR_BREAKDOWN"
     assert lib.kw_status_string(8) == b"KW_NOT_CONVERGED"
@@ -52,6 +53,7 @@ def test_default_options(lib):
     o = kw.kw_options()
     lib.kw_default_options(C.byref(o))
     assert o.prec == kw.KW_F64 and o.tol == 1e-10 and o.maxiter == 100000 and o.seed_switch == 1
+    assert o.use_graph == 1
 
 
 def test_create_rejects_bad_options_without_touching_the_gpu(lib):
@@ -74,8 +76,32 @@ def test_null_context_is_rejected(lib):
     lib.kw_destroy(None)
 
 
-def test_struct_layout_matches_header():
-    # kw_options: enum(4) pad(4) double int64 int pad int64 int64
-    assert C.sizeof(kw.kw_options) == 48
-    assert C.sizeof(kw.kw_c128) == 16
-    assert C.sizeof(kw.kw_solve_info) == 56
+_MIRRORS = {"kw_options": kw.kw_options, "kw_c128": kw.kw_c128, "kw_solve_info": kw.kw_solve_info,
+            "kw_instance": kw.kw_instance, "kw_rci_io": kw.kw_rci_io, "kw_stats": kw.kw_stats,
+            "kw_csr_term": kw.kw_csr_term}
+
+
+def test_struct_layout_matches_header(tmp_path):
+    """The ctypes mirrors have the size and field offsets that a C compiler gives
+    the header's structures (fields matched by name)."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "komega_gb300.h"', "int main(void) {"]
+    for name, mirror in _MIRRORS.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in mirror._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name, mirror in _MIRRORS.items():
+        assert got[(name, "size")] == C.sizeof(mirror), name
+        for field, _ in mirror._fields_:
+            assert got[(name, field)] == getattr(mirror, field).offset, (name, field)
