@@ -47,7 +47,7 @@ typedef enum {
     KW_ERR_BREAKDOWN = 4,    /* rho_n = 0, zero alpha denominator (Eq. 17) or pi_{n+1} = 0 (Eq. 20) */
     KW_ERR_NONFINITE = 5,    /* a seed scalar became Inf/NaN */
     KW_ERR_CALLBACK = 6,     /* reserved: user matvec callback failure */
-    KW_ERR_TIMEOUT = 7,      /* reserved: bounded device wait expired */
+    KW_ERR_TIMEOUT = 7,      /* a bounded device wait expired (a staged copy did not complete) */
     KW_NOT_CONVERGED = 8     /* maxiter reached; outputs hold the last iterates */
 } kw_status;
 
@@ -429,6 +429,22 @@ kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user);
  * linearity); on = 0: one stream, in the order K2(n), K1(n+1), K3(n), K4(n).
  * Both give the same numbers.  Errors: KW_ERR_ARG. */
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
+
+/* Loads of the three-term update (Eq. 16) in the FP32 and FP32-pair forms.
+ * on = 0 (the default): plain coalesced loads.  on = 1: the tiles of r_n, q_n,
+ * r_{n-1} and the projection rows are staged in shared memory by TMA bulk
+ * copies (cp.async.bulk) completed on mbarriers, up to three tiles ahead of the
+ * arithmetic.  Each thread sums the same elements in the same order either way;
+ * the results agree to rounding (the two kernels are compiled separately).  On
+ * the N=24 Heisenberg benchmark the staged kernel is slower (74 vs 67 us per
+ * update in the pair form, equal in the FP32 form), so it is off by default.  A
+ * staged copy that does not complete within about a second ends the solve with
+ * KW_ERR_TIMEOUT.  The FP64 form and BiCG always use plain loads.  on = 2
+ * exercises that bound: each stage is armed for 16 bytes more than its copies
+ * bring, so the first staged wait of every block runs out and the solve ends
+ * with KW_ERR_TIMEOUT after a few seconds (the context stays usable).
+ * Errors: KW_ERR_ARG. */
+kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
 
 /* Configuration of the sparse product kernel.  lanes = threads per matrix
  * row of the CSR kernel (1, 2, 4, 8 or 16), or 32 = the SELL-32 layout (an

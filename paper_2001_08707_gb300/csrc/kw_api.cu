@@ -139,6 +139,7 @@ struct kw_ctx {
   cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr;
   DBuf part_k1;   // K1's block partials (K1 overlaps K3, which uses part)
   int overlap = 1;
+  int bulk = 0;   // kw_set_bulk_copy
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -820,6 +821,8 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.nout = (int)nleft + 1;
   w.nproj = w.full ? 0 : (int)nleft + 1;
   w.tol = ctx->opt.tol;
+  w.proj_ld = (m + kw::KW_PROJ_ALIGN - 1) / kw::KW_PROJ_ALIGN * kw::KW_PROJ_ALIGN;
+  w.bulk = ctx->bulk;
   w.b = b_dev;
   w.left = left_dev;
   w.stream = ctx->stream;
@@ -835,7 +838,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->rA, Ms * vs},
       {&ctx->rB, Ms * vs},
       {&ctx->q, Ms * vs},
-      {&ctx->proj_rows, (size_t)std::max(w.nproj, 1) * Ms * rs},
+      {&ctx->proj_rows, (size_t)std::max(w.nproj, 1) * (size_t)w.proj_ld * rs},
       {&ctx->z, Ks * 16},
       {&ctx->pi1, Ks * 16},
       {&ctx->pi0, Ks * 16},
@@ -1399,6 +1402,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     c->method = ctx->method;   // BiCG instances start their shadow from b
     c->btilde = nullptr;
     c->overlap = ctx->overlap;
+    c->bulk = ctx->bulk;
     if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
     c->run_maxiter = c->opt.maxiter;
     KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
@@ -1754,6 +1758,12 @@ kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user) {
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return KW_ERR_ARG;
   ctx->overlap = on;
+  return KW_OK;
+}
+
+kw_status kw_set_bulk_copy(kw_ctx* ctx, int on) {
+  if (!ctx || on < 0 || on > 2) return KW_ERR_ARG;
+  ctx->bulk = on;
   return KW_OK;
 }
 

@@ -99,7 +99,9 @@ struct Work {
   void* q;
   const double* b;   // caller's b (FP64)
   const double* left;  // caller's left vectors (FP64) [nproj-1][m]
-  void* proj_rows;   // [nproj][m] real, vector precision (b then left vectors)
+  void* proj_rows;   // [nproj][proj_ld] real, vector precision (b then left vectors)
+  int64_t proj_ld;   // row stride of proj_rows: m rounded up to KW_PROJ_ALIGN elements (16-byte aligned rows)
+  int bulk = 0;      // 1: K2 stages its tiles in shared memory with TMA bulk copies where the form allows
   // shift state
   double2* z;
   double2* pi1;      // pi_n
@@ -230,6 +232,7 @@ cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col,
 
 // Recalculation at new shifts (kw_recalc): threads per block, log rows per
 // shared-memory chunk, and the launcher (flag: set to 1 on breakdown).
+constexpr int KW_PROJ_ALIGN = 64;   // elements; projection rows start 16-byte aligned in every form
 constexpr int kRecalcThreads = 32;
 constexpr int kRecalcChunk = 16;
 cudaError_t launch_recalc(int K, int np, long long n_iter, const double2* log, const double2* w0, const double2* z,

@@ -32,6 +32,7 @@
 #include <type_traits>
 
 #include "kw_arith.cuh"
+#include "kw_bulk.cuh"
 #include "kw_internal.cuh"
 
 namespace kw {
@@ -799,13 +800,29 @@ __global__ void k_sell_fill(int m, int nslice, const int* __restrict__ perm, con
 // METHOD (Table 1): COCG rho = r^T r; CG rho = r^dagger r = nu; BiCG also
 // advances the shadow residual (Appendix B: conjugated coefficients, A^dagger)
 // and rho = r~^dagger r.
-template <int P, int NP, int METHOD>
+//
+// BULK (kw_set_bulk_copy): the tiles of r_n, q, r_{n-1} and the projection
+// rows are staged in shared memory by TMA bulk copies, nstage tiles ahead, so
+// the loads of later tiles are in flight while the pair arithmetic of this one
+// runs.  The tile is the block (one element per thread) and tile t of a block
+// is the element set of its t-th grid-stride trip, so each thread sums the
+// same elements in the same order as without staging.  The ragged last tile
+// is read with plain loads.
+constexpr int kSeedTile = 256;
+
+// Bytes of one stage: a tile of r_n, q, r_{n-1} and of the np projection rows.
+template <class V, class R>
+__host__ __device__ constexpr uint32_t seed_stage_bytes(int np) {
+  return (uint32_t)((3 * kSeedTile * sizeof(V) + np * kSeedTile * sizeof(R) + 127) / 128 * 128);
+}
+
+template <int P, int NP, int METHOD, bool BULK>
 __global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5 && METHOD != KW_METHOD_BICG) ? 3 : 1)
 k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
-              typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int np,
-              int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out,
+              typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int64_t ld,
+              int np, int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out,
               const typename PT<P>::V* __restrict__ rtn_buf, const typename PT<P>::V* __restrict__ qt,
-              typename PT<P>::V* __restrict__ rtm_buf) {
+              typename PT<P>::V* __restrict__ rtm_buf, int nstage, uint32_t tx_pad) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   typedef typename PT<P>::A A;
@@ -897,62 +914,136 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
   for (int i = 0; i < N; ++i) chunk[i] = tot[i] = azero<A>();
   int in_chunk = 0;
   const int stride = gridDim.x * blockDim.x;
-  // ILP elements per trip, all loads issued before any store: two for the FP64
-  // and FP32 forms; one for FP32 pairs, whose arithmetic already fills the
-  // pipes and whose registers would otherwise limit occupancy.
-  constexpr int ILP = (P == PREC_DF) ? 1 : 2;
-  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += ILP * stride) {
-    V rn[ILP], rm[ILP], qv[ILP];
-    R a[ILP][NP > 0 ? NP : 1];
-    bool has[ILP];
-#pragma unroll
-    for (int u = 0; u < ILP; ++u) {
-      const int i = i0 + u * stride;
-      has[u] = i < m;
-      rn[u] = has[u] ? rn_buf[i] : vzero<V>();
-      rm[u] = has[u] ? rm_buf[i] : vzero<V>();
-      qv[u] = has[u] ? q[i] : vzero<V>();
-#pragma unroll
-      for (int l = 0; l < NP; ++l) a[u][l] = (l < np && has[u]) ? proj[(size_t)l * m + i] : rfrom_double<R>(0.0);
+  // Eq. 16 for element i and its contributions to the dots (nothing stored when !has).
+  auto element = [&](const V& rnv, const V& qvv, const V& rmv, const R* av, int i, bool has) {
+    float4 pa, pb, pc;
+    if constexpr (P == PREC_DF) {
+      pa = make_float4(vpp[0].x, vpp[0].y, vpp[0].z, vpp[0].w);
+      pb = make_float4(vpp[1].x, vpp[1].y, vpp[1].z, vpp[1].w);
+      pc = make_float4(vpp[2].x, vpp[2].y, vpp[2].z, vpp[2].w);
+    } else {
+      pa = s_pp[0];
+      pb = s_pp[1];
+      pc = s_pp[2];
+    }
+    const V ca = vscalar<V>(s_cf[0], pa), cb = vscalar<V>(s_cf[1], pb), cc = vscalar<V>(s_cf[2], pc);
+    const V r1 = csub(csub(cmul(ca, rnv), cmul(cb, qvv)), cmul(cc, rmv));   // Eq. 16; zero when !has
+    if (has) rm_buf[i] = r1;
+    if constexpr (METHOD == KW_METHOD_BICG) {
+      // shadow: the conjugated coefficients (their folded scales are the conjugate ones)
+      const V rtn = has ? rtn_buf[i] : vzero<V>(), rtm = has ? rtm_buf[i] : vzero<V>();
+      const V qtv = has ? qt[i] : vzero<V>();
+      const V rt1 = csub(csub(cmul(vconj(ca), rtn), cmul(vconj(cb), qtv)), cmul(vconj(cc), rtm));
+      if (has) rtm_buf[i] = rt1;
+      acc_cdot(chunk[0], chunk[1], rt1, r1);
+      acc_nrm(chunk[2], r1);
+    } else {
+      acc_rho_nrm(chunk[0], chunk[1], chunk[2], r1);
     }
 #pragma unroll
-    for (int u = 0; u < ILP; ++u) {
-      const int i = i0 + u * stride;
-      float4 pa, pb, pc;
-      if constexpr (P == PREC_DF) {
-        pa = make_float4(vpp[0].x, vpp[0].y, vpp[0].z, vpp[0].w);
-        pb = make_float4(vpp[1].x, vpp[1].y, vpp[1].z, vpp[1].w);
-        pc = make_float4(vpp[2].x, vpp[2].y, vpp[2].z, vpp[2].w);
-      } else {
-        pa = s_pp[0];
-        pb = s_pp[1];
-        pc = s_pp[2];
-      }
-      const V ca = vscalar<V>(s_cf[0], pa), cb = vscalar<V>(s_cf[1], pb), cc = vscalar<V>(s_cf[2], pc);
-      const V r1 = csub(csub(cmul(ca, rn[u]), cmul(cb, qv[u])), cmul(cc, rm[u]));   // Eq. 16; zero when !has
-      if (has[u]) rm_buf[i] = r1;
-      if constexpr (METHOD == KW_METHOD_BICG) {
-        // shadow: the conjugated coefficients (their folded scales are the conjugate ones)
-        const V rtn = has[u] ? rtn_buf[i] : vzero<V>(), rtm = has[u] ? rtm_buf[i] : vzero<V>();
-        const V qtv = has[u] ? qt[i] : vzero<V>();
-        const V rt1 = csub(csub(cmul(vconj(ca), rtn), cmul(vconj(cb), qtv)), cmul(vconj(cc), rtm));
-        if (has[u]) rtm_buf[i] = rt1;
-        acc_cdot(chunk[0], chunk[1], rt1, r1);
-        acc_nrm(chunk[2], r1);
-      } else {
-        acc_rho_nrm(chunk[0], chunk[1], chunk[2], r1);
-      }
-#pragma unroll
-      for (int l = 0; l < NP; ++l)
-        if (l < np) acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], a[u][l], r1);
-    }
-    if (CHUNKED && (in_chunk += ILP) >= PT<P>::CHUNK) {
+    for (int l = 0; l < NP; ++l)
+      if (l < np) acc_proj(chunk[3 + 2 * l], chunk[4 + 2 * l], av[l], r1);
+  };
+  auto close_chunk = [&](int count) {
+    if (CHUNKED && (in_chunk += count) >= PT<P>::CHUNK) {
 #pragma unroll
       for (int k = 0; k < N; ++k) {
         aadd(tot[k], chunk[k]);
         chunk[k] = azero<A>();
       }
       in_chunk = 0;
+    }
+  };
+  if constexpr (BULK) {
+    extern __shared__ __align__(128) unsigned char kw_stage[];
+    __shared__ __align__(8) uint64_t bars[3];
+    constexpr uint32_t SV = kSeedTile * sizeof(V), SR = kSeedTile * sizeof(R);
+    // tx_pad > 0 (a test of the bounded wait) arms each stage for bytes that never arrive
+    const uint32_t stage_bytes = seed_stage_bytes<V, R>(np), tx = 3 * SV + (uint32_t)np * SR + tx_pad;
+    const int nfull = m / kSeedTile, ntiles = (m + kSeedTile - 1) / kSeedTile, G = gridDim.x;
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < nstage; ++s) mbar_init(&bars[s], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int t, int s) {   // thread 0: tile t into stage s
+      unsigned char* base = kw_stage + (size_t)s * stage_bytes;
+      const size_t e0 = (size_t)t * kSeedTile;
+      mbar_arrive_expect(&bars[s], tx);
+      bulk_load(base, rn_buf + e0, SV, &bars[s]);
+      bulk_load(base + SV, q + e0, SV, &bars[s]);
+      bulk_load(base + 2 * SV, rm_buf + e0, SV, &bars[s]);
+      for (int l = 0; l < np; ++l) bulk_load(base + 3 * SV + l * SR, proj + (size_t)l * ld + e0, SR, &bars[s]);
+    };
+    if (threadIdx.x == 0)
+      for (int s = 0; s < nstage; ++s)
+        if (blockIdx.x + s * G < nfull) issue(blockIdx.x + s * G, s);
+    int k = 0;
+    bool failed = false;
+    for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
+      const int i = t * kSeedTile + (int)threadIdx.x;
+      V rnv, qvv, rmv;
+      R av[NP > 0 ? NP : 1];
+      bool late = false, has = true;
+      if (t < nfull) {
+        const int s = k % nstage;
+        late = !mbar_wait(&bars[s], (uint32_t)(k / nstage) & 1u);
+        const unsigned char* base = kw_stage + (size_t)s * stage_bytes;
+        rnv = reinterpret_cast<const V*>(base)[threadIdx.x];
+        qvv = reinterpret_cast<const V*>(base + SV)[threadIdx.x];
+        rmv = reinterpret_cast<const V*>(base + 2 * SV)[threadIdx.x];
+#pragma unroll
+        for (int l = 0; l < NP; ++l)
+          av[l] = l < np ? reinterpret_cast<const R*>(base + 3 * SV + l * SR)[threadIdx.x] : rfrom_double<R>(0.0);
+      } else {   // the ragged last tile
+        has = i < m;
+        rnv = has ? rn_buf[i] : vzero<V>();
+        qvv = has ? q[i] : vzero<V>();
+        rmv = has ? rm_buf[i] : vzero<V>();
+#pragma unroll
+        for (int l = 0; l < NP; ++l) av[l] = (l < np && has) ? proj[(size_t)l * ld + i] : rfrom_double<R>(0.0);
+      }
+      element(rnv, qvv, rmv, av, i, has);
+      close_chunk(1);
+      if (__syncthreads_or(late)) {   // every thread is done with stage k % nstage
+        failed = true;
+        break;
+      }
+      if (threadIdx.x == 0 && t + nstage * G < nfull) {
+        fence_async_smem();
+        issue(t + nstage * G, k % nstage);
+      }
+    }
+    if (failed) {   // a copy did not land in time: report it, and let in-flight copies finish before leaving
+      if (threadIdx.x == 0) {
+        set_fail(st, KW_ERR_TIMEOUT);
+        for (int j = 0; j < nstage; ++j)
+          if (blockIdx.x + (k + j) * G < nfull) mbar_wait(&bars[(k + j) % nstage], (uint32_t)((k + j) / nstage) & 1u);
+      }
+      __syncthreads();
+    }
+  } else {
+    // ILP elements per trip, all loads issued before any store: two for the FP64
+    // and FP32 forms; one for FP32 pairs, whose arithmetic already fills the
+    // pipes and whose registers would otherwise limit occupancy.
+    constexpr int ILP = (P == PREC_DF) ? 1 : 2;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < m; i0 += ILP * stride) {
+      V rn[ILP], rm[ILP], qv[ILP];
+      R a[ILP][NP > 0 ? NP : 1];
+      bool has[ILP];
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) {
+        const int i = i0 + u * stride;
+        has[u] = i < m;
+        rn[u] = has[u] ? rn_buf[i] : vzero<V>();
+        rm[u] = has[u] ? rm_buf[i] : vzero<V>();
+        qv[u] = has[u] ? q[i] : vzero<V>();
+#pragma unroll
+        for (int l = 0; l < NP; ++l) a[u][l] = (l < np && has[u]) ? proj[(size_t)l * ld + i] : rfrom_double<R>(0.0);
+      }
+#pragma unroll
+      for (int u = 0; u < ILP; ++u) element(rn[u], qv[u], rm[u], a[u], i0 + u * stride, has[u]);
+      close_chunk(ILP);
     }
   }
 #pragma unroll
@@ -1427,7 +1518,8 @@ __global__ void k_bilinear_reduce(int K, int nblk, int term, int nterm, const do
 // ================================================================ initialisation
 template <int P>
 __global__ void k_init_vectors(int m, int np, const double* __restrict__ b, const double* __restrict__ left,
-                               typename PT<P>::V* rn, typename PT<P>::V* rm, typename PT<P>::R* proj) {
+                               typename PT<P>::V* rn, typename PT<P>::V* rm, typename PT<P>::R* proj,
+                               int64_t ld) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
@@ -1436,7 +1528,7 @@ __global__ void k_init_vectors(int m, int np, const double* __restrict__ b, cons
     rm[i] = vzero<V>();
     if (np > 0) {
       proj[i] = rfrom_double<R>(bi);
-      for (int l = 1; l < np; ++l) proj[(size_t)l * m + i] = rfrom_double<R>(left[(size_t)(l - 1) * m + i]);
+      for (int l = 1; l < np; ++l) proj[(size_t)l * ld + i] = rfrom_double<R>(left[(size_t)(l - 1) * m + i]);
     }
   }
 }
@@ -1844,15 +1936,44 @@ template <int P, int NP, int METHOD>
 static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::R R;
-  static int nblk_per_sm = 0;
-  const int nblk = resident_blocks(nblk_per_sm, k_seed_update<P, NP, METHOD>, 256, w.num_sms);
-  const int grid = std::max(1, std::min(nblk, (int)((w.m + 255) / 256)));
   // shadow buffers rotate like the residual buffers (parity 0: r~_n in rtA)
   const void* rtn = parity ? w.rtB : w.rtA;
   void* rtm = parity ? w.rtA : w.rtB;
-  k_seed_update<P, NP, METHOD><<<grid, 256, 0, w.stream>>>((int)w.m, (const V*)rn, (const V*)w.q, (V*)rm,
-                                                           (const R*)w.proj_rows, w.nproj, parity, w.st, w.part,
-                                                           w.w, (const V*)rtn, (const V*)w.qt, (V*)rtm);
+  const int ntiles = (int)((w.m + kSeedTile - 1) / kSeedTile);
+  // Staged form: the FP32 and FP32-pair forms, whose update is bound by memory
+  // latency, not by the FP64 pipe; the BiCG shadow keeps plain loads.
+  if constexpr (P != PREC_F64 && METHOD != KW_METHOD_BICG) {
+    if (w.bulk && w.m >= kSeedTile) {
+      const uint32_t stage = seed_stage_bytes<V, R>(w.nproj);
+      const int nstage = 3 * stage <= 72 * 1024 ? 3 : 2;
+      const int dyn = nstage * (int)stage;
+      static int attr_bytes = 0, occ_bytes = -1, per_sm = 1;
+      auto kern = k_seed_update<P, NP, METHOD, true>;
+      cudaError_t e;
+      if (dyn > attr_bytes) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess)
+          return e;
+        attr_bytes = dyn;
+      }
+      if (occ_bytes != dyn) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, dyn) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+        occ_bytes = dyn;
+      }
+      const int grid = std::max(1, std::min(per_sm * w.num_sms, ntiles));
+      kern<<<grid, 256, dyn, w.stream>>>((int)w.m, (const V*)rn, (const V*)w.q, (V*)rm, (const R*)w.proj_rows,
+                                         w.proj_ld, w.nproj, parity, w.st, w.part, w.w, (const V*)rtn,
+                                         (const V*)w.qt, (V*)rtm, nstage, w.bulk == 2 ? 16u : 0u);
+      return cudaGetLastError();
+    }
+  }
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_seed_update<P, NP, METHOD, false>, 256, w.num_sms);
+  const int grid = std::max(1, std::min(nblk, ntiles));
+  k_seed_update<P, NP, METHOD, false><<<grid, 256, 0, w.stream>>>(
+      (int)w.m, (const V*)rn, (const V*)w.q, (V*)rm, (const R*)w.proj_rows, w.proj_ld, w.nproj, parity, w.st,
+      w.part, w.w, (const V*)rtn, (const V*)w.qt, (V*)rtm, 1, 0u);
   return cudaGetLastError();
 }
 
@@ -2009,7 +2130,7 @@ cudaError_t launch_init(Work& w) {
     return cudaErrorInvalidValue;
   const int nb = 4 * w.num_sms;
   k_init_vectors<P><<<nb, 256, 0, w.stream>>>((int)w.m, w.nproj, w.b, w.left, (V*)w.rA, (V*)w.rB,
-                                              (R*)w.proj_rows);
+                                              (R*)w.proj_rows, w.proj_ld);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (w.full) {

@@ -119,6 +119,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_spin_table": (C.c_int, [P, C.c_int]),
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
+        "kw_set_bulk_copy": (C.c_int, [P, C.c_int]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
         "kw_resume": (C.c_int, [P, I64, P, C.POINTER(kw_solve_info)]),
         "kw_rci_init": (C.c_int, [P, I64, P, I64, P, I64, P, P, C.POINTER(kw_rci_io)]),
@@ -521,6 +522,15 @@ class Solver:
         st = self._lib.kw_set_stream_overlap(self._ctx, 1 if on else 0)
         if st != KW_OK:
             raise self._err(st, "kw_set_stream_overlap")
+
+    def set_bulk_copy(self, on):
+        """kw_set_bulk_copy: stage the three-term update's tiles in shared memory
+        with TMA bulk copies (True) or read them with plain loads (False, the
+        default); 2 arms the stages for bytes that never arrive (a test of the
+        bounded wait)."""
+        st = self._lib.kw_set_bulk_copy(self._ctx, int(on))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_bulk_copy")
 
     def set_krylov_log(self, max_iters: int):
         """Record the Krylov log (at most max_iters rows) in the next solves; 0 = off."""
