@@ -325,7 +325,8 @@ def run_ours(args):
     if args.profile_iters:
         # profiling mode: the headline kernels on the same workload, one solve capped at N iterations
         prec = args.profile_prec or HEADLINE
-        s = kw.Solver(prec, tol=p.tol, maxiter=args.profile_iters)
+        # host-driven loop: every kernel is an ordinary stream launch for the profiler to replay
+        s = kw.Solver(prec, tol=p.tol, maxiter=args.profile_iters, use_graph=0)
         if args.profile_op == "spin":
             s.set_spin_operator(CHAIN_N, CHAIN_N // 2, [(i, (i + 1) % CHAIN_N) for i in range(CHAIN_N)], 1.0)
             cfg = "spin operator"
