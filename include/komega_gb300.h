@@ -84,6 +84,12 @@ typedef struct {
                             even).  The graph is kept and relaunched while the solve's descriptor is
                             unchanged.  Solves with a matrix-vector callback, or with kernel timing on
                             (kw_set_kernel_timing), use the host loop whatever this says. */
+    const char* tune_cache; /* NULL or "": the product kernel's layout is timed once per context.  A
+                            file path: the pick is looked up there first, keyed by the precision, M,
+                            nnz, a fingerprint of sampled rows (offsets, first column and value) and
+                            the device's SM count, and appended after a timing run.  One text line per
+                            pick; unreadable or foreign lines are skipped.  The string is copied by
+                            kw_create. */
 } kw_options;
 
 typedef struct {
@@ -100,7 +106,7 @@ typedef struct {
 int kw_abi_version(void);
 
 /* Fill *opt with defaults: KW_F64, tol 1e-10, maxiter 100000, seed_switch 1,
- * hist_stride 0, hist_max 0, use_graph 1. */
+ * hist_stride 0, hist_max 0, use_graph 1, tune_cache NULL. */
 void kw_default_options(kw_options* opt);
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -393,6 +399,8 @@ typedef struct {
     int64_t launches;
     int64_t timed_iters;
     double kernel_ms[4];
+    int64_t tune_runs;      /* timing runs of the product-kernel tuner in this context */
+    int64_t tune_hits;      /* picks taken from the persistent tuning cache (kw_options.tune_cache) */
 } kw_stats;
 
 /* Bracket the kernels of one iteration in every `every` with CUDA events on

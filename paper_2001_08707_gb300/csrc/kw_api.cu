@@ -12,6 +12,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "komega_gb300.h"
@@ -76,6 +77,7 @@ struct ScopedEvents {
 
 struct kw_ctx {
   kw_options opt;
+  std::string tune_cache;   // copy of opt.tune_cache (opt.tune_cache points here)
   cudaStream_t stream = nullptr;
   int device = 0;
   int num_sms = 0;
@@ -111,6 +113,8 @@ struct kw_ctx {
   DBuf valpair;               // FP32-pair copy of the values (KW_DF64, values not exact in FP32)
   DBuf inexact;
   bool val32_exact = false;   // every value representable in FP32
+  DBuf tune_fp;               // fingerprint samples for the persistent tuning cache
+  int64_t tune_runs = 0, tune_hits = 0;   // timing runs of the tuner; picks taken from the cache
   int spmv_lanes = 0;         // tuned or forced lanes per row (0 = tune at first use)
   int spmv_val_f32 = 0;       // tuned or forced: FP32 value array in FP64 mode
   int force_lanes = 0, force_val = -1;
@@ -211,6 +215,7 @@ void kw_default_options(kw_options* opt) {
   opt->hist_stride = 0;
   opt->hist_max = 0;
   opt->use_graph = 1;
+  opt->tune_cache = nullptr;
 }
 
 const char* kw_status_string(kw_status s) {
@@ -236,6 +241,8 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
     return KW_ERR_ARG;
   kw_ctx* ctx = new kw_ctx();
   ctx->opt = *opt;
+  if (opt->tune_cache) ctx->tune_cache = opt->tune_cache;
+  ctx->opt.tune_cache = ctx->tune_cache.c_str();
   ctx->stream = (cudaStream_t)cuda_stream;
   ctx->err[0] = 0;
   cudaError_t e = cudaGetDevice(&ctx->device);
@@ -263,7 +270,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->mv_r, &ctx->mv_q, &ctx->mv_r2, &ctx->mv_q2, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->sp_table, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
-                  &ctx->rc_flag};
+                  &ctx->rc_flag, &ctx->tune_fp};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
   if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
@@ -711,6 +718,65 @@ static cudaError_t spmv_dot_launch(kw::Work& w, const void* r, void* q, double2 
 // and the pick would be noise); they use one thread per row and FP64 values.
 static const int64_t kTuneMinNnz = 1 << 20;
 
+// ---------------------------------------------------------------- persistent tuning cache
+// One line per pick: "kwtune1 <prec> <m> <nnz> <fingerprint> <sms> <lanes> <val_f32>".
+struct TuneKey {
+  int prec;
+  long long m, nnz;
+  unsigned long long fp;
+  int sms;
+};
+
+// FNV-1a over sampled rows (row offsets, first column and its value's bits).
+static kw_status tune_fingerprint(kw_ctx* ctx, unsigned long long* fp) {
+  const int ns = kw::kTuneSamples;
+  KW_CUDA(ctx->tune_fp.ensure((size_t)ns * 4 * sizeof(long long)), "tune cache alloc");
+  KW_CUDA(kw::launch_fingerprint((int)ctx->m, ctx->rowptr, ctx->col, ctx->val, (long long*)ctx->tune_fp.p,
+                                 ctx->stream), "tune fingerprint");
+  std::vector<long long> h((size_t)ns * 4);
+  KW_CUDA(cudaMemcpyAsync(h.data(), ctx->tune_fp.p, h.size() * sizeof(long long), cudaMemcpyDeviceToHost,
+                          ctx->stream), "tune fingerprint copy");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "tune fingerprint sync");
+  unsigned long long x = 1469598103934665603ULL;
+  for (long long v : h)
+    for (int b = 0; b < 8; ++b) {
+      x ^= (unsigned long long)((v >> (8 * b)) & 0xff);
+      x *= 1099511628211ULL;
+    }
+  *fp = x;
+  return KW_OK;
+}
+
+static bool tune_cache_lookup(const char* path, const TuneKey& k, int* lanes, int* val) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[256];
+  bool found = false;
+  while (fgets(line, sizeof(line), f)) {
+    int prec = 0, sms = 0, l = 0, v = 0;
+    long long m = 0, nnz = 0;
+    unsigned long long fp = 0;
+    if (sscanf(line, "kwtune1 %d %lld %lld %llx %d %d %d", &prec, &m, &nnz, &fp, &sms, &l, &v) != 7) continue;
+    if (prec == k.prec && m == k.m && nnz == k.nnz && fp == k.fp && sms == k.sms) {
+      *lanes = l;   // the last matching line wins
+      *val = v;
+      found = true;
+    }
+  }
+  fclose(f);
+  return found;
+}
+
+static void tune_cache_store(const char* path, const TuneKey& k, int lanes, int val) {
+  FILE* f = fopen(path, "a");
+  if (!f) return;   // an unwritable cache only costs the next context a timing run
+  char line[256];
+  const int n = snprintf(line, sizeof(line), "kwtune1 %d %lld %lld %016llx %d %d %d\n", k.prec, k.m, k.nnz, k.fp,
+                         k.sms, lanes, val);
+  if (n > 0) fwrite(line, 1, (size_t)n, f);   // one write per line (appends do not interleave within it)
+  fclose(f);
+}
+
 static bool has_operator(const kw_ctx* ctx) {
   return ctx->rowptr || ctx->mv_fn || ctx->rci_active || ctx->op >= kw::OP_SPIN;
 }
@@ -741,6 +807,38 @@ static kw_status tune_spmv(kw_ctx* ctx) {
       return build_sell(ctx);
     }
     return KW_OK;
+  }
+  // persistent cache: a pick stored for this operator and device is applied without timing
+  const bool use_cache = ctx->opt.tune_cache && ctx->opt.tune_cache[0] && ctx->force_lanes == 0 &&
+                         ctx->force_val < 0;
+  TuneKey key = {(int)p, (long long)ctx->m, (long long)ctx->nnz, 0ULL, ctx->num_sms};
+  if (use_cache) {
+    kw_status fs = tune_fingerprint(ctx, &key.fp);
+    if (fs != KW_OK) return fs;
+    int cl = 0, cv = 0;
+    if (tune_cache_lookup(ctx->opt.tune_cache, key, &cl, &cv)) {
+      const bool lanes_ok = (cl >= 1 && cl <= 16 && (cl & (cl - 1)) == 0) || cl == kw::KW_SPMV_SELL ||
+                            (cl > kw::KW_SPMV_UNIFORM && cl <= kw::KW_SPMV_UNIFORM + 16);
+      const bool val_ok = cv == 0 || (cv == 1 && (p != KW_F64 || ctx->val32_exact));
+      bool ok = lanes_ok && val_ok;
+      if (ok && cl > kw::KW_SPMV_UNIFORM) {
+        kw_status us = build_uniform(ctx);
+        if (us != KW_OK) return us;
+        ok = ctx->u_state == 1;   // the values may differ from the operator the pick was timed on
+      }
+      if (ok && cl == kw::KW_SPMV_SELL) {
+        kw_status bs = build_sell(ctx);
+        if (bs != KW_OK) return bs;
+      }
+      if (ok) {
+        ctx->spmv_lanes = cl;
+        ctx->spmv_val_f32 = cl > kw::KW_SPMV_UNIFORM ? (ctx->u_kind == 1 ? 1 : 0)
+                            : cl == kw::KW_SPMV_SELL ? (p == KW_F64 ? 0 : cv)
+                                                     : cv;
+        ctx->tune_hits += 1;
+        return KW_OK;
+      }
+    }
   }
   const size_t vs = vec_bytes(p);
   KW_CUDA(ctx->rA.ensure(ctx->m * vs), "tune alloc");
@@ -806,6 +904,8 @@ static kw_status tune_spmv(kw_ctx* ctx) {
     ctx->sell_val.release();
     ctx->sell_built = false;
   }
+  ctx->tune_runs += 1;
+  if (use_cache) tune_cache_store(ctx->opt.tune_cache, key, ctx->spmv_lanes, ctx->spmv_val_f32);
   return KW_OK;
 }
 
@@ -1804,6 +1904,8 @@ kw_status kw_get_spmv_config(kw_ctx* ctx, int* lanes, int* val_f32) {
 kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out) {
   if (!ctx || !out) return KW_ERR_ARG;
   *out = ctx->stats;
+  out->tune_runs = ctx->tune_runs;
+  out->tune_hits = ctx->tune_hits;
   return KW_OK;
 }
 

@@ -217,6 +217,13 @@ cudaError_t launch_spin_setup(int m, int nsite, int nup, int nbond, const int* b
 cudaError_t launch_spin_table(int m, int nbond, const int* bond, const int* binom, const unsigned* basis, int* table,
                               cudaStream_t s);
 
+// Fingerprint of a CSR operator for the persistent tuning cache: for kTuneSamples
+// rows spread over [0, m), out[4s..4s+3] = row, rowptr[row+1] - rowptr[row], the
+// row's first column (or -1) and its value's bits (or 0).
+constexpr int kTuneSamples = 256;
+cudaError_t launch_fingerprint(int m, const int64_t* rowptr, const int* col, const double* val, long long* out,
+                               cudaStream_t s);
+
 // Batched solves: count of instances whose solve has stopped (written to *out).
 cudaError_t launch_count_done(int n, State* const* states, int* out, cudaStream_t s);
 // Loop condition of a CUDA graph WHILE node: continue while *count < target and

@@ -48,6 +48,24 @@ template cudaError_t launch_sell_fill<float>(int, const int*, const int*, const 
 template cudaError_t launch_sell_fill<df>(int, const int*, const int*, const int64_t*, const int64_t*, const int*,
                                            const void*, int*, void*, cudaStream_t);
 
+static __global__ void k_fingerprint(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                     const double* __restrict__ val, long long* out) {
+  for (int t = threadIdx.x; t < kTuneSamples; t += blockDim.x) {
+    const long long row = m > 1 ? (long long)t * (m - 1) / (kTuneSamples - 1) : 0;
+    const int64_t b = rowptr[row], e = rowptr[row + 1];
+    out[4 * t] = row;
+    out[4 * t + 1] = (long long)(e - b);
+    out[4 * t + 2] = e > b ? (long long)col[b] : -1;
+    out[4 * t + 3] = e > b ? __double_as_longlong(val[b]) : 0;
+  }
+}
+
+cudaError_t launch_fingerprint(int m, const int64_t* rowptr, const int* col, const double* val, long long* out,
+                               cudaStream_t s) {
+  k_fingerprint<<<1, kTuneSamples, 0, s>>>(m, rowptr, col, val, out);
+  return cudaGetLastError();
+}
+
 // Number of instances of a batch whose solve has stopped.
 static __global__ void k_count_done(int n, State* const* states, int* out) {
   int c = 0;

@@ -29,7 +29,8 @@ MAX_PROJ = 32
 
 class kw_options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tol", C.c_double), ("maxiter", C.c_int64), ("seed_switch", C.c_int),
-                ("hist_stride", C.c_int64), ("hist_max", C.c_int64), ("use_graph", C.c_int)]
+                ("hist_stride", C.c_int64), ("hist_max", C.c_int64), ("use_graph", C.c_int),
+                ("tune_cache", C.c_char_p)]
 
 ABI_VERSION = 2   # KW_ABI_VERSION of the header these structures mirror
 
@@ -59,7 +60,8 @@ class kw_rci_io(C.Structure):
 
 
 class kw_stats(C.Structure):
-    _fields_ = [("launches", C.c_int64), ("timed_iters", C.c_int64), ("kernel_ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int64), ("timed_iters", C.c_int64), ("kernel_ms", C.c_double * 4),
+                ("tune_runs", C.c_int64), ("tune_hits", C.c_int64)]
 
 
 _lib = None
@@ -214,12 +216,14 @@ class Solver:
 
     use_graph: 1 (default) runs the iterations as a device-side loop in one CUDA
     graph; 0 has the host enqueue them in chunks; n >= 2 sets the iterations per
-    trip of the device-side loop (kw_options.use_graph).
+    trip of the device-side loop (kw_options.use_graph).  tune_cache: a file in
+    which the product kernel's tuned layout is looked up and stored
+    (kw_options.tune_cache).
     """
 
     def __init__(self, prec: str = "f64", tol: float = 1e-10, maxiter: int = 100000, seed_switch: bool = True,
                  hist_stride: int = 0, hist_max: int = 0, stream=None, method: str = "cocg",
-                 use_graph: int = 1):
+                 use_graph: int = 1, tune_cache: str | None = None):
         import torch
 
         self._torch = torch
@@ -228,7 +232,8 @@ class Solver:
         lib = load_library()
         self._lib = lib
         self.prec = PRECISIONS[prec]
-        opt = kw_options(self.prec, tol, maxiter, 1 if seed_switch else 0, hist_stride, hist_max, int(use_graph))
+        opt = kw_options(self.prec, tol, maxiter, 1 if seed_switch else 0, hist_stride, hist_max, int(use_graph),
+                         tune_cache.encode() if tune_cache else None)
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
         ctx = C.c_void_p()
@@ -607,7 +612,8 @@ class Solver:
         st = self._lib.kw_get_stats(self._ctx, C.byref(s))
         if st != KW_OK:
             raise self._err(st, "kw_get_stats")
-        return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms)}
+        return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms),
+                "tune_runs": s.tune_runs, "tune_hits": s.tune_hits}
 
     def solve_batched(self, problems, check: bool = True):
         """kw_solve_batched over a list of problems, each a dict with keys H (CSR with
