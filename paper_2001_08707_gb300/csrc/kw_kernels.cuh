@@ -2102,7 +2102,11 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   *launches += (w.mv_fn && P == PREC_DF) ? 4 : 3;
   if (w.full) {
     static int nblk_xp_per_sm = 0;
-    const int nblk_xp = resident_blocks(nblk_xp_per_sm, k_update_xp<P, 8>, 256, w.num_sms);
+    // no more blocks than (shift tile, row chunk) items at full activity: every block takes part
+    // in the arrival count, so idle blocks would only add to it
+    const long long items = (long long)((w.K + 7) / 8) * ((w.m + 255) / 256);
+    const int nblk_xp = (int)std::max<long long>(
+        1, std::min<long long>(resident_blocks(nblk_xp_per_sm, k_update_xp<P, 8>, 256, w.num_sms), items));
     k_update_xp<P, 8><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
                                                       (const V*)rm, w.st);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
