@@ -519,6 +519,79 @@ def run_ours(args):
                            "projection_rel_err_vs_headline": e_proj,
                            "note": "same Hamiltonian generated on the fly instead of the CSR input"}
 
+    # Full mode (Eqs. 23-24): the fused x/p update K4 over every shift's x and p,
+    # on the J1-J2 chain N=20 (M=184,756) with K=256 shifts, the x/p sizes of the
+    # adjoint workload.  tol = 0 keeps all 256 shifts active, so each sampled K4
+    # moves exactly 4 s K M bytes of x/p (s = element size) plus r once per tile
+    # of 8 shifts.  One warm-up and one sampled solve of 240 iterations per form.
+    from paper_2001_08707_gb300 import workloads as wl
+    jm = wl.j1j2_chain(20, 1.0, 0.4, 0.2, seed=wl.SEED_BASE + 3)
+    Hj = jm.assemble()
+    jlo, jhi = wl.chain_bounds(Hj)
+    zj = wl.shiftk_grid(jlo - 0.5, jhi + 0.5, 256, 0.05)
+    bj = torch.as_tensor(wl.gaussian_unit(Hj.m, wl.SEED_BASE + 3), device=device)
+    hbm_peak, hbm_kind = load_peaks()
+    full = {"workload": "j1j2_chain_N20_K256_full_x", "M": Hj.m, "K": 256, "iterations": 240}
+    for prec in ("df64", "c32", "f64"):
+        sj = kw.Solver(prec, tol=0.0, maxiter=240)
+        sj.set_csr(Hj.rowptr, Hj.col, Hj.val)
+        xj = torch.empty((256, Hj.m), dtype=torch.complex64 if prec == "c32" else torch.complex128, device=device)
+        sj.solve(bj, zj, full=True, x_out=xj, check=False)
+        sj.set_kernel_timing(1)
+        sj.solve(bj, zj, full=True, x_out=xj, check=False)
+        jst = sj.stats()
+        sj.close()
+        ti, k = kstats([jst])
+        es = PREC_BYTES[prec][0]
+        xp_bytes = 4 * es * 256 * Hj.m + es * Hj.m * (256 // 8)
+        gbs = xp_bytes / (k[3] * 1e-3) / 1e9
+        ent = {"k_update_xp_us": 1e3 * k[3], "bytes": xp_bytes, "gbs": gbs, "sampled_iterations": ti}
+        if prec == "f64":   # complex FP64: x += alpha p (8 flops), p = r (1/pi) + beta p (14 flops)
+            tf = 22 * 256 * Hj.m / (k[3] * 1e-3) / 1e12
+            ent["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": tf / FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64"}
+        else:
+            ent["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": gbs / hbm_peak, "peak_kind": f"{hbm_kind} HBM copy bandwidth"}
+        full[prec] = ent
+    legs["full_update"] = full
+
+    # The Anderson cube L=160 (M=4,096,000), 4096 shifts, b and 16 left vectors:
+    # K1 as the generated lattice operator and as the CSR input (uniform
+    # off-diagonal layout), and K2 with 17 projection rows.  Per row: K1 reads
+    # the pair diagonal (8 B) and r, writes q (+4 B offset and 6 x 4 B columns
+    # for the CSR layout); K2 reads r_n, q, r_{n-1} and 17 rows, writes r_{n+1}.
+    pa = wl.anderson_contour()
+    ba = torch.as_tensor(pa.b, device=device)
+    la = torch.as_tensor(pa.left, device=device)
+    anderson = {"workload": "anderson_L160_K4096_projected16", "M": pa.H.m, "K": int(pa.z.size),
+                "iterations": 160}
+    es = PREC_BYTES[HEADLINE][0]
+    eps = pa.H.to_scipy().diagonal().copy()
+    for op in ("lattice", "csr"):
+        sa = kw.Solver(HEADLINE, tol=0.0, maxiter=160)
+        if op == "lattice":
+            sa.set_lattice3d(160, 160, 160, eps, -1.0)
+        else:
+            sa.set_csr(pa.H.rowptr, pa.H.col, pa.H.val)
+        sa.solve(ba, pa.z, left=la, check=False)
+        sa.set_kernel_timing(1)
+        sa.solve(ba, pa.z, left=la, check=False)
+        a_stats = sa.stats()
+        cfg = list(sa.spmv_config()) if op == "csr" else "lattice operator"
+        sa.close()
+        ti, k = kstats([a_stats])
+        k1_bytes = (8 + 2 * es + (0 if op == "lattice" else 28)) * pa.H.m
+        k2_bytes = (4 * es + 17 * PREC_BYTES[HEADLINE][1]) * pa.H.m
+        k1_gbs = k1_bytes / (k[0] * 1e-3) / 1e9
+        k2_gbs = k2_bytes / (k[1] * 1e-3) / 1e9
+        anderson[op] = {"spmv_us": 1e3 * k[0], "spmv_bytes": k1_bytes, "spmv_gbs": k1_gbs,
+                        "spmv_frac": k1_gbs / hbm_peak, "seed_update_us": 1e3 * k[1], "seed_update_bytes": k2_bytes,
+                        "seed_update_gbs": k2_gbs, "seed_update_frac": k2_gbs / hbm_peak, "shift_us": 1e3 * k[2],
+                        "sampled_iterations": ti, "spmv_config": cfg}
+    anderson["peak_kind"] = f"{hbm_kind} HBM copy bandwidth"
+    legs["anderson_L160"] = anderson
+
     peak, peak_kind = load_peaks()
     kh = kernels[HEADLINE]
     launches = sum(s["launches"] for s in h_stats)

@@ -439,19 +439,20 @@ kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user);
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
 
 /* Loads of the three-term update (Eq. 16) in the FP32 and FP32-pair forms.
- * on = 0 (the default): plain coalesced loads.  on = 1: the tiles of r_n, q_n,
- * r_{n-1} and the projection rows are staged in shared memory by TMA bulk
- * copies (cp.async.bulk) completed on mbarriers, up to three tiles ahead of the
- * arithmetic.  Each thread sums the same elements in the same order either way;
- * the results agree to rounding (the two kernels are compiled separately).  On
- * the N=24 Heisenberg benchmark the staged kernel is slower (74 vs 67 us per
- * update in the pair form, equal in the FP32 form), so it is off by default.  A
- * staged copy that does not complete within about a second ends the solve with
- * KW_ERR_TIMEOUT.  The FP64 form and BiCG always use plain loads.  on = 2
- * exercises that bound: each stage is armed for 16 bytes more than its copies
- * bring, so the first staged wait of every block runs out and the solve ends
- * with KW_ERR_TIMEOUT after a few seconds (the context stays usable).
- * Errors: KW_ERR_ARG. */
+ * on = 1: the tiles of r_n, q_n, r_{n-1} and the projection rows are staged in
+ * shared memory by TMA bulk copies (cp.async.bulk) completed on mbarriers, up to
+ * three tiles ahead of the arithmetic; on = 0: plain coalesced loads; on = -1
+ * (the default): staged when the update carries more than 9 projection rows.
+ * Each thread sums the same elements in the same order either way; the results
+ * agree to rounding (the two kernels are compiled separately).  Measured on
+ * GB300: with 17 projection rows (Anderson L=160) staging takes the update from
+ * 281 to 256 us (pairs) and 133 to 110 us (FP32); with 5 rows (Heisenberg N=24)
+ * plain loads are faster (67 vs 74 us, pairs).  A staged copy that does not
+ * complete within about a second ends the solve with KW_ERR_TIMEOUT.  The FP64
+ * form and BiCG always use plain loads.  on = 2 exercises that bound: each
+ * stage is armed for 16 bytes more than its copies bring, so the first staged
+ * wait of every block runs out and the solve ends with KW_ERR_TIMEOUT after a
+ * few seconds (the context stays usable).  Errors: KW_ERR_ARG. */
 kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
 
 /* Configuration of the sparse product kernel.  lanes = threads per matrix

@@ -143,7 +143,7 @@ struct kw_ctx {
   cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr;
   DBuf part_k1;   // K1's block partials (K1 overlaps K3, which uses part)
   int overlap = 1;
-  int bulk = 0;   // kw_set_bulk_copy
+  int bulk = -1;  // kw_set_bulk_copy (-1: auto)
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -1862,7 +1862,7 @@ kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {
 }
 
 kw_status kw_set_bulk_copy(kw_ctx* ctx, int on) {
-  if (!ctx || on < 0 || on > 2) return KW_ERR_ARG;
+  if (!ctx || on < -1 || on > 2) return KW_ERR_ARG;
   ctx->bulk = on;
   return KW_OK;
 }

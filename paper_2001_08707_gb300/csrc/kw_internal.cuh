@@ -101,7 +101,7 @@ struct Work {
   const double* left;  // caller's left vectors (FP64) [nproj-1][m]
   void* proj_rows;   // [nproj][proj_ld] real, vector precision (b then left vectors)
   int64_t proj_ld;   // row stride of proj_rows: m rounded up to KW_PROJ_ALIGN elements (16-byte aligned rows)
-  int bulk = 0;      // 1: K2 stages its tiles in shared memory with TMA bulk copies where the form allows
+  int bulk = -1;     // K2 tile staging by TMA bulk copies: -1 auto (more than 9 projection rows), 0 off, 1 on, 2 test
   // shift state
   double2* z;
   double2* pi1;      // pi_n

@@ -1943,7 +1943,9 @@ static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   // Staged form: the FP32 and FP32-pair forms, whose update is bound by memory
   // latency, not by the FP64 pipe; the BiCG shadow keeps plain loads.
   if constexpr (P != PREC_F64 && METHOD != KW_METHOD_BICG) {
-    if (w.bulk && w.m >= kSeedTile) {
+    // auto (bulk < 0): staged when more than 9 projection rows make the plain kernel register-bound
+    const bool staged = w.bulk > 0 || (w.bulk < 0 && w.nproj > 9);
+    if (staged && w.m >= kSeedTile) {
       const uint32_t stage = seed_stage_bytes<V, R>(w.nproj);
       const int nstage = 3 * stage <= 72 * 1024 ? 3 : 2;
       const int dyn = nstage * (int)stage;
@@ -2085,8 +2087,10 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   a.part = w.part;
   a.log = w.log;
   a.log_max = w.log_max;
-  const int lps = w.full ? 1 : (w.nproj <= 1 ? 1 : w.nproj <= 2 ? 2 : w.nproj <= 4 ? 4 : w.nproj <= 8 ? 8
-                                                                     : w.nproj <= 16 ? 16 : 32);
+  // lanes per shift: one per projection row up to 4; beyond that each lane takes several rows, so
+  // that the shift's FP64 scalars are not recomputed on many lanes and the grid (one warp per block,
+  // each arriving on the block counter) stays small.  Every choice gives the same numbers.
+  const int lps = w.full ? 1 : (w.nproj <= 1 ? 1 : w.nproj <= 2 ? 2 : 4);
   const int spw = 32 / lps;
   const int nb3 = (w.K + spw - 1) / spw;
   switch (lps) {

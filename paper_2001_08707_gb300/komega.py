@@ -530,9 +530,9 @@ class Solver:
 
     def set_bulk_copy(self, on):
         """kw_set_bulk_copy: stage the three-term update's tiles in shared memory
-        with TMA bulk copies (True) or read them with plain loads (False, the
-        default); 2 arms the stages for bytes that never arrive (a test of the
-        bounded wait)."""
+        with TMA bulk copies (True), read them with plain loads (False), or -1
+        (the default) to stage only with more than 9 projection rows; 2 arms the
+        stages for bytes that never arrive (a test of the bounded wait)."""
         st = self._lib.kw_set_bulk_copy(self._ctx, int(on))
         if st != KW_OK:
             raise self._err(st, "kw_set_bulk_copy")

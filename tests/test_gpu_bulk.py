@@ -102,7 +102,25 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     np.testing.assert_array_equal(again.proj, good.proj)
 
 
+@pytest.mark.parametrize("nleft,staged", [(16, True), (8, True), (4, False)])
+def test_default_stages_only_many_projection_rows(nleft, staged):
+    """The default (-1) runs the staged kernel above 9 projection rows (b and
+    nleft left vectors), the plain one otherwise: it equals that choice bit for bit."""
+    m = 4113
+    H = _chain(m)
+    b = w.gaussian_unit(m, 21)
+    left = np.stack([w.gaussian_unit(m, 22 + i) for i in range(nleft)])
+    z = w.shiftk_grid(-3, 3, 24, 0.04)
+    out = {}
+    for mode in (-1, 1 if staged else 0):
+        s = kw.Solver("df64", tol=1e-9, maxiter=8)
+        s.set_bulk_copy(mode)
+        s.set_csr(H.rowptr, H.col, H.val)
+        out[mode] = s.solve(b, z, left=left, check=False).proj
+    np.testing.assert_array_equal(out[-1], out[1 if staged else 0])
+
+
 def test_bulk_copy_argument():
     s = kw.Solver("df64")
     assert s._lib.kw_set_bulk_copy(s._ctx, 3) == kw.KW_ERR_ARG
-    assert s._lib.kw_set_bulk_copy(s._ctx, -1) == kw.KW_ERR_ARG
+    assert s._lib.kw_set_bulk_copy(s._ctx, -2) == kw.KW_ERR_ARG
