@@ -102,7 +102,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     np.testing.assert_array_equal(again.proj, good.proj)
 
 
-@pytest.mark.parametrize("nleft,staged", [(16, True), (8, True), (4, False)])
+@pytest.mark.parametrize("nleft,staged", [(16, True), (9, True), (8, False), (4, False)])
 def test_default_stages_only_many_projection_rows(nleft, staged):
     """The default (-1) runs the staged kernel above 9 projection rows (b and
     nleft left vectors), the plain one otherwise: it equals that choice bit for bit."""
