@@ -261,7 +261,7 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
 
 void kw_destroy(kw_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->stream || true) cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->stream);   // the caller's stream (possibly the legacy one) may hold our work
   DBuf* bufs[] = {&ctx->bil_part, &ctx->bil_out, &ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->sell_perm, &ctx->sell_len,
                   &ctx->sell_slen, &ctx->sell_ptr, &ctx->sell_col, &ctx->sell_val, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
@@ -1494,7 +1494,6 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   ScopedEvents ev;
   KW_CUDA(ev.create((size_t)n + 1, cudaEventDisableTiming), "batch events");
   kw_status result = KW_OK;
-  auto cleanup = [&]() {};   // the events are released by their holder
   KW_CUDA(cudaEventRecord(ev[n], bs), "batch event");   // instances start after the caller's work
   for (int64_t i = 0; i < n; ++i) {
     kw_ctx* c = ctx->children[i];
@@ -1511,7 +1510,6 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
       s = solve_begin(c, inst[i].b_dev, inst[i].nshift, inst[i].z_host, inst[i].nleft, inst[i].left_dev,
                       inst[i].x_out_dev);
     if (s != KW_OK) {
-      cleanup();
       return fail(ctx, s, "kw_solve_batched: instance %lld: %s", (long long)i, c->err);
     }
     KW_CUDA(cudaEventRecord(ev[i], c->stream), "batch event");
@@ -1618,7 +1616,6 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
   }
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
-  cleanup();
   if (ce != cudaSuccess) return cuda_fail(ctx, ce, "kw_solve_batched: graph launch");
   for (int64_t i = 0; i < n; ++i) {
     kw_ctx* c = ctx->children[i];
