@@ -406,7 +406,7 @@ def run_ours(args):
                 float((np.abs(res.proj - h_res.proj).max(axis=0) / np.abs(h_res.proj).max(axis=0)).max()))
 
     legs = {}
-    # Plain FP64 form (the spec comparison), one warm-up and one timed solve.
+    # Plain FP64 form (the comparison for the FP32-vector form), one warm-up and one timed solve.
     f_times, f_stats, f_res, f_cfg = device_leg("f64", 1, 1, 200000)
     f_ms = reduce_max(statistics.mean(f_times), ws, device)
     kernels["f64"] = kern("f64", f_cfg, f_stats, f_res.iters, f_ms)

@@ -117,7 +117,7 @@ def test_recalc_from_device_log_matches_dense(prec):
     if prec != "c32":                           # the FP32-vector form may stall above tol
         assert r.status == "KW_OK" and rc.status == "KW_OK"
     ref, bound = _dense_bound(H, b, left, znew, rc.final_res)
-    if prec == "c32":                           # FP32 vectors: judged on the spectrum error
+    if prec == "c32":                           # FP32 vectors: checked on the spectrum error
         assert np.abs(rc.proj - ref).max() <= 1e-5 * np.abs(ref).max()
     else:
         assert np.all(np.abs(rc.proj - ref) <= bound + 1e-12)
