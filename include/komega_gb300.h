@@ -46,7 +46,7 @@ typedef enum {
     KW_ERR_OOM = 3,          /* device allocation failed */
     KW_ERR_BREAKDOWN = 4,    /* rho_n = 0, zero alpha denominator (Eq. 17) or pi_{n+1} = 0 (Eq. 20) */
     KW_ERR_NONFINITE = 5,    /* a seed scalar became Inf/NaN */
-    KW_ERR_CALLBACK = 6,     /* reserved: user matvec callback failure */
+    KW_ERR_CALLBACK = 6,     /* the matrix-vector callback returned nonzero */
     KW_ERR_TIMEOUT = 7,      /* a bounded device wait expired (a staged copy did not complete) */
     KW_NOT_CONVERGED = 8     /* maxiter reached; outputs hold the last iterates */
 } kw_status;
