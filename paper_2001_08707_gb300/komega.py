@@ -206,6 +206,21 @@ class RecalcResult:
     status: str
 
 
+def check_solve_arrays(m, b, left, x_out, K, vec_dtype):
+    """Sizes the C ABI cannot see (it takes bare pointers): b holds m values,
+    left is [nleft][m] (or one row of m), and x_out, when given, is a
+    contiguous [K][m] tensor of the form's complex type.  Raises ValueError."""
+    if m is not None and b.numel() != m:
+        raise ValueError(f"b has {b.numel()} entries, the operator has {m} rows")
+    if left is not None and m is not None and (left.shape[-1] != m or left.dim() > 2):
+        raise ValueError(f"left has shape {tuple(left.shape)}, expected [nleft, {m}]")
+    if x_out is not None:
+        if x_out.dtype != vec_dtype:
+            raise ValueError(f"x_out has dtype {x_out.dtype}, the form writes {vec_dtype}")
+        if not x_out.is_contiguous() or (m is not None and x_out.numel() != K * m):
+            raise ValueError(f"x_out must be a contiguous [{K}, {m}] tensor, got {tuple(x_out.shape)}")
+
+
 def _z_array(z):
     z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
     return z, z.ctypes.data_as(C.c_void_p)
@@ -288,6 +303,8 @@ class Solver:
         self.m = m
 
     def solve(self, b, z, left=None, full: bool = False, x_out=None, check: bool = True) -> SolveResult:
+        """kw_solve.  x_out (a CUDA tensor [K, m] of the form's complex type)
+        receives x^(k) and implies full mode."""
         t = self._torch
         bd = self._dev(b, t.float64)
         zz, zp = _z_array(z)
@@ -298,6 +315,11 @@ class Solver:
             lp = C.c_void_p(ld.data_ptr())
         else:
             ld, nleft, lp = None, 0, None
+        if x_out is not None:
+            if not x_out.is_cuda:
+                raise ValueError("x_out must be a CUDA tensor")
+            full = True
+        check_solve_arrays(self.m, bd, ld, x_out, K, self.vec_dtype)
         x = None
         xp = None
         if full:

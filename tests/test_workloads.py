@@ -99,3 +99,27 @@ def test_shift_grids():
     c = w.circle_points(0.3, 0.5, 2048)
     np.testing.assert_allclose(np.abs(c - 0.3), 0.5)
     assert np.isclose(np.min(np.abs(c.imag)), 0.5 * np.sin(np.pi / 2048))
+
+
+def test_solve_array_checks():
+    """The binding checks the sizes the C ABI cannot see before any call."""
+    import torch
+
+    from paper_2001_08707_gb300.komega import check_solve_arrays
+
+    m, K = 10, 3
+    b = torch.zeros(m, dtype=torch.float64)
+    left = torch.zeros(2, m, dtype=torch.float64)
+    x = torch.zeros(K, m, dtype=torch.complex128)
+    check_solve_arrays(m, b, left, x, K, torch.complex128)
+    check_solve_arrays(None, b, None, None, K, torch.complex128)   # no operator yet: nothing to compare
+    bad = [dict(b=torch.zeros(m + 1, dtype=torch.float64)),
+           dict(left=torch.zeros(2, m - 1, dtype=torch.float64)),
+           dict(x=torch.zeros(K, m, dtype=torch.complex64)),
+           dict(x=torch.zeros(K + 1, m, dtype=torch.complex128)),
+           dict(x=torch.zeros(m, K, dtype=torch.complex128).t())]
+    for case in bad:
+        args = dict(b=b, left=left, x=x)
+        args.update(case)
+        with pytest.raises(ValueError):
+            check_solve_arrays(m, args["b"], args["left"], args["x"], K, torch.complex128)
