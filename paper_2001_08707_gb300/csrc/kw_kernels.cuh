@@ -5,6 +5,8 @@
 //   K2 k_seed_update  r_{n+1} = (1+c_n) r_n - alpha_n q - c_n r_{n-1} (Eq. 16), with
 //                     rho_{n+1} = r^T r, nu = r^dagger r and w_l = a_l^T r_{n+1} (the
 //                     P r_{n+1} of Eq. 26); last block: beta_n = rho_{n+1}/rho_n.
+//                     With more than 9 projection rows (FP32 and pair forms) its tiles
+//                     are staged in shared memory by TMA bulk copies on mbarriers.
 //   K3 k_shift        per active shift: pi_{n+1} (Eq. 20), alpha^k, beta^k (Eq. 21-22),
 //                     projected y/u update (Eq. 25-26), residual ||r||/|pi|, freeze,
 //                     compaction; last block: seed switch (Sec. 2.2.4), stop flag.
@@ -21,7 +23,9 @@
 // Every kernel reads the iteration state from device memory, so the host only
 // enqueues launches; no host synchronisation happens inside the loop.
 // Reductions are deterministic: fixed per-block partials summed in a fixed
-// order by the last block to finish (arrival counter, no spin-wait).
+// order by the last block to finish (arrival counter, no spin-wait).  The only
+// waits are the staged K2's mbarrier waits, each bounded by a poll limit after
+// which the solve stops with KW_ERR_TIMEOUT.
 #pragma once
 
 #include <cuda_runtime.h>
