@@ -221,6 +221,14 @@ def check_solve_arrays(m, b, left, x_out, K, vec_dtype):
             raise ValueError(f"x_out must be a contiguous [{K}, {m}] tensor, got {tuple(x_out.shape)}")
 
 
+def check_vector_bytes(name, v, m, elem_bytes):
+    """A device vector handed to the C ABI as a bare pointer: contiguous and
+    exactly m elements of elem_bytes bytes.  Raises ValueError."""
+    if m is not None and (not v.is_contiguous() or v.numel() * v.element_size() != m * elem_bytes):
+        raise ValueError(f"{name} must be a contiguous vector of {m} elements of {elem_bytes} bytes, "
+                         f"got {tuple(v.shape)} {v.dtype}")
+
+
 def _z_array(z):
     z = np.ascontiguousarray(np.asarray(z, dtype=np.complex128))
     return z, z.ctypes.data_as(C.c_void_p)
@@ -689,6 +697,11 @@ class Solver:
         """q = zs r - H r and t = r^T q on the device.  r, q: device tensors in the
         context's element layout (complex128 for f64, complex64 for c32, float32
         [m, 4] pairs (re.hi, re.lo, im.hi, im.lo) for df64)."""
+        eb = 8 if self.prec == KW_C32V_F64S else 16
+        for name, v in (("r", r), ("q", q)):
+            if not v.is_cuda:
+                raise ValueError(f"{name} must be a CUDA tensor")
+            check_vector_bytes(name, v, self.m, eb)
         t = kw_c128()
         st = self._lib.kw_spmv_dot(self._ctx, kw_c128(zs.real, zs.imag), C.c_void_p(r.data_ptr()),
                                    C.c_void_p(q.data_ptr()), C.byref(t))

@@ -123,3 +123,18 @@ def test_solve_array_checks():
         args.update(case)
         with pytest.raises(ValueError):
             check_solve_arrays(m, args["b"], args["left"], args["x"], K, torch.complex128)
+
+
+def test_vector_byte_checks():
+    import torch
+
+    from paper_2001_08707_gb300.komega import check_vector_bytes
+
+    m = 7
+    check_vector_bytes("r", torch.zeros(m, dtype=torch.complex128), m, 16)
+    check_vector_bytes("r", torch.zeros(m, 4, dtype=torch.float32), m, 16)   # FP32 pairs
+    check_vector_bytes("r", torch.zeros(m, dtype=torch.complex64), m, 8)
+    for bad in (torch.zeros(m + 1, dtype=torch.complex128), torch.zeros(m, dtype=torch.complex64),
+                torch.zeros(4, m, dtype=torch.float32).t()):
+        with pytest.raises(ValueError):
+            check_vector_bytes("r", bad, m, 16)
