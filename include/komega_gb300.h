@@ -102,29 +102,38 @@ typedef struct {
     kw_status status;
 } kw_solve_info;
 
-/* ABI version of the loaded library (KW_ABI_VERSION it was built with). */
+/* ABI version of the loaded library (KW_ABI_VERSION it was built with); no
+ * paper counterpart.  Never fails. */
 int kw_abi_version(void);
 
-/* Fill *opt with defaults: KW_F64, tol 1e-10, maxiter 100000, seed_switch 1,
- * hist_stride 0, hist_max 0, use_graph 1, tune_cache NULL. */
+/* Fill *opt with defaults: KW_F64, tol 1e-10, maxiter 100000, seed_switch 1
+ * (Sec. 2.2.4), hist_stride 0, hist_max 0, use_graph 1, tune_cache NULL.  The
+ * tolerance is the per-shift criterion of Sec. 3.2.2.  Errors: none (a NULL
+ * opt is ignored). */
 void kw_default_options(kw_options* opt);
 
-/* Human-readable name of a status code (static string, never NULL). */
+/* No paper counterpart.  Human-readable name of a status code (static string, never NULL; unknown
+ * codes give "KW_UNKNOWN").  Errors: none. */
 const char* kw_status_string(kw_status s);
 
-/* Create a context on the current CUDA device.  cuda_stream is a cudaStream_t
- * (NULL = legacy default stream) on which all work is issued.  Errors:
+/* Create a context on the current CUDA device: the solver state of one
+ * shifted system family (Eq. 4-5), with no operator yet.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream) on which all work is issued; the
+ * options are copied (tune_cache included).  Errors:
  * KW_ERR_ARG (out or opt NULL, tol < 0, maxiter < 1, hist_stride < 0, bad
  * precision), KW_ERR_CUDA. */
 kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream);
 
-/* Release the context and every device buffer it owns.  NULL is ignored. */
+/* No paper counterpart.  Release the context and every device buffer it owns, after synchronising
+ * its stream.  Buffers the caller lent (kw_set_csr, outputs) are not freed.
+ * Errors: none (NULL is ignored). */
 void kw_destroy(kw_ctx* ctx);
 
-/* Copy the last error message (NUL-terminated, truncated to n) into buf. */
+/* No paper counterpart.  Copy the last error message (NUL-terminated, truncated to n) into buf.
+ * Errors: KW_ERR_ARG (ctx or buf NULL, n = 0). */
 kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
 
-/* Set the operator H (real symmetric, M x M) as a device CSR matrix:
+/* Set the operator H of Eq. 4 (real symmetric, M x M) as a device CSR matrix:
  * rowptr_dev int64 [m+1] (rowptr[0] = 0, nondecreasing, rowptr[m] = nnz),
  * col_dev int32 [nnz] in [0, m), val_dev float64 [nnz].  The pointers are
  * borrowed in KW_F64 mode (they must stay valid until the next kw_set_csr or
@@ -194,7 +203,8 @@ kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user);
 kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const int32_t* bonds_host,
                                const double* J_host, const double* h_host);
 
-/* Spin operator storage.  on = 0 (default): every product regenerates the
+/* Spin operator storage (the matrix-free product of Sec. 3.1 (i) for the
+ * Heisenberg-type Hamiltonians of Eq. 41).  on = 0 (default): every product regenerates the
  * exchanged words' rows from the combinatorial number system (4 + 4 bytes per
  * row: basis word and diagonal).  on = 1: the context also keeps an exchange
  * table of nbond * M int32 (the row of each bond's exchanged word, -1 for
@@ -233,10 +243,12 @@ kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c1
                    int64_t nleft, const double* left_dev, void* x_out_dev,
                    kw_c128* proj_out_host, kw_solve_info* info);
 
-/* kw_solve with every array in host memory: copies H (CSR as in kw_set_csr),
- * b and the left vectors to the device, solves, and copies x (if x_out_host is
- * not NULL; same layout as x_out_dev) and the projections back.  The device
- * copies are owned by the context and reused by later calls. */
+/* kw_solve (Eq. 4-5, Eqs. 23-26) with every array in host memory: copies H
+ * (CSR as in kw_set_csr), b and the left vectors to the device, solves, and
+ * copies x (if x_out_host is not NULL; same layout as x_out_dev) and the
+ * projections back.  The device copies are owned by the context and reused by
+ * later calls.  Errors: those of kw_set_csr and kw_solve, KW_ERR_ARG (NULL
+ * host arrays, m < 1, nshift < 1), KW_ERR_OOM. */
 kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_host,
                         const int32_t* col_host, const double* val_host, const double* b_host,
                         int64_t nshift, const kw_c128* z_host, int64_t nleft,
@@ -274,14 +286,17 @@ typedef struct {
     int elem;        /* KW_ELEM_C128, or KW_ELEM_C64 in the KW_C32V_F64S form */
 } kw_rci_io;
 
-/* Start a solve of (z_k I - H) x_k = b of size m (arguments as kw_solve) with
+/* Reverse communication (Sec. 3.1 (iii), Algorithm 1: the library's _init,
+ * _update, _getresidual and _finalize steps).  Start a solve of
+ * (z_k I - H) x_k = b of size m (arguments as kw_solve) with
  * the caller as the operator: any CSR matrix, callback or generated operator of
  * ctx is dropped.  *io receives the first vectors.  The solver of
  * kw_set_method is used (COCG by default).  Errors: those of kw_solve. */
 kw_status kw_rci_init(kw_ctx* ctx, int64_t m, const double* b_dev, int64_t nshift, const kw_c128* z_host,
                       int64_t nleft, const double* left_dev, void* x_out_dev, kw_rci_io* io);
 
-/* After the caller has written q = H r (and, for BiCG, qt = H^dagger rt) for
+/* The update step of Algorithm 1 (Sec. 3.1 (iii)).  After the caller has
+ * written q = H r (and, for BiCG, qt = H^dagger rt) for
  * the vectors of the last *io: finish the iteration; *done = 1 when every
  * shift has converged or the iteration cap or a breakdown was reached, else 0
  * with the next vectors in *io (their addresses change between iterations).
@@ -289,11 +304,16 @@ kw_status kw_rci_init(kw_ctx* ctx, int64_t m, const double* b_dev, int64_t nshif
  * applies by linearity.  Errors: KW_ERR_ARG (no kw_rci_init), KW_ERR_CUDA. */
 kw_status kw_rci_update(kw_ctx* ctx, int* done, kw_rci_io* io);
 
-/* Current residual estimate ||r_n||/|pi_n^k| of every shift (host, [nshift]). */
+/* Current residual estimate ||r_n||/|pi_n^k| of every shift (Sec. 3.2.2; host,
+ * [nshift]).  Errors: KW_ERR_ARG (no reverse-communication solve, NULL res),
+ * KW_ERR_CUDA. */
 kw_status kw_rci_get_residual(kw_ctx* ctx, double* res_host);
 
-/* End the solve: outputs and status as kw_solve returns them.  ctx then has no
- * operator until the next kw_set_csr, kw_set_matvec or generated operator. */
+/* End the solve: outputs and status as kw_solve returns them (x^(k) of
+ * Eq. 23-24 or the projections of Eq. 25-26).  ctx then has no operator until
+ * the next kw_set_csr, kw_set_matvec or generated operator.  Errors:
+ * KW_ERR_ARG (no reverse-communication solve), the solve's own status
+ * (KW_NOT_CONVERGED, KW_ERR_BREAKDOWN, KW_ERR_NONFINITE), KW_ERR_CUDA. */
 kw_status kw_rci_finalize(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* info);
 
 /* Continue the last kw_solve of ctx for up to more_iters further iterations
@@ -311,25 +331,29 @@ kw_status kw_rci_finalize(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* in
  * KW_ERR_ARG (more_iters < 1, nothing to resume), the kw_solve errors. */
 kw_status kw_resume(kw_ctx* ctx, int64_t more_iters, kw_c128* proj_out_host, kw_solve_info* info);
 
-/* Solve n independent problems (uneven sizes and shift counts) together.
- * Each instance runs the kw_solve iteration on its own stream and workspace,
- * owned by the context and reused by later calls; one CUDA graph holds a chunk
- * of iterations of every instance, and the host replays it until every
- * instance has stopped (instances that stop early return from their kernels at
- * the first instruction).  Results are those kw_solve gives for each instance
+/* Solve n independent problems (uneven sizes and shift counts; each one
+ * Eq. 4-5) together.  Each instance runs the kw_solve iteration on its own
+ * stream and workspace, owned by the context and reused by later calls; one
+ * CUDA graph holds a trip of iterations of every instance, repeated on the
+ * device by a WHILE node until every instance has stopped (use_graph 0: the
+ * host relaunches it per chunk); instances that stop early return from their
+ * kernels at the first instruction.  Results are those kw_solve gives for each instance
  * alone.  info: [n] or NULL.  Returns KW_OK if every instance converged, else
  * the first other status (per-instance status in info).  Errors: KW_ERR_ARG
  * (n < 1, NULL pointer, an instance's own argument errors), KW_ERR_CUDA. */
 kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_solve_info* info);
 
 /* Per-shift results of the last solve: the iteration at which shift k met the
- * tolerance (-1 if never) and its last residual estimate ||r_n||/|pi_n^k|.
- * Either pointer may be NULL.  Arrays have the last solve's nshift entries. */
+ * tolerance of Sec. 3.2.2 (-1 if never) and its last residual estimate
+ * ||r_n||/|pi_n^k| (Eq. 19).  Either pointer may be NULL.  Arrays have the
+ * last solve's nshift entries.  Errors: KW_ERR_ARG (no solve yet), KW_ERR_CUDA. */
 kw_status kw_get_shift_status(kw_ctx* ctx, int64_t* conv_iter_host, double* final_res_host);
 
-/* Residual history of the last solve: *n_rec records of nshift doubles,
- * record i taken after iteration (i+1)*hist_stride.  hist_host may be NULL to
- * query *n_rec; otherwise it must hold hist_max * nshift doubles. */
+/* Residual history of the last solve (the per-shift ||r_n||/|pi_n^k| of
+ * Sec. 3.2.2 over the iterations): *n_rec records of nshift doubles, record i
+ * taken after iteration (i+1)*hist_stride.  hist_host may be NULL to query
+ * *n_rec; otherwise it must hold hist_max * nshift doubles.  Before any solve
+ * *n_rec is 0.  Errors: KW_ERR_ARG (ctx or n_rec NULL), KW_ERR_CUDA. */
 kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec);
 
 /* ---------------------------------------------------------------------------
@@ -351,13 +375,15 @@ kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec
  * --------------------------------------------------------------------------- */
 #define KW_LOG_FIXED 7
 
-/* Record the log in the next solves of ctx (kw_solve, kw_solve_host), at most
+/* Krylov log for recalculation at new shifts (Sec. 3.3 (iv): the seed scalars
+ * and projections a run needs to replay Eqs. 20-22 and 25-26 without products).
+ * Record the log in the next solves of ctx (kw_solve, kw_solve_host), at most
  * max_iters rows (0 = off, the default).  The device log takes
  * max_iters * (KW_LOG_FIXED + nproj) * 16 bytes, allocated at the next solve.
  * Errors: KW_ERR_ARG (max_iters < 0). */
 kw_status kw_set_krylov_log(kw_ctx* ctx, int64_t max_iters);
 
-/* The log of the last solve.  *n_iter = rows recorded (fewer than *n_run, the
+/* The log of the last solve (Sec. 3.3 (iv)).  *n_iter = rows recorded (fewer than *n_run, the
  * solve's iteration count, when max_iters cut it short), *nproj = columns of
  * P, *thresh = the solve's absolute threshold tol*||b||_2.  log_host (NULL to
  * query sizes) receives n_iter rows of KW_LOG_FIXED + nproj values; w0_host
@@ -403,8 +429,11 @@ typedef struct {
     int64_t tune_hits;      /* picks taken from the persistent tuning cache (kw_options.tune_cache) */
 } kw_stats;
 
-/* Bracket the kernels of one iteration in every `every` with CUDA events on
- * the context stream (0 turns it off; the default).  Errors: KW_ERR_ARG. */
+/* Measurement only (no paper counterpart): bracket the kernels of one
+ * iteration in every `every` with CUDA events on the context stream (0 turns it
+ * off; the default).  While it is on, solves run the host-driven loop (events
+ * cannot sit inside the device loop); kw_get_stats reports the times.
+ * Errors: KW_ERR_ARG (ctx NULL, every < 0), KW_ERR_CUDA. */
 kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
 
 /* Select the solver of Table 1 for the next solves of ctx (kw_solve,
@@ -425,12 +454,13 @@ kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
  * Errors: KW_ERR_ARG (unknown method, btilde_dev with a method other than BiCG). */
 kw_status kw_set_method(kw_ctx* ctx, int method, const double* btilde_dev);
 
-/* Adjoint product q = H^dagger r for BiCG with a callback operator that is not
+/* Adjoint product q = H^dagger r (the A^dagger of Appendix B) for BiCG with a callback operator that is not
  * Hermitian (same calling rules as kw_matvec_fn; NULL: H is Hermitian).  A later
  * kw_set_matvec or kw_set_csr clears it.  Errors: KW_ERR_ARG (no callback set). */
 kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user);
 
-/* Schedule of an iteration.  on = 1 (the default): the shift scalars of
+/* Schedule of an iteration (the steps of Sec. 2.2: Eq. 16-17, then Eq. 20-26).
+ * on = 1 (the default): the shift scalars of
  * iteration n (and the full-mode x/p update) run on a second stream while the
  * product of iteration n+1 runs, since neither needs the other's results (a
  * seed switch reaches that product through the next three-term update, by
@@ -455,7 +485,8 @@ kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
  * few seconds (the context stays usable).  Errors: KW_ERR_ARG. */
 kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
 
-/* Configuration of the sparse product kernel.  lanes = threads per matrix
+/* Configuration of the sparse product kernel (the "q = H r" of Algorithm 1).
+ * lanes = threads per matrix
  * row of the CSR kernel (1, 2, 4, 8 or 16), or 32 = the SELL-32 layout (an
  * internal sliced-ELLPACK copy: rows sorted by length within windows of 1024
  * rows, 32 rows per slice, column-major inside a slice, one thread per row);
@@ -473,17 +504,21 @@ kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
  * used); 0 = FP64 values; -1 = choose by timing.  Errors: KW_ERR_ARG. */
 kw_status kw_set_spmv_config(kw_ctx* ctx, int lanes, int val_f32);
 
-/* The configuration the next solve will use (tunes first if needed). */
+/* The configuration the next solve will use (tunes first if needed; the layout
+ * of the product of Algorithm 1).  Errors: KW_ERR_ARG (a NULL pointer, no CSR
+ * operator set), KW_ERR_CUDA, KW_ERR_OOM (tuning copies). */
 kw_status kw_get_spmv_config(kw_ctx* ctx, int* lanes, int* val_f32);
 
-/* Statistics of the last kw_solve / kw_solve_host. */
+/* Statistics of the last kw_solve / kw_solve_host (measurement only; no paper
+ * counterpart).  Errors: KW_ERR_ARG (ctx or out NULL). */
 kw_status kw_get_stats(kw_ctx* ctx, kw_stats* out);
 
 /* One seed matrix-vector step (Alg. 1 "q = H r" combined with the seed shift,
  * and the first dot of Eq. 17): q = zs r - H r and t = r^T q (unconjugated),
  * with the context's operator and precision.  r_dev, q_dev: [m] complex in the
- * context precision (KW_DF64: the 4-float pair layout); t_host receives the
- * FP64 dot. */
+ * context precision (KW_DF64: the 4-float pair layout), not overlapping;
+ * t_host receives the FP64 dot.  Errors: KW_ERR_ARG (no operator, NULL
+ * pointer), KW_ERR_CALLBACK, KW_ERR_CUDA, KW_ERR_OOM. */
 kw_status kw_spmv_dot(kw_ctx* ctx, kw_c128 zs, const void* r_dev, void* q_dev, kw_c128* t_host);
 
 /* One parameter matrix H_t of H(theta) = sum_t theta_t H_t, as a device CSR
@@ -518,8 +553,9 @@ kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* 
  * memory is entirely owned by another allocator (for example a framework's
  * caching pool, or a fixed budget) and latency-critical loops that cannot pay
  * for the implicit synchronisation of cudaMalloc.  The paper has no
- * counterpart; it is the same seed step (q = zs r - H r, t = r^T q,
- * unconjugated) as kw_spmv_dot, in FP64, without a context.
+ * counterpart for the entry point; it is the same seed step (Algorithm 1
+ * "q = H r" with the seed shift, and the first dot of Eq. 17: q = zs r - H r,
+ * t = r^T q, unconjugated) as kw_spmv_dot, in FP64, without a context.
  *   m, nnz, rowptr_dev, col_dev, val_dev: the operator as in kw_set_csr.
  *   r_dev, q_dev: [m] kw_c128 device arrays (input r, output q).
  *   t_host: receives t.  cuda_stream: the stream to run on (NULL = default).
