@@ -112,8 +112,8 @@ int kw_abi_version(void);
  * opt is ignored). */
 void kw_default_options(kw_options* opt);
 
-/* No paper counterpart.  Human-readable name of a status code (static string, never NULL; unknown
- * codes give "KW_UNKNOWN").  Errors: none. */
+/* No paper counterpart.  Human-readable name of a status code (static string,
+ * never NULL; unknown codes give "KW_UNKNOWN").  Errors: none. */
 const char* kw_status_string(kw_status s);
 
 /* Create a context on the current CUDA device: the solver state of one
@@ -124,13 +124,13 @@ const char* kw_status_string(kw_status s);
  * precision), KW_ERR_CUDA. */
 kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream);
 
-/* No paper counterpart.  Release the context and every device buffer it owns, after synchronising
- * its stream.  Buffers the caller lent (kw_set_csr, outputs) are not freed.
- * Errors: none (NULL is ignored). */
+/* No paper counterpart.  Release the context and every device buffer it owns,
+ * after synchronising its stream.  Buffers the caller lent (kw_set_csr,
+ * outputs) are not freed. Errors: none (NULL is ignored). */
 void kw_destroy(kw_ctx* ctx);
 
-/* No paper counterpart.  Copy the last error message (NUL-terminated, truncated to n) into buf.
- * Errors: KW_ERR_ARG (ctx or buf NULL, n = 0). */
+/* No paper counterpart.  Copy the last error message (NUL-terminated,
+ * truncated to n) into buf. Errors: KW_ERR_ARG (ctx or buf NULL, n = 0). */
 kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
 
 /* Set the operator H of Eq. 4 (real symmetric, M x M) as a device CSR matrix:
@@ -454,9 +454,10 @@ kw_status kw_set_kernel_timing(kw_ctx* ctx, int64_t every);
  * Errors: KW_ERR_ARG (unknown method, btilde_dev with a method other than BiCG). */
 kw_status kw_set_method(kw_ctx* ctx, int method, const double* btilde_dev);
 
-/* Adjoint product q = H^dagger r (the A^dagger of Appendix B) for BiCG with a callback operator that is not
- * Hermitian (same calling rules as kw_matvec_fn; NULL: H is Hermitian).  A later
- * kw_set_matvec or kw_set_csr clears it.  Errors: KW_ERR_ARG (no callback set). */
+/* Adjoint product q = H^dagger r (the A^dagger of Appendix B) for BiCG with a
+ * callback operator that is not Hermitian (same calling rules as kw_matvec_fn;
+ * NULL: H is Hermitian).  A later kw_set_matvec or kw_set_csr clears it.
+ * Errors: KW_ERR_ARG (no callback set). */
 kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user);
 
 /* Schedule of an iteration (the steps of Sec. 2.2: Eq. 16-17, then Eq. 20-26).
