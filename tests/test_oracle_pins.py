@@ -56,6 +56,27 @@ def test_iterates_equal_galerkin(n, switch):
         assert np.linalg.norm(r.x[k] - xg) <= 1e-11 * np.linalg.norm(xg)
 
 
+@pytest.mark.parametrize("switch", [True, False])
+@pytest.mark.parametrize("n", [2, 5, 12])
+def test_galerkin_error_identity_of_the_spectrum(n, switch):
+    """COCG's error in b^T x: with G = (zI - H)^{-1} complex symmetric and the
+    iterate x_n in K_n with V^T r_n = 0, b^T G b - b^T x_n = x*^T r_n =
+    (G r_n)^T r_n = r_n^T G r_n, where r_n = b - (zI - H) x_n is the true
+    residual of the shift (Appendix A; Eq. 19 makes it the seed residual over
+    pi_n).  Checked against a dense inverse for every shift, with and without
+    seed switching."""
+    Hd, b = _random_symmetric(50, 4)
+    r = oc.shifted_cocg(Hd, b, Z5, tol=0.0, maxiter=n, full=True, seed_switch=switch)
+    assert r.iters == n
+    for k, zk in enumerate(Z5):
+        G = np.linalg.inv(zk * np.eye(b.size) - Hd)
+        x = r.x[k]
+        rn = b - (zk * x - Hd @ x)
+        lhs = b @ G @ b - b @ x
+        rhs = rn @ G @ rn
+        assert abs(lhs - rhs) <= 1e-9 * abs(lhs) + 1e-13 * abs(b @ G @ b), (k, lhs, rhs)
+
+
 @pytest.mark.parametrize("seed0", [0, 2, 4])
 def test_iterates_independent_of_initial_seed(seed0):
     Hd, b = _random_symmetric(30, 2)
