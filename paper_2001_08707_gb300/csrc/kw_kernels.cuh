@@ -1125,10 +1125,11 @@ struct ShiftArgs {
   long long log_max;
 };
 
-// One warp per block, LPS lanes per shift (LPS = 1 in full mode, else the
-// projection count rounded up to a power of two, at most 32): the lanes of a
-// shift compute its scalars redundantly and update one projection row each, so
-// the FP64 work spreads over many SMs.
+// One warp per block, LPS lanes per shift (the launcher picks 1 in full mode,
+// else the projection count rounded up to a power of two, at most 4): the lanes
+// of a shift compute its scalars redundantly and update every LPS-th projection
+// row, so the FP64 work spreads over many SMs without recomputing the scalars
+// on many lanes.
 template <int LPS>
 __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   if (st->done) return;
