@@ -36,6 +36,11 @@ extern "C" {
 #define KW_ABI_VERSION 2
 /* Largest number of projection rows (b plus left vectors) in projected mode. */
 #define KW_MAX_PROJ 32
+/* Largest operator dimension M and largest nnz any call accepts: 2^31 - 2^22.
+ * Row and entry counters on the device are 32-bit; a grid-stride step is at
+ * most 2^22, so no counter passes 2^31 - 1. */
+#define KW_MAX_ROWS 2143289344LL
+#define KW_MAX_NNZ 2143289344LL
 
 typedef struct kw_ctx kw_ctx;
 
@@ -141,7 +146,8 @@ kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n);
  * values (and, in KW_F64 mode, uses an FP32 copy only if every value is
  * exactly representable in FP32).  Symmetry is the caller's promise and is
  * not checked.  Errors:
- * KW_ERR_ARG (m < 1, nnz < 0, nnz >= 2^31, NULL pointer), KW_ERR_OOM. */
+ * KW_ERR_ARG (m < 1, m > KW_MAX_ROWS, nnz < 0, nnz > KW_MAX_NNZ, NULL pointer),
+ * KW_ERR_OOM. */
 kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev,
                      const int32_t* col_dev, const double* val_dev);
 
@@ -177,7 +183,7 @@ typedef int (*kw_matvec_fn)(void* user, const void* r_dev, void* q_dev, int64_t 
  * is exact by linearity).  kw_solve_batched and kw_bilinear take their own
  * matrices and ignore the callback; kw_solve_host sets its matrix as the
  * operator (as kw_set_csr does), which ends the callback.  Errors: KW_ERR_ARG
- * (m < 1, m >= 2^31, fn NULL). */
+ * (m < 1, m > KW_MAX_ROWS, fn NULL). */
 kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user);
 
 /* Most bonds and sites of a spin operator (kw_set_spin_operator). */
@@ -199,7 +205,7 @@ kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user);
  * diagonal (4 or 8 bytes per row) on the device; a product then reads only
  * these, r and q.  Ends any CSR matrix or callback.  Errors: KW_ERR_ARG
  * (1 <= nup < nsite <= KW_SPIN_MAX_SITES, 1 <= nbond <= KW_SPIN_MAX_BONDS, bad
- * bond, M >= 2^31, non-finite J or h), KW_ERR_OOM. */
+ * bond, M > KW_MAX_ROWS, non-finite J or h), KW_ERR_OOM. */
 kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const int32_t* bonds_host,
                                const double* J_host, const double* h_host);
 
@@ -219,7 +225,7 @@ kw_status kw_set_spin_table(kw_ctx* ctx, int on);
  * Sec. 4 with eps_i the disorder).  eps_dev float64 [nx ny nz] (device; the
  * context keeps its own copy in the form's precision).  Each extent must be at
  * least 3 (six distinct neighbours).  Ends any CSR matrix or callback.  Errors:
- * KW_ERR_ARG (extent < 3, nx ny nz >= 2^31, eps_dev NULL, hopping not finite),
+ * KW_ERR_ARG (extent < 3, nx ny nz > KW_MAX_ROWS, eps_dev NULL, hopping not finite),
  * KW_ERR_OOM. */
 kw_status kw_set_lattice3d(kw_ctx* ctx, int64_t nx, int64_t ny, int64_t nz, const double* eps_dev, double hopping);
 
@@ -496,7 +502,12 @@ kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
  * hoppings, spin-flip amplitudes): an internal copy holding int32 row offsets,
  * the off-diagonal columns only and the summed diagonal, so that
  * H r = d_i r_i + v * (sum of r over the row's off-diagonal columns); forcing
- * it on another operator fails with KW_ERR_ARG at the next solve;
+ * it on another operator fails with KW_ERR_ARG at the next solve; 96 = the
+ * same uniform layout stored as SELL-32: the off-diagonal columns of each slice
+ * of 32 consecutive rows (rows not reordered) slot-major, -1 past a row's end,
+ * one thread per row, so that a warp's index loads are contiguous (not built,
+ * and forcing it fails with KW_ERR_ARG, when the padding would exceed three
+ * times the columns);
  * 0 = choose by timing every candidate on the current operator at the next
  * solve, the default (operators with fewer than 2^20 non-zeros are not timed
  * and use 1).  val_f32 (KW_F64 mode only): 1 =
@@ -554,21 +565,24 @@ kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* 
  * memory is entirely owned by another allocator (for example a framework's
  * caching pool, or a fixed budget) and latency-critical loops that cannot pay
  * for the implicit synchronisation of cudaMalloc.  The paper has no
- * counterpart for the entry point; it is the same seed step (Algorithm 1
- * "q = H r" with the seed shift, and the first dot of Eq. 17: q = zs r - H r,
- * t = r^T q, unconjugated) as kw_spmv_dot, in FP64, without a context.
+ * counterpart for this entry point.  It computes q = zs r - H r and
+ * t = r^T q (unconjugated) in FP64, as kw_spmv_dot does in the KW_F64 form,
+ * without a context.
  *   m, nnz, rowptr_dev, col_dev, val_dev: the operator as in kw_set_csr.
  *   r_dev, q_dev: [m] kw_c128 device arrays (input r, output q).
  *   t_host: receives t.  cuda_stream: the stream to run on (NULL = default).
  * Nothing is allocated: the scratch is one static device array of about 66 KiB
  * that every GPU loading this library keeps until the process exits, and the
  * launch uses at most KW_NOALLOC_MAX_BLOCKS blocks (grid-stride loops cover any
- * m below 2^31).  The first call on a device resolves the array's device
- * address for that device (make that first call before any stream capture).
- * All calls share the array and each call leaves its last contents there, so
- * calls that overlap on the GPU (other streams, other threads) race: serialise
- * them.  Returns after synchronising cuda_stream.  Errors: KW_ERR_ARG (m < 1,
- * m or nnz >= 2^31, NULL pointer), KW_ERR_CUDA. */
+ * m up to KW_MAX_ROWS).  The first call on a device resolves the array's device
+ * address for that device and keeps it for the life of the process (make that
+ * first call before any stream capture).  The address belongs to the device's
+ * primary context: do not call this entry point again on a device after
+ * cudaDeviceReset or after its primary context was destroyed.  All calls share
+ * the array and each call leaves its last contents there, so calls that
+ * overlap on the GPU (other streams, other threads) race: serialise them.
+ * Returns after synchronising cuda_stream.  Errors: KW_ERR_ARG (m < 1,
+ * m > KW_MAX_ROWS, nnz > KW_MAX_NNZ, NULL pointer), KW_ERR_CUDA. */
 kw_status kw_spmv_dot_noalloc(int64_t m, int64_t nnz, const int64_t* rowptr_dev, const int32_t* col_dev,
                               const double* val_dev, kw_c128 zs, const kw_c128* r_dev, kw_c128* q_dev,
                               kw_c128* t_host, void* cuda_stream);

@@ -123,6 +123,8 @@ struct kw_ctx {
   bool sell_built = false;
   // uniform off-diagonal copy (built when the tuner tries it or it is forced)
   int u_state = 0;            // 0: not examined, 1: built, -1: off-diagonal values differ
+  DBuf u_sptr, u_scol;        // SELL-32 copy of the uniform layout
+  int us_state = 0;           // 0: not built, 1: built, -1: not applicable
   double u_v = 0.0;
   int u_kind = 0;             // diagonal/value storage for the context's form (kw::Work::u_kind)
   DBuf u_fm, u_dcount, u_scratch, u_rowptr, u_col, u_diag64, u_diag32, u_diagpair;
@@ -269,7 +271,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->hist, &ctx->list, &ctx->X, &ctx->P, &ctx->part, &ctx->part_k1, &ctx->st, &ctx->projx, &ctx->tdot,
                   &ctx->mv_r, &ctx->mv_q, &ctx->mv_r2, &ctx->mv_q2, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->sp_table, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
-                  &ctx->u_col, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
+                  &ctx->u_col, &ctx->u_sptr, &ctx->u_scol, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
                   &ctx->rc_flag, &ctx->tune_fp};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
@@ -305,9 +307,9 @@ kw_status kw_last_error(const kw_ctx* ctx, char* buf, size_t n) {
 kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_dev, const int32_t* col_dev,
                      const double* val_dev) {
   if (!ctx) return KW_ERR_ARG;
-  if (m < 1 || m > 0x7fffffffLL || nnz < 0 || nnz > 0x7fffffffLL || !rowptr_dev ||
+  if (m < 1 || m > KW_MAX_ROWS || nnz < 0 || nnz > KW_MAX_NNZ || !rowptr_dev ||
       (nnz > 0 && (!col_dev || !val_dev)))
-    return fail(ctx, KW_ERR_ARG, "kw_set_csr: need 1 <= m < 2^31, 0 <= nnz < 2^31 and non-NULL arrays");
+    return fail(ctx, KW_ERR_ARG, "kw_set_csr: need 1 <= m <= KW_MAX_ROWS, 0 <= nnz <= KW_MAX_NNZ and non-NULL arrays");
   ctx->mv_fn = nullptr;
   ctx->mv_user = nullptr;
   ctx->mv_fn_adj = nullptr;
@@ -323,6 +325,7 @@ kw_status kw_set_csr(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowptr_
   ctx->spmv_lanes = 0;   // re-tune for the new operator
   ctx->sell_built = false;
   ctx->u_state = 0;
+  ctx->us_state = 0;
   if (nnz > 0) {
     KW_CUDA(ctx->val32.ensure((size_t)nnz * sizeof(float)), "kw_set_csr: FP32 value copy");
     KW_CUDA(ctx->inexact.ensure(sizeof(unsigned long long)), "kw_set_csr: counter");
@@ -386,6 +389,7 @@ static void become_generated(kw_ctx* ctx, int op, int64_t m) {
   ctx->spmv_val_f32 = 0;
   ctx->sell_built = false;
   ctx->u_state = 0;
+  ctx->us_state = 0;
 }
 
 kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const int32_t* bonds_host,
@@ -397,7 +401,7 @@ kw_status kw_set_spin_operator(kw_ctx* ctx, int nsite, int nup, int nbond, const
                 KW_SPIN_MAX_SITES, KW_SPIN_MAX_BONDS);
   double M = 1.0;
   for (int k = 0; k < nup; ++k) M = M * (nsite - k) / (k + 1);
-  if (M >= 2147483647.0) return fail(ctx, KW_ERR_ARG, "kw_set_spin_operator: C(nsite, nup) >= 2^31");
+  if (M > (double)KW_MAX_ROWS) return fail(ctx, KW_ERR_ARG, "kw_set_spin_operator: C(nsite, nup) > KW_MAX_ROWS");
   const int64_t m = (int64_t)(M + 0.5);
   std::vector<int> bond(nbond);
   bool uniform = true, exact32 = true;
@@ -484,7 +488,7 @@ kw_status kw_set_spin_table(kw_ctx* ctx, int on) {
 
 kw_status kw_set_lattice3d(kw_ctx* ctx, int64_t nx, int64_t ny, int64_t nz, const double* eps_dev, double hopping) {
   if (!ctx) return KW_ERR_ARG;
-  if (nx < 3 || ny < 3 || nz < 3 || !eps_dev || !isfinite(hopping) || (double)nx * ny * nz >= 2147483647.0)
+  if (nx < 3 || ny < 3 || nz < 3 || !eps_dev || !isfinite(hopping) || (double)nx * ny * nz > (double)KW_MAX_ROWS)
     return fail(ctx, KW_ERR_ARG, "kw_set_lattice3d: need extents >= 3, nx ny nz < 2^31, eps and a finite hopping");
   const int64_t m = nx * ny * nz;
   KW_CUDA(ctx->g_diag64.ensure((size_t)m * 8), "operator allocation");
@@ -502,7 +506,7 @@ kw_status kw_set_lattice3d(kw_ctx* ctx, int64_t nx, int64_t ny, int64_t nz, cons
 
 kw_status kw_set_matvec(kw_ctx* ctx, int64_t m, kw_matvec_fn fn, void* user) {
   if (!ctx) return KW_ERR_ARG;
-  if (m < 1 || m > 0x7fffffffLL || !fn) return fail(ctx, KW_ERR_ARG, "kw_set_matvec: need 1 <= m < 2^31 and fn");
+  if (m < 1 || m > KW_MAX_ROWS || !fn) return fail(ctx, KW_ERR_ARG, "kw_set_matvec: need 1 <= m <= KW_MAX_ROWS and fn");
   ctx->mv_fn = fn;
   ctx->mv_user = user;
   ctx->mv_fn_adj = nullptr;
@@ -543,6 +547,10 @@ static void spmv_work(kw_ctx* ctx, kw::Work& w, int lanes, int val_f32) {
                     : (p == KW_DF64 ? (const void*)ctx->valpair.p : (const void*)ctx->val);
   w.spmv_lanes = lanes;
   if (lanes > kw::KW_SPMV_UNIFORM && ctx->u_state == 1) {
+    if (lanes == kw::KW_SPMV_UNIFORM_SELL && ctx->us_state == 1) {
+      w.u_sptr = (const int*)ctx->u_sptr.p;
+      w.u_scol = (const int*)ctx->u_scol.p;
+    }
     w.u_rowptr = (const int*)ctx->u_rowptr.p;
     w.u_col = (const int*)ctx->u_col.p;
     w.u_kind = ctx->u_kind;
@@ -662,7 +670,8 @@ static kw_status build_uniform(kw_ctx* ctx) {
   const int64_t noff = ctx->nnz;   // upper bound: the diagonal entries are dropped
   KW_CUDA(ctx->u_scratch.ensure((size_t)((m + 1023) / 1024) * 4), "uniform layout allocation");
   KW_CUDA(ctx->u_rowptr.ensure((size_t)(m + 1) * 4), "uniform layout allocation");
-  KW_CUDA(ctx->u_col.ensure((size_t)std::max<int64_t>(noff, 1) * 4), "uniform layout allocation");
+  // four entries of padding: K1 reads the columns as aligned groups of four
+  KW_CUDA(ctx->u_col.ensure((size_t)(noff + 4) * 4), "uniform layout allocation");
   KW_CUDA(ctx->u_diag64.ensure((size_t)m * 8), "uniform layout allocation");
   KW_CUDA(kw::launch_uniform_build(m, ctx->rowptr, ctx->col, ctx->val, (int*)ctx->u_dcount.p,
                                    (int*)ctx->u_scratch.p, (int*)ctx->u_rowptr.p, (int*)ctx->u_col.p,
@@ -691,6 +700,51 @@ static kw_status build_uniform(kw_ctx* ctx) {
   ctx->u_v = v;
   ctx->u_state = 1;
   return KW_OK;
+}
+
+// SELL-32 copy of the uniform layout: the off-diagonal columns of each slice of
+// 32 consecutive rows stored slot-major (slot k = each row's k-th column, -1
+// past its end), so that K1's index loads are coalesced.  Not built when the
+// padding would more than triple the column array (rows of very different
+// lengths in one slice) or the slots overflow 32-bit offsets.
+static kw_status build_uniform_sell(kw_ctx* ctx) {
+  if (ctx->us_state != 0) return KW_OK;
+  kw_status us = build_uniform(ctx);
+  if (us != KW_OK) return us;
+  if (ctx->u_state != 1) {
+    ctx->us_state = -1;
+    return KW_OK;
+  }
+  const int m = (int)ctx->m;
+  const int nslice = (m + 31) / 32;
+  KW_CUDA(ctx->u_sptr.ensure((size_t)(nslice + 1) * 4), "uniform SELL allocation");
+  KW_CUDA(ctx->u_fm.ensure(2 * sizeof(unsigned long long)), "uniform SELL allocation");
+  KW_CUDA(kw::launch_uniform_sell_count(m, (const int*)ctx->u_rowptr.p, (int*)ctx->u_sptr.p,
+                                        (unsigned long long*)ctx->u_fm.p, ctx->stream), "uniform SELL count");
+  unsigned long long total = 0;
+  int last = 0, noff = 0;
+  KW_CUDA(cudaMemcpyAsync(&total, ctx->u_fm.p, sizeof(total), cudaMemcpyDeviceToHost, ctx->stream), "uniform SELL");
+  KW_CUDA(cudaMemcpyAsync(&last, (const int*)ctx->u_sptr.p + (nslice - 1), sizeof(int), cudaMemcpyDeviceToHost,
+                          ctx->stream), "uniform SELL");
+  KW_CUDA(cudaMemcpyAsync(&noff, (const int*)ctx->u_rowptr.p + m, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+          "uniform SELL");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "uniform SELL sync");
+  if (total > 0x7fffffffULL || 32ULL * total > 3ULL * (unsigned long long)noff + 32ULL * (unsigned long long)nslice) {
+    ctx->us_state = -1;
+    return KW_OK;
+  }
+  KW_CUDA(ctx->u_scol.ensure((size_t)std::max<unsigned long long>(total, 1) * 32 * 4), "uniform SELL allocation");
+  KW_CUDA(kw::launch_uniform_sell_fill(m, (const int*)ctx->u_rowptr.p, (const int*)ctx->u_col.p,
+                                       (int*)ctx->u_sptr.p, (int*)ctx->u_scratch.p, last, (int*)ctx->u_scol.p,
+                                       ctx->stream), "uniform SELL fill");
+  ctx->us_state = 1;
+  return KW_OK;
+}
+
+static void release_uniform_sell(kw_ctx* ctx) {
+  ctx->u_scol.release();
+  ctx->u_sptr.release();
+  ctx->us_state = 0;
 }
 
 // kw_c128 staging vectors of the callback operator in the FP32-pair form.
@@ -799,6 +853,13 @@ static kw_status tune_spmv(kw_ctx* ctx) {
         ctx->spmv_lanes = 0;
         return fail(ctx, KW_ERR_ARG, "uniform off-diagonal layout requested, but the off-diagonal values differ");
       }
+      if (ctx->spmv_lanes == kw::KW_SPMV_UNIFORM_SELL) {
+        if ((us = build_uniform_sell(ctx)) != KW_OK) return us;
+        if (ctx->us_state != 1) {
+          ctx->spmv_lanes = 0;
+          return fail(ctx, KW_ERR_ARG, "uniform SELL-32 layout requested, but its padding would exceed 3x");
+        }
+      }
       ctx->spmv_val_f32 = ctx->u_kind == 1 ? 1 : 0;
       return KW_OK;
     }
@@ -818,13 +879,19 @@ static kw_status tune_spmv(kw_ctx* ctx) {
     int cl = 0, cv = 0;
     if (tune_cache_lookup(ctx->opt.tune_cache, key, &cl, &cv)) {
       const bool lanes_ok = (cl >= 1 && cl <= 16 && (cl & (cl - 1)) == 0) || cl == kw::KW_SPMV_SELL ||
-                            (cl > kw::KW_SPMV_UNIFORM && cl <= kw::KW_SPMV_UNIFORM + 16);
+                            (cl > kw::KW_SPMV_UNIFORM && cl <= kw::KW_SPMV_UNIFORM + 16 &&
+                             ((cl - kw::KW_SPMV_UNIFORM) & (cl - kw::KW_SPMV_UNIFORM - 1)) == 0) ||
+                            cl == kw::KW_SPMV_UNIFORM_SELL;
       const bool val_ok = cv == 0 || (cv == 1 && (p != KW_F64 || ctx->val32_exact));
       bool ok = lanes_ok && val_ok;
       if (ok && cl > kw::KW_SPMV_UNIFORM) {
         kw_status us = build_uniform(ctx);
         if (us != KW_OK) return us;
         ok = ctx->u_state == 1;   // the values may differ from the operator the pick was timed on
+        if (ok && cl == kw::KW_SPMV_UNIFORM_SELL) {
+          if ((us = build_uniform_sell(ctx)) != KW_OK) return us;
+          ok = ctx->us_state == 1;
+        }
       }
       if (ok && cl == kw::KW_SPMV_SELL) {
         kw_status bs = build_sell(ctx);
@@ -849,7 +916,7 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   KW_CUDA(cudaMemsetAsync(ctx->rA.p, 0, ctx->m * vs, ctx->stream), "tune memset");
   KW_CUDA(cudaMemsetAsync(ctx->st.p, 0, sizeof(kw::State), ctx->stream), "tune memset");
   const int lane_opts[] = {1, 2, 4, 8, 16, kw::KW_SPMV_SELL, kw::KW_SPMV_UNIFORM + 1, kw::KW_SPMV_UNIFORM + 2,
-                           kw::KW_SPMV_UNIFORM + 4, kw::KW_SPMV_UNIFORM + 8};
+                           kw::KW_SPMV_UNIFORM + 4, kw::KW_SPMV_UNIFORM + 8, kw::KW_SPMV_UNIFORM_SELL};
   // value storage candidates: only the FP64 form has a choice (FP64 or exact FP32 values)
   int vals[2] = {0, 1}, nvals = 1;
   if (p == KW_F64 && ctx->val32_exact) nvals = 2;
@@ -877,6 +944,10 @@ static kw_status tune_spmv(kw_ctx* ctx) {
         kw_status us = build_uniform(ctx);
         if (us != KW_OK) return us;
         if (ctx->u_state != 1) continue;
+        if (l == kw::KW_SPMV_UNIFORM_SELL) {
+          if ((us = build_uniform_sell(ctx)) != KW_OK) return us;
+          if (ctx->us_state != 1) continue;
+        }
       }
       kw::Work w;
       spmv_work(ctx, w, l, vals[vi]);
@@ -899,6 +970,7 @@ static kw_status tune_spmv(kw_ctx* ctx) {
   ctx->spmv_lanes = best_l;
   ctx->spmv_val_f32 = best_l == kw::KW_SPMV_SELL ? (p == KW_F64 ? 0 : best_v) : best_v;
   if (best_l > kw::KW_SPMV_UNIFORM) ctx->spmv_val_f32 = ctx->u_kind == 1 ? 1 : 0;
+  if (best_l != kw::KW_SPMV_UNIFORM_SELL && ctx->us_state == 1) release_uniform_sell(ctx);
   if (best_l != kw::KW_SPMV_SELL && ctx->sell_built) {   // not chosen: give the memory back
     ctx->sell_col.release();
     ctx->sell_val.release();
@@ -1339,7 +1411,7 @@ static void rci_io(kw_ctx* ctx, kw_rci_io* io) {
 kw_status kw_rci_init(kw_ctx* ctx, int64_t m, const double* b_dev, int64_t nshift, const kw_c128* z_host,
                       int64_t nleft, const double* left_dev, void* x_out_dev, kw_rci_io* io) {
   if (!ctx) return KW_ERR_ARG;
-  if (m < 1 || m > 0x7fffffffLL || !io) return fail(ctx, KW_ERR_ARG, "kw_rci_init: need 1 <= m < 2^31 and io");
+  if (m < 1 || m > KW_MAX_ROWS || !io) return fail(ctx, KW_ERR_ARG, "kw_rci_init: need 1 <= m <= KW_MAX_ROWS and io");
   // the caller is the operator from now on
   ctx->op = kw::OP_CALLBACK;
   ctx->m = m;
@@ -1353,6 +1425,7 @@ kw_status kw_rci_init(kw_ctx* ctx, int64_t m, const double* b_dev, int64_t nshif
   ctx->mv_user_adj = nullptr;
   ctx->spmv_lanes = 1;
   ctx->u_state = 0;
+  ctx->us_state = 0;
   ctx->sell_built = false;
   ctx->resumable = false;
   ctx->rci_active = true;
@@ -1694,10 +1767,10 @@ kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec
 kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms, int64_t nshift,
                       const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host) {
   if (!ctx) return KW_ERR_ARG;
-  if (m < 1 || m > 0x7fffffffLL || nterm < 1 || nshift < 1 || nshift > 0x7fffffffLL || !terms || !X_dev || !out_host)
+  if (m < 1 || m > KW_MAX_ROWS || nterm < 1 || nshift < 1 || nshift > 0x7fffffffLL || !terms || !X_dev || !out_host)
     return fail(ctx, KW_ERR_ARG, "kw_bilinear: invalid sizes or NULL pointer");
   for (int64_t t = 0; t < nterm; ++t)
-    if (!terms[t].rowptr_dev || terms[t].nnz < 0 || terms[t].nnz > 0x7fffffffLL ||
+    if (!terms[t].rowptr_dev || terms[t].nnz < 0 || terms[t].nnz > KW_MAX_NNZ ||
         (terms[t].nnz > 0 && (!terms[t].col_dev || !terms[t].val_dev)))
       return fail(ctx, KW_ERR_ARG, "kw_bilinear: term %lld is invalid", (long long)t);
   const int nblk = 2 * ctx->num_sms;
@@ -1878,7 +1951,8 @@ kw_status kw_set_spmv_config(kw_ctx* ctx, int lanes, int val_f32) {
   if (!ctx ||
       !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
         lanes == kw::KW_SPMV_SELL || lanes == kw::KW_SPMV_UNIFORM + 1 || lanes == kw::KW_SPMV_UNIFORM + 2 ||
-        lanes == kw::KW_SPMV_UNIFORM + 4 || lanes == kw::KW_SPMV_UNIFORM + 8 || lanes == kw::KW_SPMV_UNIFORM + 16) ||
+        lanes == kw::KW_SPMV_UNIFORM + 4 || lanes == kw::KW_SPMV_UNIFORM + 8 || lanes == kw::KW_SPMV_UNIFORM + 16 ||
+        lanes == kw::KW_SPMV_UNIFORM_SELL) ||
       val_f32 < -1 || val_f32 > 1)
     return KW_ERR_ARG;
   ctx->force_lanes = lanes;

@@ -92,6 +92,8 @@ struct Work {
   const void* u_diag;        // [m] diagonal: double, float (u_kind 1) or FP32 pair (u_kind 2)
   int u_kind;                // 0: FP64 diagonal and value, 1: FP32 (exact), 2: FP32 pair
   double u_v;                // the off-diagonal value
+  const int* u_sptr = nullptr;   // SELL-32 copy: [nslice + 1] first slot of each 32-row slice
+  const int* u_scol = nullptr;   // [slots * 32] slot-major off-diagonal columns, -1 = none
   int val_f32;       // matrix values stored as FP32 (always in C32 mode; in F64 mode when lossless)
   // seed vectors
   void* rA;          // two rotating residual buffers and q
@@ -193,8 +195,10 @@ cudaError_t launch_convert_f64_to_pair(const double* in, void* out, int64_t n, c
 // spmv_lanes value that selects the SELL-32 layout.
 constexpr int KW_SPMV_SELL = 32;
 // spmv_lanes = KW_SPMV_UNIFORM + G selects the uniform off-diagonal layout with
-// G lanes per row (G = 1, 2, 4, 8, 16).
+// G lanes per row (G = 1, 2, 4, 8, 16); KW_SPMV_UNIFORM_SELL selects the same
+// layout stored as SELL-32 (slot-major columns of 32-row slices, one lane per row).
 constexpr int KW_SPMV_UNIFORM = 64;
+constexpr int KW_SPMV_UNIFORM_SELL = KW_SPMV_UNIFORM + 32;
 // Uniform off-diagonal layout: find the first off-diagonal entry and count the
 // off-diagonal values that differ from it (bitwise) and the diagonal entries
 // per row (dcount [m]); then build u_rowptr, u_col and the FP64 diagonal.
@@ -203,6 +207,15 @@ cudaError_t launch_uniform_check(int m, const int64_t* rowptr, const int* col, c
                                  unsigned long long* first_and_mismatch, int* dcount, cudaStream_t s);
 cudaError_t launch_uniform_build(int m, const int64_t* rowptr, const int* col, const double* val, int* dcount,
                                  int* scratch, int* u_rowptr, int* u_col, double* diag, cudaStream_t s);
+// SELL-32 copy of the uniform layout (spmv_lanes == KW_SPMV_UNIFORM_SELL):
+// count: cnt[s] = slots of slice s (its longest row), *total = their sum;
+// fill: cnt becomes the slice offsets sptr [nslice + 1] (in place; scratch
+// [ceil(nslice / 1024)] ints; last_cnt = cnt[nslice - 1] before the call) and
+// scol [total * 32] receives the slot-major columns, -1 past a row's end.
+cudaError_t launch_uniform_sell_count(int m, const int* u_rowptr, int* cnt, unsigned long long* total,
+                                      cudaStream_t s);
+cudaError_t launch_uniform_sell_fill(int m, const int* u_rowptr, const int* u_col, int* sptr, int* scratch,
+                                     int last_cnt, int* scol, cudaStream_t s);
 cudaError_t launch_sell_order(int m, const int64_t* rowptr, int* perm, int* rlen, int* slen, cudaStream_t s);
 template <class RV>
 cudaError_t launch_sell_fill(int m, const int* perm, const int* rlen, const int64_t* sptr, const int64_t* rowptr,

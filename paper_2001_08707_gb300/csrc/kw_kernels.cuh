@@ -449,6 +449,67 @@ __device__ __forceinline__ bool k1_seed(const State* st, const SpmvMode& mode, V
   return true;
 }
 
+// K1 on the uniform off-diagonal layout stored as SELL-32: one warp per slice of
+// 32 consecutive rows (rows are not reordered), one lane per row; the slice's
+// off-diagonal columns are slot-major (slot k holds each row's k-th column, -1
+// past the row's end), so every index load of the warp reads 128 contiguous
+// bytes.  sptr[s] is the first slot of slice s (in units of 32 columns).  The
+// sum over a row's columns runs in the row's column order, as in k_spmv_u.
+template <int P, class DV>
+__global__ void __launch_bounds__(256)
+k_spmv_us(int m, int nslice, const int* __restrict__ sptr, const int* __restrict__ scol,
+          const DV* __restrict__ diag, DV uv, const typename PT<P>::V* __restrict__ r,
+          typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::A A;
+  V zsv;
+  if (!k1_seed(st, mode, zsv)) return;
+  const int lane = threadIdx.x & 31;
+  const int warp_global = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  A c_re = azero<A>(), c_im = azero<A>();
+  double t_re = 0, t_im = 0;
+  int in_chunk = 0;
+  for (int s = warp_global; s < nslice; s += nwarps) {   // uniform across the warp
+    const int row = s * 32 + lane;
+    const int k0 = sptr[s], k1 = sptr[s + 1];
+    const int* cp = scol + (size_t)k0 * 32 + lane;
+    V sum = vzero<V>();
+    int k = k0;
+    for (; k + 3 < k1; k += 4, cp += 128) {   // four slots: four coalesced index loads, four gathers
+      const int c0 = cp[0], c1 = cp[32], c2 = cp[64], c3 = cp[96];
+      const V x0 = c0 >= 0 ? r[c0] : vzero<V>(), x1 = c1 >= 0 ? r[c1] : vzero<V>();
+      const V x2 = c2 >= 0 ? r[c2] : vzero<V>(), x3 = c3 >= 0 ? r[c3] : vzero<V>();
+      vacc(sum, x0);
+      vacc(sum, x1);
+      vacc(sum, x2);
+      vacc(sum, x3);
+    }
+    for (; k < k1; ++k, cp += 32) {
+      const int c0 = cp[0];
+      if (c0 >= 0) vacc(sum, r[c0]);
+    }
+    sum = normalize(sum);
+    if (row < m) {
+      V ri = r[row];
+      V hr = vzero<V>();
+      mac(hr, diag[row], ri);
+      mac(hr, uv, sum);
+      hr = normalize(hr);
+      V qi = csub(cmul(zsv, ri), hr);         // z_s r - H r
+      q[row] = qi;
+      acc_cplx(c_re, c_im, cmul(mode.conj_dot ? vconj(ri) : ri, qi));   // r^T q (COCG) or r^dagger q (CG)
+    }
+    if (++in_chunk == PT<P>::CHUNK) {   // uniform across the warp
+      t_re += ato_double(warp_sum(anorm(c_re)));
+      t_im += ato_double(warp_sum(anorm(c_im)));
+      c_re = c_im = azero<A>();
+      in_chunk = 0;
+    }
+  }
+  spmv_finish<A>(c_re, c_im, t_re, t_im, lane, st, part, mode);
+}
+
 // Row of the word sw (row `row`) with the spins of bond (a, c), a < c, exchanged
 // (they differ): the combinatorial-number-system rank change described below.
 __device__ __forceinline__ int spin_exchange_row(unsigned sw, int row, int a, int c, const int* binom) {
@@ -1768,7 +1829,28 @@ static cudaError_t uniform_launch(Work& w, const void* r, void* q, SpmvMode mode
 }
 
 template <int P, class DV>
+static cudaError_t uniform_sell_launch(Work& w, const void* r, void* q, SpmvMode mode) {
+  typedef typename PT<P>::V V;
+  if (!w.u_sptr || !w.u_scol) return cudaErrorInvalidValue;
+  static int nblk_per_sm = 0;
+  const int nblk = resident_blocks(nblk_per_sm, k_spmv_us<P, DV>, 256, w.num_sms);
+  const int nslice = (int)((w.m + 31) / 32);
+  const int grid = std::max(1, std::min(nblk, (nslice + 7) / 8));   // one warp per slice, eight per block
+  DV uv;
+  if constexpr (std::is_same<DV, double>::value) uv = w.u_v;
+  else if constexpr (std::is_same<DV, float>::value) uv = (float)w.u_v;
+  else {
+    uv.hi = (float)w.u_v;
+    uv.lo = (float)(w.u_v - (double)uv.hi);
+  }
+  k_spmv_us<P, DV><<<grid, 256, 0, w.stream>>>((int)w.m, nslice, w.u_sptr, w.u_scol, (const DV*)w.u_diag, uv,
+                                               (const V*)r, (V*)q, w.st, w.part_k1, mode);
+  return cudaGetLastError();
+}
+
+template <int P, class DV>
 static cudaError_t uniform_dispatch_g(Work& w, const void* r, void* q, SpmvMode mode) {
+  if (w.spmv_lanes == KW_SPMV_UNIFORM_SELL) return uniform_sell_launch<P, DV>(w, r, q, mode);
   switch (w.spmv_lanes - KW_SPMV_UNIFORM) {
     case 1: return uniform_launch<P, DV, 1>(w, r, q, mode);
     case 2: return uniform_launch<P, DV, 2>(w, r, q, mode);

@@ -252,6 +252,77 @@ cudaError_t launch_uniform_build(int m, const int64_t* rowptr, const int* col, c
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- SELL-32 copy of the uniform layout
+// Slots of each 32-row slice (its longest row) into cnt, and their sum over
+// all slices (64-bit) into *total.
+static __global__ void __launch_bounds__(256) k_us_count(int m, int nslice, const int* __restrict__ u_rowptr,
+                                                         int* __restrict__ cnt, unsigned long long* total) {
+  unsigned long long acc = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslice; s += gridDim.x * blockDim.x) {
+    const int r0 = s * 32, r1 = min(r0 + 32, m);
+    int mx = 0;
+    for (int r = r0; r < r1; ++r) mx = max(mx, u_rowptr[r + 1] - u_rowptr[r]);
+    cnt[s] = mx;
+    acc += (unsigned long long)mx;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(total, acc);
+}
+
+// sptr[s] = block-local exclusive prefix + the prefix of the block totals;
+// sptr[nslice] = the total.
+static __global__ void k_us_ptr(int nslice, int* __restrict__ sptr, const int* __restrict__ tops, int last_cnt) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslice; s += gridDim.x * blockDim.x) {
+    const int v = sptr[s] + tops[s >> 10];
+    sptr[s] = v;
+    if (s == nslice - 1) sptr[nslice] = v + last_cnt;
+  }
+}
+
+// One warp per slice: slot k of lane t = the k-th off-diagonal column of row
+// 32 s + t, or -1 past the row's end (or past m).
+static __global__ void __launch_bounds__(256) k_us_fill(int m, int nslice, const int* __restrict__ u_rowptr,
+                                                        const int* __restrict__ u_col, const int* __restrict__ sptr,
+                                                        int* __restrict__ scol) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < nslice; s += nw) {
+    const int row = s * 32 + lane;
+    int beg = 0, len = 0;
+    if (row < m) {
+      beg = u_rowptr[row];
+      len = u_rowptr[row + 1] - beg;
+    }
+    const int k0 = sptr[s], n = sptr[s + 1] - k0;
+    for (int k = 0; k < n; ++k) scol[(size_t)(k0 + k) * 32 + lane] = k < len ? u_col[beg + k] : -1;
+  }
+}
+
+cudaError_t launch_uniform_sell_count(int m, const int* u_rowptr, int* cnt, unsigned long long* total,
+                                      cudaStream_t s) {
+  const int nslice = (m + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(total, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(1024, (nslice + 255) / 256));
+  k_us_count<<<grid, 256, 0, s>>>(m, nslice, u_rowptr, cnt, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_uniform_sell_fill(int m, const int* u_rowptr, const int* u_col, int* sptr, int* scratch,
+                                     int last_cnt, int* scol, cudaStream_t s) {
+  const int nslice = (m + 31) / 32;
+  const int nb = (nslice + 1023) / 1024;
+  k_scan_blocks<<<nb, 1024, 0, s>>>(nslice, sptr, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_scan_tops<<<1, 1024, 0, s>>>(nb, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_us_ptr<<<std::max(1, std::min(1024, (nslice + 255) / 256)), 256, 0, s>>>(nslice, sptr, scratch, last_cnt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_us_fill<<<std::max(1, std::min(4096, (nslice + 7) / 8)), 256, 0, s>>>(m, nslice, u_rowptr, u_col, sptr, scol);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- spin operator set-up
 static __global__ void k_binom(int* binom) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;

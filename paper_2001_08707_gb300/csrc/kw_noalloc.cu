@@ -62,7 +62,7 @@ kw_status setup(int dev, void** addr, int* grid_cap) {
 extern "C" kw_status kw_spmv_dot_noalloc(int64_t m, int64_t nnz, const int64_t* rowptr_dev, const int32_t* col_dev,
                                          const double* val_dev, kw_c128 zs, const kw_c128* r_dev, kw_c128* q_dev,
                                          kw_c128* t_host, void* cuda_stream) {
-  if (m < 1 || m > 0x7fffffffLL || nnz < 0 || nnz > 0x7fffffffLL) return KW_ERR_ARG;
+  if (m < 1 || m > KW_MAX_ROWS || nnz < 0 || nnz > KW_MAX_NNZ) return KW_ERR_ARG;
   if (!rowptr_dev || (nnz > 0 && (!col_dev || !val_dev)) || !r_dev || !q_dev || !t_host) return KW_ERR_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return KW_ERR_CUDA;

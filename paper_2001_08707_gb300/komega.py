@@ -142,14 +142,31 @@ def load_library(path: str = LIB_PATH):
 
 def spmv_dot_noalloc(rowptr, col, val, zs: complex, r, q, stream=None) -> complex:
     """kw_spmv_dot_noalloc: q = zs r - H r and t = r^T q in FP64 without any
-    device allocation by the library (all arguments are CUDA tensors: int64
-    rowptr, int32 col, float64 val, complex128 r and q)."""
+    device allocation by the library (all arguments are contiguous tensors on
+    the current CUDA device: int64 rowptr [m+1], int32 col and float64 val of
+    equal length, complex128 r and q [m]).  Every type, device and length is
+    checked here and a mismatch raises ValueError before the library is
+    called; the row offsets and column indices themselves are the caller's
+    promise (kw_set_csr's contract)."""
     import torch
 
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name, v, dt in (("rowptr", rowptr, torch.int64), ("col", col, torch.int32), ("val", val, torch.float64)):
+        if not isinstance(v, torch.Tensor) or v.device != dev or v.dtype != dt or not v.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt} tensor on {dev}")
+    if rowptr.dim() != 1 or rowptr.numel() < 2:
+        raise ValueError("rowptr must hold m + 1 >= 2 offsets")
+    if col.numel() != val.numel():
+        raise ValueError(f"col and val must have the same length, got {col.numel()} and {val.numel()}")
+    m = rowptr.numel() - 1
+    for name, v in (("r", r), ("q", q)):
+        if not isinstance(v, torch.Tensor) or v.device != dev or v.dtype != torch.complex128:
+            raise ValueError(f"{name} must be a complex128 tensor on {dev}")
+        check_vector_bytes(name, v, m, 16)
     lib = load_library()
     s = stream if stream is not None else torch.cuda.current_stream()
     t = kw_c128()
-    st = lib.kw_spmv_dot_noalloc(rowptr.numel() - 1, col.numel(), C.c_void_p(rowptr.data_ptr()),
+    st = lib.kw_spmv_dot_noalloc(m, col.numel(), C.c_void_p(rowptr.data_ptr()),
                                  C.c_void_p(col.data_ptr()), C.c_void_p(val.data_ptr()),
                                  kw_c128(zs.real, zs.imag), C.c_void_p(r.data_ptr()), C.c_void_p(q.data_ptr()),
                                  C.byref(t), C.c_void_p(s.cuda_stream))

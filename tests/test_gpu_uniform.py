@@ -4,12 +4,14 @@ Every off-diagonal entry of the lattice operators has one value (Anderson
 hopping -1, Heisenberg spin-flip J/2); the layout keeps only int32 offsets, the
 off-diagonal columns and the summed diagonal.  Checks, through the C ABI:
 
-* q = z_s r - H r and t = r^T q for G = 1..16 in all three forms on lattice
-  operators and on ragged uniform matrices (empty rows, rows without a
+* q = z_s r - H r and t = r^T q for G = 1..16, and for the layout's SELL-32
+  copy (config 96: slot-major columns of 32-row slices), in all three forms on
+  lattice operators and on ragged uniform matrices (empty rows, rows without a
   diagonal, a diagonal split into two entries, a diagonal-only matrix, 1x1),
   with the tolerances of the CSR kernel's parity test;
 * forcing the layout on an operator with two off-diagonal values fails with
-  KW_ERR_ARG;
+  KW_ERR_ARG, and so does forcing the SELL-32 copy where its padding would
+  exceed three times the columns;
 * converged solves on the layout agree with the oracle.
 """
 import numpy as np
@@ -90,7 +92,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("G", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("G", [1, 2, 4, 8, 16, 32])
 @pytest.mark.parametrize("prec", ["f64", "c32", "df64"])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_uniform_spmv_dot(case, prec, G):
@@ -142,9 +144,32 @@ def test_forcing_uniform_on_two_valued_operator_fails():
     assert ei.value.status == kw.KW_ERR_ARG
 
 
+def test_forcing_uniform_sell_with_heavy_padding_fails():
+    # a star: row 0 couples to the 63 others, so slice 0 needs 63 slots for 32 rows
+    m = 64
+    rows = [[(j, -1.0) for j in range(1, m)]] + [[(0, -1.0)] for _ in range(1, m)]
+    rowptr = np.zeros(m + 1, np.int64)
+    col, val = [], []
+    for i in range(m):
+        col += [c for c, _ in rows[i]]
+        val += [v for _, v in rows[i]]
+        rowptr[i + 1] = len(col)
+    H = w.CSR(m, rowptr, np.array(col, np.int32), np.array(val, np.float64))
+    s = kw.Solver("f64")
+    s.set_spmv_config(UNIFORM + 32, -1)
+    s.set_csr(H.rowptr, H.col, H.val)
+    with pytest.raises(kw.KomegaError) as ei:
+        s.solve(w.gaussian_unit(H.m, 1), [0.1 + 0.1j])
+    assert ei.value.status == kw.KW_ERR_ARG
+    s.set_spmv_config(UNIFORM + 1, -1)          # the row-per-thread form of the layout still works
+    r = s.solve(w.gaussian_unit(H.m, 1), [0.1 + 0.1j])
+    assert r.status == "KW_OK"
+
+
+@pytest.mark.parametrize("layout", [UNIFORM + 1, UNIFORM + 32])
 @pytest.mark.parametrize("prec", ["f64", "df64"])
 @pytest.mark.parametrize("case", ["anderson_L10", "heisenberg_N12"])
-def test_uniform_converged_solve_matches_oracle(case, prec):
+def test_uniform_converged_solve_matches_oracle(case, prec, layout):
     H = CASES[case]()
     Hs = H.to_scipy()
     b = w.gaussian_unit(H.m, 21)
@@ -152,7 +177,7 @@ def test_uniform_converged_solve_matches_oracle(case, prec):
     lo, hi = w.chain_bounds(H) if case.startswith("heis") else (-8.0, 8.0)
     z = w.shiftk_grid(lo, hi, 48, 0.05)
     s = kw.Solver(prec, tol=1e-10, maxiter=20000)
-    s.set_spmv_config(UNIFORM + 1, -1)
+    s.set_spmv_config(layout, -1)
     s.set_csr(H.rowptr, H.col, H.val)
     r = s.solve(b, z, left=left)
     ro = oc.shifted_cocg(Hs, b, z, left=left, tol=1e-10, full=False)

@@ -52,3 +52,20 @@ def test_descent_direction_lowers_loss():
     _, loss2, _, _ = oa.spectrum_and_gradient(terms, j.theta - 1e-3 * grad / np.linalg.norm(grad), b, z, target,
                                               tol=1e-13)
     assert loss2 < loss
+
+
+def test_assemble_matches_the_generators():
+    """oracle.adjoint.assemble against two builds that share none of its code:
+    the generator's own COO assembly of H(theta), and, for theta = (1, 0, 0, ...),
+    the nearest-neighbour Heisenberg chain built bond by bond (Eq. 41)."""
+    j = w.j1j2_chain(8, 1.0, 0.4, 0.2, seed=3)
+    terms = [t.to_scipy() for t in j.terms]
+    A = oa.assemble(terms, j.theta).toarray()
+    B = j.assemble().to_scipy().toarray()
+    np.testing.assert_allclose(A, B, rtol=0, atol=1e-15)
+    th = np.zeros_like(j.theta)
+    th[0] = 1.0
+    C = oa.assemble(terms, th).toarray()
+    np.testing.assert_allclose(C, w.heisenberg_chain(8).to_scipy().toarray(), rtol=0, atol=1e-15)
+    # every term enters: dropping the last field term changes the matrix
+    assert np.abs(oa.assemble(terms[:-1], j.theta[:-1]).toarray() - A).max() > 1e-3

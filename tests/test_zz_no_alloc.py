@@ -45,6 +45,13 @@ def test_noalloc_matches_allocating_entry_point_twice(case):
         qr = q_ref.cpu().numpy()
         np.testing.assert_allclose(q.cpu().numpy(), qr, rtol=0, atol=1e-13 * np.abs(qr).max())
         assert abs(t - t_ref) <= 1e-12 * np.sum(np.abs(r.cpu().numpy() * qr)), (call, t, t_ref)
+        # and against the product formed on the host from the CSR arrays (scipy)
+        rh = r.cpu().numpy()
+        q_host = zs * rh - H.to_scipy() @ rh
+        scale = np.abs(zs) * np.abs(rh) + abs(H.to_scipy()) @ np.abs(rh)
+        np.testing.assert_array_less(np.abs(q.cpu().numpy() - q_host), 1e-14 * scale.max() + 1e-300)
+        t_host = np.sum(rh * q_host)
+        assert abs(t - t_host) <= 1e-13 * np.sum(np.abs(rh) * scale), (call, t, t_host)
 
 
 def test_noalloc_rejects_bad_sizes():
@@ -65,3 +72,28 @@ def test_noalloc_rejects_bad_sizes():
     r.fill_(1.0)
     assert kw.spmv_dot_noalloc(rp, cl, vl, 2.0 + 0j, r, q) == 8.0
     assert torch.all(q == 2.0)
+
+
+def test_noalloc_binding_rejects_mismatched_tensors():
+    """The binding checks types, devices and lengths before the library sees a
+    bare pointer: a short q, an int32 rowptr, val and col of different lengths
+    or a complex64 r raise ValueError on the host."""
+    H = w.anderson_3d(4, 2.0, seed=5)
+    rp = torch.as_tensor(H.rowptr, device="cuda")
+    cl = torch.as_tensor(H.col, device="cuda")
+    vl = torch.as_tensor(H.val, device="cuda")
+    r = torch.ones(H.m, dtype=torch.complex128, device="cuda")
+    q = torch.empty_like(r)
+    with pytest.raises(ValueError):
+        kw.spmv_dot_noalloc(rp, cl, vl, 1j, r, q[:-1])
+    with pytest.raises(ValueError):
+        kw.spmv_dot_noalloc(rp.to(torch.int32), cl, vl, 1j, r, q)
+    with pytest.raises(ValueError):
+        kw.spmv_dot_noalloc(rp, cl, vl[:-1], 1j, r, q)
+    with pytest.raises(ValueError):
+        kw.spmv_dot_noalloc(rp, cl, vl, 1j, r.to(torch.complex64), q)
+    with pytest.raises(ValueError):
+        kw.spmv_dot_noalloc(rp, cl, vl, 1j, r.cpu(), q)
+    # the well-formed call still works after the refusals
+    kw.spmv_dot_noalloc(rp, cl, vl, 1j, r, q)
+    np.testing.assert_allclose(q.cpu().numpy(), 1j - H.to_scipy() @ np.ones(H.m), atol=1e-14)
