@@ -492,6 +492,22 @@ kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
  * few seconds (the context stays usable).  Errors: KW_ERR_ARG. */
 kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
 
+/* Storage of the shifted vectors in full mode (Eq. 23-24; the K*M-sized part of
+ * the state, Sec. 2.2.3).  fp32 = 1: x^(k) and p^(k) are stored and updated as
+ * complex FP32 (8 bytes per element) in the KW_F64 and KW_DF64 forms, while
+ * the seed vectors, the seed and shift scalars and the convergence test keep
+ * the form's precision; r_{n+1} enters the update rounded to FP32 and the
+ * scalars alpha^k, beta^k, 1/pi^k as their FP32 roundings.  The full-mode
+ * x_out buffer is then [nshift][m] complex FP32 ({float re, im}), and proj_out
+ * (b^T x_k and a_l^T x_k) comes from the projected recurrences of Eq. 25-26,
+ * which run in the same solve (FP64 y/u, P r_{n+1} formed by the seed update
+ * in the form's precision), not from the stored x.  Errors in x/p never feed
+ * back into the seed recurrence, so the iteration is the form's; x carries
+ * FP32 storage error.  fp32 = 0 (default): x/p in the form's vector type.  No
+ * effect in KW_C32V_F64S (already FP32) or in projected mode.  Applies from
+ * the next solve (kw_solve_batched instances included).  Errors: KW_ERR_ARG. */
+kw_status kw_set_shift_storage(kw_ctx* ctx, int fp32);
+
 /* Configuration of the sparse product kernel (the "q = H r" of Algorithm 1).
  * lanes = threads per matrix
  * row of the CSR kernel (1, 2, 4, 8 or 16), or 32 = the SELL-32 layout (an
@@ -556,6 +572,15 @@ typedef struct {
  * KW_ERR_ARG (sizes, NULL pointers), KW_ERR_OOM, KW_ERR_CUDA. */
 kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms_host, int64_t nshift,
                       const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host);
+
+/* kw_bilinear for complex FP32 solution vectors (full-mode x from the
+ * KW_C32V_F64S form or from FP32 shift storage, kw_set_shift_storage): X_dev,
+ * Y_dev are [nshift][m] {float re, im} device arrays (Y_dev NULL means Y = X),
+ * widened to FP64 on load; the sums and out_host are FP64 as in kw_bilinear
+ * (the same bilinear forms y_k^T H_t x_k of Eq. 2's derivative).  Errors: as
+ * kw_bilinear. */
+kw_status kw_bilinear_c64(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms_host, int64_t nshift,
+                          const void* X_dev, const void* Y_dev, kw_c128* out_host);
 
 /* Most thread blocks kw_spmv_dot_noalloc launches; its static scratch holds
  * one FP64 complex partial per block (64 KiB) plus a counter and the result. */

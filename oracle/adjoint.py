@@ -43,3 +43,20 @@ def spectrum_and_gradient(terms, theta, b, z, target, tol=1e-12, maxiter=100000)
         dA[:, m] = -np.imag(np.sum(X * HX, axis=1)) / np.pi
     res = A - target
     return A, 0.5 * float(res @ res), dA.T @ res, dA
+
+
+def green_and_gradient(terms, theta, a, b, z, tol=1e-12, maxiter=100000):
+    """G_ab(z_k) = a^T G(z_k) b for every shift and its parameter derivative
+    dG_ab/dtheta_m = y_k^T H_m x_k with x_k = G(z_k) b and y_k = G(z_k) a (Eq. 2:
+    dG/dtheta_m = G H_m G, and a^T G = (G^T a)^T = (G a)^T for complex symmetric
+    G).  Returns (G_ab [K], dG [K, nterm]); a is b gives the single-solve case."""
+    H = assemble(terms, theta)
+    rx = shifted_cocg(H, b, z, tol=tol, full=True, maxiter=maxiter)
+    X = rx.x
+    Y = X if a is b else shifted_cocg(H, a, z, tol=tol, full=True, maxiter=maxiter).x
+    G = np.sum(X * a[None, :], axis=1)                 # a^T x_k, unconjugated
+    dG = np.empty((z.size, len(terms)), dtype=np.complex128)
+    for m, Hm in enumerate(terms):
+        HX = (Hm @ X.T).T
+        dG[:, m] = np.sum(Y * HX, axis=1)
+    return G, dG

@@ -146,6 +146,7 @@ struct kw_ctx {
   DBuf part_k1;   // K1's block partials (K1 overlaps K3, which uses part)
   int overlap = 1;
   int bulk = -1;  // kw_set_bulk_copy (-1: auto)
+  int xp32 = 0;   // kw_set_shift_storage: full-mode x/p as complex FP32
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -991,7 +992,10 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.K = (int)K;
   w.full = x_out_dev != nullptr;
   w.nout = (int)nleft + 1;
-  w.nproj = w.full ? 0 : (int)nleft + 1;
+  // FP32 shift storage (full mode, FP64 and FP32-pair forms): the projections come from the
+  // projected recurrences run beside the x/p update, so K2 forms P r_{n+1} in full mode too
+  w.xp32 = (w.full && ctx->xp32 && ctx->opt.prec != KW_C32V_F64S) ? 1 : 0;
+  w.nproj = (w.full && !w.xp32) ? 0 : (int)nleft + 1;
   w.tol = ctx->opt.tol;
   w.proj_ld = (m + kw::KW_PROJ_ALIGN - 1) / kw::KW_PROJ_ALIGN * kw::KW_PROJ_ALIGN;
   w.bulk = ctx->bulk;
@@ -1025,7 +1029,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->w0, (size_t)KW_MAX_PROJ * 16},
       {&ctx->hist, std::max<size_t>((size_t)nrecmax * Ks, 1) * 8},
       {&ctx->list, Ks * 4},
-      {&ctx->P, w.full ? Ks * Ms * vs : 16},
+      {&ctx->P, w.full ? Ks * Ms * (w.xp32 ? 8 : vs) : 16},
       {&ctx->part, part_d * 8},
       {&ctx->part_k1, part_d * 8},
       {&ctx->st, sizeof(kw::State)},
@@ -1333,7 +1337,7 @@ static kw_status run_iterations(kw_ctx* ctx, int64_t start = 0) {
 static kw_status solve_end(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* info) {
   kw::Work& w = ctx->work;
   const int64_t nshift = ctx->work_K;
-  if (w.full && w.prec == kw::PREC_DF) {   // FP32-pair x is converted to FP64 in place (the caller's buffer holds kw_c128)
+  if (w.full && w.prec == kw::PREC_DF && !w.xp32) {   // FP32-pair x is converted to FP64 in place (the caller's buffer holds kw_c128)
     KW_CUDA(kw::launch_finish_x<kw::PREC_DF>(w), "finish x");
   }
   KW_CUDA(cudaMemcpyAsync(ctx->st_host, w.st, sizeof(kw::State), cudaMemcpyDeviceToHost, ctx->stream), "read state");
@@ -1347,7 +1351,7 @@ static kw_status solve_end(kw_ctx* ctx, kw_c128* proj_out_host, kw_solve_info* i
   ctx->last_log_np = w.nproj;
   ctx->last_thresh = st.thresh;
   if (proj_out_host) {
-    if (w.full) {
+    if (w.full && !w.xp32) {
       cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_project_x<kw::PREC_C32>(w, (double2*)ctx->projx.p)
                       : w.prec == kw::PREC_DF ? kw::launch_project_x<kw::PREC_DF>(w, (double2*)ctx->projx.p)
                                               : kw::launch_project_x<kw::PREC_F64>(w, (double2*)ctx->projx.p);
@@ -1503,7 +1507,7 @@ kw_status kw_resume(kw_ctx* ctx, int64_t more_iters, kw_c128* proj_out_host, kw_
   ctx->resumable = false;
   ctx->run_maxiter = it + more_iters;
   memset(&ctx->stats, 0, sizeof(ctx->stats));
-  if (w.full && w.prec == kw::PREC_DF) {   // x was handed out as kw_c128: back to FP32 pairs
+  if (w.full && w.prec == kw::PREC_DF && !w.xp32) {   // x was handed out as kw_c128: back to FP32 pairs
     KW_CUDA(kw::launch_unfinish_x<kw::PREC_DF>(w), "kw_resume: x to pairs");
   }
   // restart the device loop: new cap, stop flag cleared, K1 counter reset
@@ -1575,6 +1579,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     c->btilde = nullptr;
     c->overlap = ctx->overlap;
     c->bulk = ctx->bulk;
+    c->xp32 = ctx->xp32;
     if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
     c->run_maxiter = c->opt.maxiter;
     KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
@@ -1719,7 +1724,8 @@ kw_status kw_solve_host(kw_ctx* ctx, int64_t m, int64_t nnz, const int64_t* rowp
   if (m < 1 || nnz < 0 || !rowptr_host || (nnz > 0 && (!col_host || !val_host)) || !b_host || nshift < 1 ||
       nleft < 0 || (nleft > 0 && !left_host))
     return fail(ctx, KW_ERR_ARG, "kw_solve_host: invalid sizes or NULL host arrays");
-  const size_t vs = vec_bytes(ctx->opt.prec);
+  // x element: complex FP32 under FP32 shift storage (or in the FP32 form), else 16 bytes
+  const size_t vs = (ctx->xp32 && ctx->opt.prec != KW_C32V_F64S) ? 8 : vec_bytes(ctx->opt.prec);
   KW_CUDA(ctx->h_rowptr.ensure((m + 1) * 8), "alloc rowptr");
   KW_CUDA(ctx->h_col.ensure(std::max<int64_t>(nnz, 1) * 4), "alloc col");
   KW_CUDA(ctx->h_val.ensure(std::max<int64_t>(nnz, 1) * 8), "alloc val");
@@ -1764,30 +1770,39 @@ kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec
   return KW_OK;
 }
 
-kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms, int64_t nshift,
-                      const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host) {
+static kw_status bilinear(kw_ctx* ctx, const char* name, int64_t m, int64_t nterm, const kw_csr_term* terms,
+                          int64_t nshift, const void* X_dev, const void* Y_dev, int x32, kw_c128* out_host) {
   if (!ctx) return KW_ERR_ARG;
   if (m < 1 || m > KW_MAX_ROWS || nterm < 1 || nshift < 1 || nshift > 0x7fffffffLL || !terms || !X_dev || !out_host)
-    return fail(ctx, KW_ERR_ARG, "kw_bilinear: invalid sizes or NULL pointer");
+    return fail(ctx, KW_ERR_ARG, "%s: invalid sizes or NULL pointer", name);
   for (int64_t t = 0; t < nterm; ++t)
     if (!terms[t].rowptr_dev || terms[t].nnz < 0 || terms[t].nnz > KW_MAX_NNZ ||
         (terms[t].nnz > 0 && (!terms[t].col_dev || !terms[t].val_dev)))
-      return fail(ctx, KW_ERR_ARG, "kw_bilinear: term %lld is invalid", (long long)t);
+      return fail(ctx, KW_ERR_ARG, "%s: term %lld is invalid", name, (long long)t);
   const int nblk = 2 * ctx->num_sms;
   const int64_t ntile = (nshift + kw::kBilinearTile - 1) / kw::kBilinearTile;
   KW_CUDA(ctx->bil_part.ensure((size_t)ntile * nblk * kw::kBilinearTile * 16), "kw_bilinear: scratch");
   KW_CUDA(ctx->bil_out.ensure((size_t)nshift * nterm * 16), "kw_bilinear: result");
-  const double2* X = (const double2*)X_dev;
-  const double2* Y = Y_dev ? (const double2*)Y_dev : X;
+  const void* Y = Y_dev ? Y_dev : X_dev;
   for (int64_t t = 0; t < nterm; ++t)
-    KW_CUDA(kw::launch_bilinear((int)m, (int)nshift, terms[t].rowptr_dev, terms[t].col_dev, terms[t].val_dev, X, Y,
-                                nblk, (double2*)ctx->bil_part.p, (int)t, (int)nterm, (double2*)ctx->bil_out.p,
-                                ctx->stream),
+    KW_CUDA(kw::launch_bilinear((int)m, (int)nshift, terms[t].rowptr_dev, terms[t].col_dev, terms[t].val_dev, X_dev,
+                                Y, x32, nblk, (double2*)ctx->bil_part.p, (int)t, (int)nterm,
+                                (double2*)ctx->bil_out.p, ctx->stream),
             "kw_bilinear launch");
   KW_CUDA(cudaMemcpyAsync(out_host, ctx->bil_out.p, (size_t)nshift * nterm * 16, cudaMemcpyDeviceToHost, ctx->stream),
           "kw_bilinear read");
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_bilinear sync");
   return KW_OK;
+}
+
+kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms, int64_t nshift,
+                      const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host) {
+  return bilinear(ctx, "kw_bilinear", m, nterm, terms, nshift, X_dev, Y_dev, 0, out_host);
+}
+
+kw_status kw_bilinear_c64(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms, int64_t nshift,
+                          const void* X_dev, const void* Y_dev, kw_c128* out_host) {
+  return bilinear(ctx, "kw_bilinear_c64", m, nterm, terms, nshift, X_dev, Y_dev, 1, out_host);
 }
 
 kw_status kw_set_krylov_log(kw_ctx* ctx, int64_t max_iters) {
@@ -1928,6 +1943,13 @@ kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user) {
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return KW_ERR_ARG;
   ctx->overlap = on;
+  return KW_OK;
+}
+
+kw_status kw_set_shift_storage(kw_ctx* ctx, int fp32) {
+  if (!ctx || (fp32 != 0 && fp32 != 1)) return KW_ERR_ARG;
+  ctx->xp32 = fp32;
+  ctx->resumable = false;   // a stopped solve keeps its own storage
   return KW_OK;
 }
 

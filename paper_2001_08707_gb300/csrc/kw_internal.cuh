@@ -121,6 +121,8 @@ struct Work {
   int* list;
   void* X;           // full mode [K][m]
   void* P;           // full mode [K][m]
+  int xp32 = 0;      // full mode: X and P stored as complex FP32 (float2) whatever the form; the
+                     // projections then come from the projected recurrences (nproj = nout)
   // operator kind: CSR arrays (spmv_lanes picks the layout), callback, or generated on the fly
   int op = 0;             // OP_CSR, OP_CALLBACK, OP_SPIN, OP_LATTICE
   // spin operator (kw_set_spin_operator); diagonal in u_diag/u_kind, uniform J/2 in u_v
@@ -246,9 +248,10 @@ cudaError_t launch_loop_cond(const int* count, int target, unsigned* loop, cudaG
 
 // Adjoint bilinear forms (kw_bilinear): shifts per tile and the launcher.
 constexpr int kBilinearTile = 8;
-cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,
-                            const double2* X, const double2* Y, int nblk, double2* part, int term, int nterm,
-                            double2* out, cudaStream_t s);
+// X, Y: [K][m] kw_c128 (x32 = 0) or complex FP32 (x32 = 1).
+cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val, const void* X,
+                            const void* Y, int x32, int nblk, double2* part, int term, int nterm, double2* out,
+                            cudaStream_t s);
 
 // Recalculation at new shifts (kw_recalc): threads per block, log rows per
 // shared-memory chunk, and the launcher (flag: set to 1 on breakdown).

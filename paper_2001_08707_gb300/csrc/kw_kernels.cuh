@@ -1233,16 +1233,15 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
       const double2 ak = cmul(ratio, alpha);          // Eq. 21
       const double2 bk = cmul(cmul(ratio, ratio), beta);  // Eq. 22
       if (sub == 0) a.coef[3 * k + 2] = ipn;       // read by the seed switch and by K4
-      if (a.full) {
-        if (sub == 0) {
-          a.coef[3 * k + 0] = ak;
-          a.coef[3 * k + 1] = bk;
-          a.coef[3 * k + 2] = ipn;
-          a.coef_pair[3 * k + 0] = pair_of(ak);
-          a.coef_pair[3 * k + 1] = pair_of(bk);
-          a.coef_pair[3 * k + 2] = pair_of(ipn);
-        }
-      } else {
+      if (a.full && sub == 0) {
+        a.coef[3 * k + 0] = ak;
+        a.coef[3 * k + 1] = bk;
+        a.coef[3 * k + 2] = ipn;
+        a.coef_pair[3 * k + 0] = pair_of(ak);
+        a.coef_pair[3 * k + 1] = pair_of(bk);
+        a.coef_pair[3 * k + 2] = pair_of(ipn);
+      }
+      {   // projected mode, and full mode with FP32 shift storage: a.np > 0
         for (int l = sub; l < a.np; l += LPS) {       // Eq. 25-26
           const size_t o = (size_t)k * a.np + l;
           const double2 u = a.U[o], y = a.Y[o], wl = a.w[l];
@@ -1472,12 +1471,24 @@ __global__ void __launch_bounds__(kRecalcThreads)
 }
 
 // ================================================================ K4: fused x/p update
-template <int P, int TS>
+// The shifted vectors' element type: the form's vector type, or complex FP32
+// when the shift storage is FP32 (XP32); r_{n+1} is then rounded to FP32 once
+// per element (the leading part of an FP32 pair is its FP32 rounding) and the
+// update runs in FP32 with the scalars' leading parts.
+template <int P, bool XP32> struct XT { typedef typename PT<P>::V V; };
+template <int P> struct XT<P, true> { typedef float2 V; };
+__device__ __forceinline__ double2 to_x(double2 v, double2*) { return v; }
+__device__ __forceinline__ float2 to_x(float2 v, float2*) { return v; }
+__device__ __forceinline__ dfc to_x(dfc v, dfc*) { return v; }
+__device__ __forceinline__ float2 to_x(dfc v, float2*) { return make_float2(v.re.hi, v.im.hi); }
+__device__ __forceinline__ float2 to_x(double2 v, float2*) { return make_float2((float)v.x, (float)v.y); }
+
+template <int P, int TS, bool XP32 = false>
 __global__ void __launch_bounds__(256)
 k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coef,
-            const float4* __restrict__ coef_pair, typename PT<P>::V* __restrict__ X,
-            typename PT<P>::V* __restrict__ Pv, const typename PT<P>::V* __restrict__ r1, State* st) {
-  typedef typename PT<P>::V V;
+            const float4* __restrict__ coef_pair, typename XT<P, XP32>::V* __restrict__ X,
+            typename XT<P, XP32>::V* __restrict__ Pv, const typename PT<P>::V* __restrict__ r1, State* st) {
+  typedef typename XT<P, XP32>::V V;
   if (!st->xp_pending) return;
   const int nl = st->n_list;
   const int ntile = (nl + TS - 1) / TS;
@@ -1498,7 +1509,7 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
     __syncthreads();
     const int i = chunk * blockDim.x + threadIdx.x;
     if (i < m) {
-      const V ri = r1[i];
+      const V ri = to_x(r1[i], (V*)nullptr);
 #pragma unroll 4
       for (int s = 0; s < nts; ++s) {
         const size_t o = (size_t)ks[s] * m + i;
@@ -1520,12 +1531,17 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
 // ================================================================ adjoint bilinear forms
 // out[k] = y_k^T H x_k (unconjugated) for a tile of BT shifts: one thread per
 // row reads the row's indices and values once and applies them to every shift
-// of the tile.  X, Y: [K][m] FP64 complex, shift-major.  Per-block partials
-// part[(tile * gridDim.x + block) * BT + t] are summed by k_bilinear_reduce.
-template <int BT>
+// of the tile.  X, Y: [K][m] complex, shift-major, FP64 (XV = double2) or FP32
+// (XV = float2, widened to FP64 on load); the sums are FP64.  Per-block
+// partials part[(tile * gridDim.x + block) * BT + t] are summed by
+// k_bilinear_reduce.
+__device__ __forceinline__ double2 wide(double2 v) { return v; }
+__device__ __forceinline__ double2 wide(float2 v) { return make_double2(v.x, v.y); }
+
+template <int BT, class XV>
 __global__ void __launch_bounds__(256)
 k_bilinear(int m, int K, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
-           const double* __restrict__ val, const double2* __restrict__ X, const double2* __restrict__ Y,
+           const double* __restrict__ val, const XV* __restrict__ X, const XV* __restrict__ Y,
            double2* __restrict__ part) {
   const int tile = blockIdx.y, k0 = tile * BT;
   const int nt = min(BT, K - k0);
@@ -1537,15 +1553,15 @@ k_bilinear(int m, int K, const int64_t* __restrict__ rowptr, const int* __restri
 #pragma unroll
     for (int t = 0; t < BT; ++t) {
       if (t < nt) {
-        const double2* xk = X + (size_t)(k0 + t) * m;
+        const XV* xk = X + (size_t)(k0 + t) * m;
         double2 s = make_double2(0.0, 0.0);
         for (int j = beg; j < end; ++j) {
           const double v = val[j];
-          const double2 x = xk[col[j]];
+          const double2 x = wide(xk[col[j]]);
           s.x = fma(v, x.x, s.x);
           s.y = fma(v, x.y, s.y);
         }
-        const double2 y = Y[(size_t)(k0 + t) * m + i];
+        const double2 y = wide(Y[(size_t)(k0 + t) * m + i]);
         re[t] = fma(y.x, s.x, fma(-y.y, s.y, re[t]));
         im[t] = fma(y.x, s.y, fma(y.y, s.x, im[t]));
       }
@@ -1600,10 +1616,8 @@ __global__ void k_init_vectors(int m, int np, const double* __restrict__ b, cons
 }
 
 // x_k = 0, p_k = b for every shift (full mode, Eq. 23-24 initialisation).
-template <int P>
-__global__ void k_init_xp(int m, int K, const double* __restrict__ b, typename PT<P>::V* X,
-                          typename PT<P>::V* Pv) {
-  typedef typename PT<P>::V V;
+template <class V>
+__global__ void k_init_xp(int m, int K, const double* __restrict__ b, V* X, V* Pv) {
   const long long total = (long long)K * m;
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
        o += (long long)gridDim.x * blockDim.x) {
@@ -2177,7 +2191,7 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   // lanes per shift: one per projection row up to 4; beyond that each lane takes several rows, so
   // that the shift's FP64 scalars are not recomputed on many lanes and the grid (one warp per block,
   // each arriving on the block counter) stays small.  Every choice gives the same numbers.
-  const int lps = w.full ? 1 : (w.nproj <= 1 ? 1 : w.nproj <= 2 ? 2 : 4);
+  const int lps = w.nproj <= 1 ? 1 : w.nproj <= 2 ? 2 : 4;
   const int spw = 32 / lps;
   const int nb3 = (w.K + spw - 1) / spw;
   switch (lps) {
@@ -2196,10 +2210,18 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
     // no more blocks than (shift tile, row chunk) items at full activity: every block takes part
     // in the arrival count, so idle blocks would only add to it
     const long long items = (long long)((w.K + 7) / 8) * ((w.m + 255) / 256);
-    const int nblk_xp = (int)std::max<long long>(
-        1, std::min<long long>(resident_blocks(nblk_xp_per_sm, k_update_xp<P, 8>, 256, w.num_sms), items));
-    k_update_xp<P, 8><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
-                                                      (const V*)rm, w.st);
+    if (w.xp32) {
+      static int nblk_xp32_per_sm = 0;
+      const int nblk_xp = (int)std::max<long long>(
+          1, std::min<long long>(resident_blocks(nblk_xp32_per_sm, k_update_xp<P, 8, true>, 256, w.num_sms), items));
+      k_update_xp<P, 8, true><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (float2*)w.X,
+                                                       (float2*)w.P, (const V*)rm, w.st);
+    } else {
+      const int nblk_xp = (int)std::max<long long>(
+          1, std::min<long long>(resident_blocks(nblk_xp_per_sm, k_update_xp<P, 8>, 256, w.num_sms), items));
+      k_update_xp<P, 8><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
+                                                 (const V*)rm, w.st);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *launches += 1;
   }
@@ -2229,7 +2251,8 @@ cudaError_t launch_init(Work& w) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (w.full) {
-    k_init_xp<P><<<8 * w.num_sms, 256, 0, w.stream>>>((int)w.m, w.K, w.b, (V*)w.X, (V*)w.P);
+    if (w.xp32) k_init_xp<float2><<<8 * w.num_sms, 256, 0, w.stream>>>((int)w.m, w.K, w.b, (float2*)w.X, (float2*)w.P);
+    else k_init_xp<V><<<8 * w.num_sms, 256, 0, w.stream>>>((int)w.m, w.K, w.b, (V*)w.X, (V*)w.P);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (w.nproj <= 8)

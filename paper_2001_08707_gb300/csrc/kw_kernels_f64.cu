@@ -103,11 +103,16 @@ cudaError_t launch_loop_cond(const int* count, int target, unsigned* loop, cudaG
 
 // Bilinear forms y_k^T H x_k of one term for every shift; partials need
 // kBilinearTile * nblk * ceil(K / kBilinearTile) double2.
-cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val,
-                            const double2* X, const double2* Y, int nblk, double2* part, int term, int nterm,
-                            double2* out, cudaStream_t s) {
+cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val, const void* X,
+                            const void* Y, int x32, int nblk, double2* part, int term, int nterm, double2* out,
+                            cudaStream_t s) {
   const int ntile = (K + kBilinearTile - 1) / kBilinearTile;
-  k_bilinear<kBilinearTile><<<dim3(nblk, ntile), 256, 0, s>>>(m, K, rowptr, col, val, X, Y, part);
+  if (x32)
+    k_bilinear<kBilinearTile, float2><<<dim3(nblk, ntile), 256, 0, s>>>(m, K, rowptr, col, val, (const float2*)X,
+                                                                        (const float2*)Y, part);
+  else
+    k_bilinear<kBilinearTile, double2><<<dim3(nblk, ntile), 256, 0, s>>>(m, K, rowptr, col, val, (const double2*)X,
+                                                                         (const double2*)Y, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_bilinear_reduce<kBilinearTile><<<(K + 127) / 128, 128, 0, s>>>(K, nblk, term, nterm, part, out);

@@ -122,6 +122,8 @@ def load_library(path: str = LIB_PATH):
         "kw_set_krylov_log": (C.c_int, [P, I64]),
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
         "kw_set_bulk_copy": (C.c_int, [P, C.c_int]),
+        "kw_set_shift_storage": (C.c_int, [P, C.c_int]),
+        "kw_bilinear_c64": (C.c_int, [P, I64, I64, C.POINTER(kw_csr_term), I64, P, P, P]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
         "kw_resume": (C.c_int, [P, I64, P, C.POINTER(kw_solve_info)]),
         "kw_rci_init": (C.c_int, [P, I64, P, I64, P, I64, P, P, C.POINTER(kw_rci_io)]),
@@ -443,7 +445,7 @@ class Solver:
         nleft = 0 if ll is None else ll.shape[0]
         x = None
         if full:
-            x = np.zeros((K, m), dtype=np.complex64 if self.prec == KW_C32V_F64S else np.complex128)
+            x = np.zeros((K, m), dtype=np.complex64 if self.vec_dtype == self._torch.complex64 else np.complex128)
         proj = np.zeros((K, nleft + 1), dtype=np.complex128)
         info = kw_solve_info()
         vp = lambda a: None if a is None else a.ctypes.data_as(C.c_void_p)
@@ -575,6 +577,16 @@ class Solver:
         if st != KW_OK:
             raise self._err(st, "kw_set_stream_overlap")
 
+    def set_shift_storage(self, fp32: bool):
+        """kw_set_shift_storage: in full mode keep x^(k) and p^(k) as complex FP32
+        (the seed recurrence keeps the form's precision); x tensors are then
+        complex64 and the projections come from the projected recurrences."""
+        st = self._lib.kw_set_shift_storage(self._ctx, int(bool(fp32)))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_shift_storage")
+        t = self._torch
+        self.vec_dtype = t.complex64 if (fp32 or self.prec == KW_C32V_F64S) else t.complex128
+
     def set_bulk_copy(self, on):
         """kw_set_bulk_copy: stage the three-term update's tiles in shared memory
         with TMA bulk copies (True), read them with plain loads (False), or -1
@@ -662,14 +674,12 @@ class Solver:
         return {"launches": s.launches, "timed_iters": s.timed_iters, "kernel_ms": list(s.kernel_ms),
                 "tune_runs": s.tune_runs, "tune_hits": s.tune_hits}
 
-    def solve_batched(self, problems, check: bool = True):
-        """kw_solve_batched over a list of problems, each a dict with keys H (CSR with
-        rowptr, col, val arrays), b, z and optionally left, full (default True) and
-        tol.  Returns one SolveResult per problem."""
+    def prepare_batch(self, problems):
+        """Device-resident inputs and outputs of a kw_solve_batched call, built once
+        (problems as in solve_batched); run_batch(handle) then makes only the call."""
         t = self._torch
         n = len(problems)
         arr = (kw_instance * n)()
-        infos = (kw_solve_info * n)()
         keep, outs = [], []
         for i, pr in enumerate(problems):
             H = pr["H"]
@@ -687,27 +697,47 @@ class Solver:
                                  bd.data_ptr(), zz.size, zp.value, nleft, None if ld is None else ld.data_ptr(),
                                  None if x is None else x.data_ptr(), proj.ctypes.data, float(pr.get("tol", 0.0)))
             outs.append((proj, x))
-        st = self._lib.kw_solve_batched(self._ctx, n, arr, infos)
+        return {"arr": arr, "keep": keep, "outs": outs, "n": n}
+
+    def run_batch(self, handle, check: bool = True):
+        """kw_solve_batched on a prepare_batch handle; one SolveResult per instance."""
+        infos = (kw_solve_info * handle["n"])()
+        st = self._lib.kw_solve_batched(self._ctx, handle["n"], handle["arr"], infos)
         if check and st not in (KW_OK, KW_NOT_CONVERGED):
             raise self._err(st, "kw_solve_batched")
         res = []
-        for (proj, x), info in zip(outs, infos):
-            res.append(SolveResult(proj, x, info.iters, info.n_converged, info.max_res, info.n_seed_switch,
+        for (proj, x), info in zip(handle["outs"], infos):
+            res.append(SolveResult(proj.copy(), x, info.iters, info.n_converged, info.max_res, info.n_seed_switch,
                                    info.updates, info.seed, STATUS.get(info.status, str(info.status))))
         return res
 
+    def solve_batched(self, problems, check: bool = True):
+        """kw_solve_batched over a list of problems, each a dict with keys H (CSR with
+        rowptr, col, val arrays), b, z and optionally left, full (default True) and
+        tol.  Returns one SolveResult per problem."""
+        return self.run_batch(self.prepare_batch(problems), check)
+
     def bilinear(self, terms, X, Y=None) -> np.ndarray:
-        """kw_bilinear: out[k][t] = y_k^T H_t x_k for device CSR terms (each a tuple of
-        CUDA tensors (rowptr int64, col int32, val float64)) and X, Y [K, m] complex128."""
+        """kw_bilinear / kw_bilinear_c64: out[k][t] = y_k^T H_t x_k for device CSR terms
+        (each a tuple of CUDA tensors (rowptr int64, col int32, val float64)) and X, Y
+        [K, m] CUDA tensors, both complex128 or both complex64 (FP64 sums either way)."""
+        t = self._torch
         K, m = X.shape
+        if X.dtype not in (t.complex128, t.complex64) or not X.is_cuda or not X.is_contiguous():
+            raise ValueError("X must be a contiguous complex128 or complex64 CUDA tensor [K, m]")
+        if Y is not None and (Y.dtype != X.dtype or tuple(Y.shape) != tuple(X.shape) or not Y.is_cuda
+                              or not Y.is_contiguous()):
+            raise ValueError("Y must match X in dtype, shape and device and be contiguous")
         arr = (kw_csr_term * len(terms))()
         for i, (rp, cl, vl) in enumerate(terms):
             arr[i] = kw_csr_term(cl.numel(), rp.data_ptr(), cl.data_ptr(), vl.data_ptr())
         out = np.zeros((K, len(terms)), dtype=np.complex128)
-        st = self._lib.kw_bilinear(self._ctx, m, len(terms), arr, K, C.c_void_p(X.data_ptr()),
-                                   None if Y is None else C.c_void_p(Y.data_ptr()), out.ctypes.data_as(C.c_void_p))
+        fn, name = ((self._lib.kw_bilinear_c64, "kw_bilinear_c64") if X.dtype == t.complex64
+                    else (self._lib.kw_bilinear, "kw_bilinear"))
+        st = fn(self._ctx, m, len(terms), arr, K, C.c_void_p(X.data_ptr()),
+                None if Y is None else C.c_void_p(Y.data_ptr()), out.ctypes.data_as(C.c_void_p))
         if st != KW_OK:
-            raise self._err(st, "kw_bilinear")
+            raise self._err(st, name)
         return out
 
     def spmv_dot(self, zs: complex, r, q):

@@ -102,3 +102,77 @@ def test_fullsize_gradient_vs_central_differences():
         fd = (lp - lm) / (2 * h)
         print(f"param {t}: adjoint {g[t]:.10e} central difference {fd:.10e}")
         assert abs(fd - g[t]) <= 1e-5 * abs(g[t]) + 1e-9
+
+
+def test_bilinear_c64_matches_numpy():
+    """kw_bilinear_c64: complex FP32 X and Y widened to FP64, FP64 sums."""
+    j = w.j1j2_chain(10, 1.0, 0.4, 0.2, seed=2)
+    m = j.terms[0].m
+    rng = np.random.default_rng(4)
+    K = 11
+    X = (rng.standard_normal((K, m)) + 1j * rng.standard_normal((K, m))).astype(np.complex64)
+    Y = (rng.standard_normal((K, m)) + 1j * rng.standard_normal((K, m))).astype(np.complex64)
+    s = kw.Solver("f64")
+    ts = adjoint.TermSet(j.terms)
+    Xd, Yd = torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")
+    X64, Y64 = X.astype(np.complex128), Y.astype(np.complex128)
+    for y_is_x in (True, False):
+        out = s.bilinear(ts.device_terms, Xd, None if y_is_x else Yd)
+        YY = X64 if y_is_x else Y64
+        ref = np.stack([np.sum(YY * (t.to_scipy() @ X64.T).T, axis=1) for t in j.terms], axis=1)
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    with pytest.raises(ValueError):
+        s.bilinear(ts.device_terms, Xd, Yd.to(torch.complex128))
+
+
+@pytest.mark.parametrize("form", ["f64", "df64", "df64+x32"])
+def test_green_a_ne_b_gradient_matches_oracle(form):
+    """d(a^T G b)/dtheta for a left vector a different from b (second solve with
+    rhs a) against the oracle's two solves, through a real loss on the complex
+    G_ab.  With FP32 shift storage the stored x_k, y_k carry FP32 error, so the
+    gradient is compared at 1e-5 (the values still come from the FP64-class
+    recurrences)."""
+    j, z, b, theta_star = _problem(12, 24)
+    terms = [t.to_scipy() for t in j.terms]
+    a = w.gaussian_unit(j.terms[0].m, 13, w.STREAM_LEFT)
+    G_star, _ = oa.green_and_gradient(terms, theta_star, a, b, z, tol=1e-12)
+    G_o, dG_o = oa.green_and_gradient(terms, j.theta, a, b, z, tol=1e-12)
+    grad_o = np.real(np.conj(2 * (G_o - G_star)) @ dG_o)     # L = sum |G - G*|^2
+    prec = form.split("+")[0]
+    model = adjoint.GreenBilinear(j.terms, b, z, a=a, prec=prec, tol=1e-12, shift_fp32=form.endswith("x32"))
+    theta = torch.tensor(j.theta, dtype=torch.float64, requires_grad=True)
+    G = model(theta)
+    loss = torch.sum(torch.abs(G - torch.as_tensor(G_star)) ** 2)
+    loss.backward()
+    np.testing.assert_allclose(G.detach().numpy(), G_o, rtol=0, atol=1e-10 * np.abs(G_o).max())
+    g = theta.grad.numpy()
+    tol = 1e-5 if form.endswith("x32") else 1e-8
+    print(f"{form}: max gradient error {np.abs(g - grad_o).max() / np.abs(grad_o).max():.2e}")
+    assert np.abs(g - grad_o).max() <= tol * np.abs(grad_o).max(), (g, grad_o)
+
+
+def test_green_a_ne_b_gradcheck_tiny():
+    """gradcheck of the complex outputs G_ab(theta) (a != b) on N=8, 5 shifts."""
+    j, z, b, _ = _problem(8, 5)
+    a = w.gaussian_unit(j.terms[0].m, 17, w.STREAM_LEFT)
+    model = adjoint.GreenBilinear(j.terms, b, z, a=a, prec="f64", tol=1e-13)
+    theta = torch.tensor(j.theta, dtype=torch.float64, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda th: model(th), (theta,), eps=1e-6, atol=1e-6, rtol=1e-5)
+
+
+def test_spectrum_gradient_with_fp32_shift_storage():
+    """GreenSpectrum with FP32 x/p storage: the spectrum keeps the FP64-class
+    agreement (projected recurrences), the gradient agrees at FP32 level."""
+    j, z, b, theta_star = _problem(12, 32)
+    terms = [t.to_scipy() for t in j.terms]
+    target = oa.spectrum(terms, theta_star, b, z, tol=1e-12)[0]
+    A_o, _, grad_o, _ = oa.spectrum_and_gradient(terms, j.theta, b, z, target, tol=1e-12)
+    model = adjoint.GreenSpectrum(j.terms, b, z, prec="df64", tol=1e-12, shift_fp32=True)
+    theta = torch.tensor(j.theta, dtype=torch.float64, requires_grad=True)
+    A = model(theta)
+    loss = 0.5 * torch.sum((A - torch.as_tensor(target)) ** 2)
+    loss.backward()
+    np.testing.assert_allclose(A.detach().numpy(), A_o, rtol=0, atol=1e-10 * np.abs(A_o).max())
+    g = theta.grad.numpy()
+    print(f"max gradient error {np.abs(g - grad_o).max() / np.abs(grad_o).max():.2e}")
+    assert np.abs(g - grad_o).max() <= 1e-5 * np.abs(grad_o).max()

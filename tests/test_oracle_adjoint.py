@@ -69,3 +69,41 @@ def test_assemble_matches_the_generators():
     np.testing.assert_allclose(C, w.heisenberg_chain(8).to_scipy().toarray(), rtol=0, atol=1e-15)
     # every term enters: dropping the last field term changes the matrix
     assert np.abs(oa.assemble(terms[:-1], j.theta[:-1]).toarray() - A).max() > 1e-3
+
+
+def test_green_gradient_a_ne_b_matches_dense_inverse_and_is_symmetric():
+    """dG_ab/dtheta_m = a^T G H_m G b with G the explicit inverse, for a left vector
+    a different from b; and swapping a and b gives the same derivative (G and H_m
+    symmetric), which a transposed operand or a y/x mix-up would break."""
+    j, terms, b, z = _model(N=8, seed=4)
+    a = w.gaussian_unit(j.terms[0].m, 9, w.STREAM_LEFT)
+    G, dG = oa.green_and_gradient(terms, j.theta, a, b, z, tol=1e-13)
+    H = oa.assemble(terms, j.theta).toarray()
+    M = H.shape[0]
+    for k, zk in enumerate(z):
+        Gi = np.linalg.inv(zk * np.eye(M) - H)
+        assert abs(G[k] - a @ Gi @ b) <= 1e-10 * (1 + abs(G[k]))
+        for m, Hm in enumerate(terms):
+            ref = a @ Gi @ Hm.toarray() @ Gi @ b
+            assert abs(dG[k, m] - ref) <= 1e-9 * (1 + abs(ref))
+    G2, dG2 = oa.green_and_gradient(terms, j.theta, b, a, z, tol=1e-13)
+    np.testing.assert_allclose(G2, G, rtol=0, atol=1e-10 * np.abs(G).max())
+    np.testing.assert_allclose(dG2, dG, rtol=0, atol=1e-9 * np.abs(dG).max())
+    # a = b reduces to the spectrum gradient: dA/dtheta = -(1/pi) Im dG_bb/dtheta
+    _, _, _, dA = oa.spectrum_and_gradient(terms, j.theta, b, z, np.zeros(z.size), tol=1e-13)
+    _, dGbb = oa.green_and_gradient(terms, j.theta, b, b, z, tol=1e-13)
+    np.testing.assert_allclose(-np.imag(dGbb) / np.pi, dA, rtol=0, atol=1e-10 * np.abs(dA).max())
+
+
+def test_green_gradient_a_ne_b_central_differences():
+    j, terms, b, z = _model(N=10, seed=6)
+    a = w.gaussian_unit(j.terms[0].m, 11, w.STREAM_LEFT)
+    _, dG = oa.green_and_gradient(terms, j.theta, a, b, z, tol=1e-13)
+    h = 1e-5
+    for m in (0, 1, 3):
+        e = np.zeros_like(j.theta)
+        e[m] = h
+        Gp, _ = oa.green_and_gradient(terms, j.theta + e, a, b, z, tol=1e-13)
+        Gm, _ = oa.green_and_gradient(terms, j.theta - e, a, b, z, tol=1e-13)
+        fd = (Gp - Gm) / (2 * h)
+        assert np.abs(fd - dG[:, m]).max() <= 1e-6 * np.abs(dG[:, m]).max()
