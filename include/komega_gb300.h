@@ -492,6 +492,18 @@ kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
  * few seconds (the context stays usable).  Errors: KW_ERR_ARG. */
 kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
 
+/* Form of the three-term update kernel (Eq. 16 with rho, nu and P r_{n+1} of
+ * Eq. 26) in the KW_DF64 form with the COCG or CG solver.  mode 1: two phases
+ * per 256-element tile, r_{n+1} of each element first, then four thread groups
+ * each forming every fourth projection row from shared memory (few
+ * accumulators per thread, for many projection rows); 0: one element per
+ * thread with every projection accumulated by that thread (kw_set_bulk_copy
+ * then selects plain or staged loads); -1 (default): mode 1 above nine
+ * projection rows (b plus the left vectors), else 0.  Results agree to
+ * rounding, not bit for bit (different summation order).  Applies from the next
+ * solve.  Errors: KW_ERR_ARG. */
+kw_status kw_set_seed_update(kw_ctx* ctx, int mode);
+
 /* Storage of the shifted vectors in full mode (Eq. 23-24; the K*M-sized part of
  * the state, Sec. 2.2.3).  fp32 = 1: x^(k) and p^(k) are stored and updated as
  * complex FP32 (8 bytes per element) in the KW_F64 and KW_DF64 forms, while

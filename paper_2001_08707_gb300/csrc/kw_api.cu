@@ -147,6 +147,7 @@ struct kw_ctx {
   int overlap = 1;
   int bulk = -1;  // kw_set_bulk_copy (-1: auto)
   int xp32 = 0;   // kw_set_shift_storage: full-mode x/p as complex FP32
+  int seed_rg = -1;  // kw_set_seed_update: K2 row-group form (-1 auto)
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -999,6 +1000,7 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
   w.tol = ctx->opt.tol;
   w.proj_ld = (m + kw::KW_PROJ_ALIGN - 1) / kw::KW_PROJ_ALIGN * kw::KW_PROJ_ALIGN;
   w.bulk = ctx->bulk;
+  w.seed_rg = ctx->seed_rg;
   w.b = b_dev;
   w.left = left_dev;
   w.stream = ctx->stream;
@@ -1580,6 +1582,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     c->overlap = ctx->overlap;
     c->bulk = ctx->bulk;
     c->xp32 = ctx->xp32;
+    c->seed_rg = ctx->seed_rg;
     if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
     c->run_maxiter = c->opt.maxiter;
     KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
@@ -1943,6 +1946,12 @@ kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user) {
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return KW_ERR_ARG;
   ctx->overlap = on;
+  return KW_OK;
+}
+
+kw_status kw_set_seed_update(kw_ctx* ctx, int mode) {
+  if (!ctx || mode < -1 || mode > 1) return KW_ERR_ARG;
+  ctx->seed_rg = mode;
   return KW_OK;
 }
 

@@ -104,6 +104,7 @@ struct Work {
   void* proj_rows;   // [nproj][proj_ld] real, vector precision (b then left vectors)
   int64_t proj_ld;   // row stride of proj_rows: m rounded up to KW_PROJ_ALIGN elements (16-byte aligned rows)
   int bulk = -1;     // K2 tile staging by TMA bulk copies: -1 auto (more than 9 projection rows), 0 off, 1 on, 2 test
+  int seed_rg = -1;  // K2 row-group form (pair form): -1 auto (more than 9 projection rows), 0 off, 1 on
   // shift state
   double2* z;
   double2* pi1;      // pi_n

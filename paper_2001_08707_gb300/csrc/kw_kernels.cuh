@@ -873,40 +873,19 @@ __global__ void k_sell_fill(int m, int nslice, const int* __restrict__ perm, con
 // is the element set of its t-th grid-stride trip, so each thread sums the
 // same elements in the same order as without staging.  The ragged last tile
 // is read with plain loads.
-constexpr int kSeedTile = 256;
-
-// Bytes of one stage: a tile of r_n, q, r_{n-1} and of the np projection rows.
-template <class V, class R>
-__host__ __device__ constexpr uint32_t seed_stage_bytes(int np) {
-  return (uint32_t)((3 * kSeedTile * sizeof(V) + np * kSeedTile * sizeof(R) + 127) / 128 * 128);
-}
-
-template <int P, int NP, int METHOD, bool BULK>
-__global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5 && METHOD != KW_METHOD_BICG) ? 3 : 1)
-k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
-              typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int64_t ld,
-              int np, int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out,
-              const typename PT<P>::V* __restrict__ rtn_buf, const typename PT<P>::V* __restrict__ qt,
-              typename PT<P>::V* __restrict__ rtm_buf, int nstage, uint32_t tx_pad) {
-  typedef typename PT<P>::V V;
-  typedef typename PT<P>::R R;
-  typedef typename PT<P>::A A;
-  constexpr int N = 3 + 2 * NP;
-  constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
-  if (st->done) return;
-  // Seed scalars of Eq. 17 and the three coefficients of Eq. 16.  The two
-  // residual buffers carry pending scales (bscale) from seed switches
-  // (Sec. 2.2.4: r_{n+1} <- r_{n+1}/pi^j_{n+1}, r_n <- r_n/pi^j_n), and K1 ran
-  // concurrently with the last K3, i.e. with the seed before its switch
-  // (q_raw = z_K1 r_raw - H r_raw).  With s_n, s_{n-1} the buffers' scales and
-  // dz = z_s - z_K1, by linearity r_n = s_n r_raw, q = s_n (q_raw + dz r_raw),
-  // r_n^T A r_n = s_n^2 (u + dz rho_raw), so that
-  //   r_{n+1} = [s_n (1 + c - alpha dz)] r_raw - [alpha s_n] q_raw - [c s_{n-1}] r_{n-1,raw}:
-  // a switch changes the coefficients, not the per-element work.
-  __shared__ double2 s_sc[2];   // c_n, 1/rho_n
-  __shared__ double2 s_cf[3];   // the three coefficients in FP64
-  __shared__ float4 s_pp[3];    // FP32-pair images of the three coefficients
-  __shared__ int s_fail;
+// K2's head (thread 0): the seed scalars of Eq. 17 and the three coefficients
+// of Eq. 16 into shared memory (s_sc = c_n, 1/rho_n; s_cf = the coefficients
+// in FP64; s_pp = their FP32-pair images; *s_fail = a breakdown status); block
+// 0 also records the scalars in the state.  The two residual buffers carry
+// pending scales (bscale) from seed switches (Sec. 2.2.4: r_{n+1} <-
+// r_{n+1}/pi^j_{n+1}, r_n <- r_n/pi^j_n), and K1 ran concurrently with the last
+// K3, i.e. with the seed before its switch (q_raw = z_K1 r_raw - H r_raw).  With
+// s_n, s_{n-1} the buffers' scales and dz = z_s - z_K1, by linearity
+// r_n = s_n r_raw, q = s_n (q_raw + dz r_raw), r_n^T A r_n = s_n^2 (u + dz rho_raw), so that
+//   r_{n+1} = [s_n (1 + c - alpha dz)] r_raw - [alpha s_n] q_raw - [c s_{n-1}] r_{n-1,raw}:
+// a switch changes the coefficients, not the per-element work.
+__device__ __forceinline__ void seed_coefficients(State* st, int parity, double2* s_sc, double2* s_cf, float4* s_pp,
+                                                  int* s_fail) {
   if (threadIdx.x == 0) {
     const double2 one = make_double2(1.0, 0.0), zero = make_double2(0.0, 0.0);
     const double2 sn = st->bscale[parity], sm = st->bscale[1 - parity];
@@ -949,7 +928,7 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
     }
     s_sc[0] = c;
     s_sc[1] = inv_rho;
-    s_fail = fail;
+    *s_fail = fail;
     if (blockIdx.x == 0) {
       if (fail) {
         set_fail(st, fail);
@@ -967,6 +946,60 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
     s_cf[1] = plain ? alpha : cmul(alpha, sn);
     s_cf[2] = plain ? c : cmul(c, sm);
   }
+}
+
+// K2's tail (last block, after the grid reduction): P r_{n+1} to w_out, and
+// rho_{n+1} (r^T r for COCG, ||r||^2 for CG, r~^dagger r for BiCG), beta_n,
+// nu = ||r_{n+1}||^2 into the state.  all = [rho.re, rho.im, nu, w...];
+// inv_rho = this block's 1/rho_n.
+template <int METHOD>
+__device__ __forceinline__ void seed_finish(const double* all, int np, int parity, State* st, double2* w_out,
+                                            double2 inv_rho) {
+  for (int l = threadIdx.x; l < np; l += blockDim.x) w_out[l] = make_double2(all[3 + 2 * l], all[4 + 2 * l]);
+  if (threadIdx.x == 0) {
+    st->cnt_seed = 0;
+    st->bscale[1 - parity] = make_double2(1.0, 0.0);   // r_{n+1} was just written
+    st->switched = 0;
+    st->zs_k1 = st->zs;                                // the seed the next K1 uses
+    st->p_zs_k1 = st->p_zs;
+    // rho_{n+1}: r^T r (COCG), ||r||^2 (CG), r~^dagger r (BiCG)
+    const double2 rho1 = METHOD == KW_METHOD_CG ? make_double2(all[2], 0.0) : make_double2(all[0], all[1]);
+    // beta_n = rho_{n+1} / rho_n, with this block's own 1/rho_n (block 0's copy in
+    // the state was written during this kernel and may not be visible here)
+    const double2 beta = cmul(rho1, inv_rho);
+    st->rho1 = rho1;
+    st->beta = beta;
+    st->nu = all[2];
+    if (!cfinite(beta) || !isfinite(all[2])) set_fail(st, KW_ERR_NONFINITE);
+  }
+}
+
+constexpr int kSeedTile = 256;
+
+// Bytes of one stage: a tile of r_n, q, r_{n-1} and of the np projection rows.
+template <class V, class R>
+__host__ __device__ constexpr uint32_t seed_stage_bytes(int np) {
+  return (uint32_t)((3 * kSeedTile * sizeof(V) + np * kSeedTile * sizeof(R) + 127) / 128 * 128);
+}
+
+template <int P, int NP, int METHOD, bool BULK>
+__global__ void __launch_bounds__(256, (P == PREC_DF && NP <= 5 && METHOD != KW_METHOD_BICG) ? 3 : 1)
+k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typename PT<P>::V* __restrict__ q,
+              typename PT<P>::V* __restrict__ rm_buf, const typename PT<P>::R* __restrict__ proj, int64_t ld,
+              int np, int parity, State* st, double* __restrict__ part, double2* __restrict__ w_out,
+              const typename PT<P>::V* __restrict__ rtn_buf, const typename PT<P>::V* __restrict__ qt,
+              typename PT<P>::V* __restrict__ rtm_buf, int nstage, uint32_t tx_pad) {
+  typedef typename PT<P>::V V;
+  typedef typename PT<P>::R R;
+  typedef typename PT<P>::A A;
+  constexpr int N = 3 + 2 * NP;
+  constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
+  if (st->done) return;
+  __shared__ double2 s_sc[2];   // c_n, 1/rho_n
+  __shared__ double2 s_cf[3];   // the three coefficients in FP64
+  __shared__ float4 s_pp[3];    // FP32-pair images of the three coefficients
+  __shared__ int s_fail;
+  seed_coefficients(st, parity, s_sc, s_cf, s_pp, &s_fail);
   __syncthreads();
   if (s_fail) return;
   // the coefficients are re-read from shared memory at each element (the pair
@@ -1146,23 +1179,169 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
     if (!arrive_last(&st->cnt_seed)) return;
     reduce_partials<N>(part, gridDim.x, n, n, all);
   }
-  for (int l = threadIdx.x; l < np; l += blockDim.x) w_out[l] = make_double2(all[3 + 2 * l], all[4 + 2 * l]);
+  seed_finish<METHOD>(all, np, parity, st, w_out, s_sc[1]);
+}
+
+// K2 for many projection rows in the FP32-pair form.  The plain kernel keeps
+// 3 + 2 NP pair accumulators per thread (rho, nu and every P r_{n+1} entry),
+// which above nine rows limits it to one or two blocks per SM.  Here each
+// 256-element tile goes through two phases: (A) every thread forms r_{n+1} for
+// one element (Eq. 16), stores it, accumulates rho and nu, and leaves it in
+// shared memory; (B) the block's four 64-thread groups each take every fourth
+// projection row over all 256 elements (four per thread), reading r_{n+1} from
+// shared memory, for w_l = a_l^T r_{n+1} (the P r_{n+1} of Eq. 26).  A thread
+// holds 3 + 2 ceil(NP / 4) accumulators.  The tile of the np projection rows
+// (np x 2 KB) is copied into shared memory by TMA bulk copies two tiles ahead
+// (full tiles; the ragged last tile reads the rows directly), on the same
+// bounded mbarrier protocol as the staged kernel above: a wait that runs out
+// ends the solve with KW_ERR_TIMEOUT after the block's copies have landed.
+// Sums run in a fixed order (deterministic), with pair block and grid
+// reductions.
+constexpr int kRowGroups = 4;
+constexpr int kRgStages = 2;
+
+__host__ __device__ constexpr uint32_t rg_stage_bytes(int np) { return (uint32_t)(np * kSeedTile * sizeof(df)); }
+
+template <int NP, int METHOD>
+__global__ void __launch_bounds__(256, 3)
+k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ q, dfc* __restrict__ rm_buf,
+                 const df* __restrict__ proj, int64_t ld, int np, int parity, State* st, double* __restrict__ part,
+                 double2* __restrict__ w_out, uint32_t tx_pad) {
+  constexpr int RPG = (NP + kRowGroups - 1) / kRowGroups;
+  constexpr int N = 3 + 2 * NP;
+  static_assert(kSeedTile == 256, "four 64-thread row groups per 256-element tile");
+  extern __shared__ __align__(128) unsigned char kw_rg_stage[];
+  __shared__ __align__(8) uint64_t bars[kRgStages];
+  if (st->done) return;
+  __shared__ double2 s_sc[2];
+  __shared__ double2 s_cf[3];
+  __shared__ float4 s_pp[3];
+  __shared__ int s_fail;
+  __shared__ dfc s_r1[kSeedTile];
+  __shared__ df sw[N][8];
+  __shared__ df red[N];
+  __shared__ double all[N];
+  seed_coefficients(st, parity, s_sc, s_cf, s_pp, &s_fail);
+  __syncthreads();
+  if (s_fail) return;
+  const dfc ca = vscalar<dfc>(s_cf[0], s_pp[0]), cb = vscalar<dfc>(s_cf[1], s_pp[1]);
+  const dfc cc = vscalar<dfc>(s_cf[2], s_pp[2]);
+  const int n = 3 + 2 * np;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = threadIdx.x / 64, e0 = threadIdx.x % 64;
+  df rho_re = azero<df>(), rho_im = azero<df>(), nu = azero<df>();
+  df pr[RPG], pim[RPG];
+#pragma unroll
+  for (int j = 0; j < RPG; ++j) pr[j] = pim[j] = azero<df>();
+  const int ntiles = (m + kSeedTile - 1) / kSeedTile, nfull = m / kSeedTile, G = gridDim.x;
+  const uint32_t sbytes = rg_stage_bytes(np), tx = sbytes + tx_pad;
   if (threadIdx.x == 0) {
-    st->cnt_seed = 0;
-    st->bscale[1 - parity] = make_double2(1.0, 0.0);   // r_{n+1} was just written
-    st->switched = 0;
-    st->zs_k1 = st->zs;                                // the seed the next K1 uses
-    st->p_zs_k1 = st->p_zs;
-    // rho_{n+1}: r^T r (COCG), ||r||^2 (CG), r~^dagger r (BiCG)
-    const double2 rho1 = METHOD == KW_METHOD_CG ? make_double2(all[2], 0.0) : make_double2(all[0], all[1]);
-    // beta_n = rho_{n+1} / rho_n, with this block's own 1/rho_n (block 0's copy in
-    // the state was written during this kernel and may not be visible here)
-    const double2 beta = cmul(rho1, s_sc[1]);
-    st->rho1 = rho1;
-    st->beta = beta;
-    st->nu = all[2];
-    if (!cfinite(beta) || !isfinite(all[2])) set_fail(st, KW_ERR_NONFINITE);
+    for (int s = 0; s < kRgStages; ++s) mbar_init(&bars[s], 1);
+    mbar_init_fence();
   }
+  __syncthreads();
+  auto issue = [&](int t, int s) {   // thread 0: the projection rows of tile t into stage s
+    unsigned char* dst = kw_rg_stage + (size_t)s * sbytes;
+    const size_t e = (size_t)t * kSeedTile;
+    mbar_arrive_expect(&bars[s], tx);
+    for (int l = 0; l < np; ++l)
+      bulk_load(dst + (size_t)l * kSeedTile * sizeof(df), proj + (size_t)l * ld + e, kSeedTile * sizeof(df), &bars[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int s = 0; s < kRgStages; ++s)
+      if (blockIdx.x + s * G < nfull) issue(blockIdx.x + s * G, s);
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
+    const int base = t * kSeedTile;
+    const int i = base + (int)threadIdx.x;
+    dfc r1 = vzero<dfc>();
+    if (i < m) {                                      // phase A: Eq. 16 for one element
+      const dfc rnv = rn_buf[i], qv = q[i], rmv = rm_buf[i];
+      r1 = csub(csub(cmul(ca, rnv), cmul(cb, qv)), cmul(cc, rmv));
+      rm_buf[i] = r1;
+      if constexpr (METHOD == KW_METHOD_CG) acc_nrm(nu, r1);
+      else acc_rho_nrm(rho_re, rho_im, nu, r1);
+    }
+    s_r1[threadIdx.x] = r1;
+    const bool staged = t < nfull;
+    const int s = k % kRgStages;
+    const bool late = staged && !mbar_wait(&bars[s], (uint32_t)(k / kRgStages) & 1u);
+    if (__syncthreads_or(late)) {   // a copy did not land in time: report, let copies in flight finish, stop
+      if (threadIdx.x == 0) {
+        set_fail(st, KW_ERR_TIMEOUT);
+        for (int j = 0; j < kRgStages; ++j)
+          if (blockIdx.x + (k + j) * G < nfull)
+            mbar_wait(&bars[(k + j) % kRgStages], (uint32_t)((k + j) / kRgStages) & 1u);
+      }
+      __syncthreads();
+      break;
+    }
+    const df* sa = reinterpret_cast<const df*>(kw_rg_stage + (size_t)s * sbytes);
+#pragma unroll
+    for (int jj = 0; jj < kSeedTile / 64; ++jj) {    // phase B: this group's rows over the tile
+      const int e = e0 + 64 * jj, ie = base + e;
+      if (ie < m) {
+        const dfc rv = s_r1[e];
+#pragma unroll
+        for (int j = 0; j < RPG; ++j) {
+          const int l = g + kRowGroups * j;
+          if (l < np) {
+            const df a = staged ? sa[l * kSeedTile + e] : proj[(size_t)l * ld + ie];
+            acc_proj(pr[j], pim[j], a, rv);
+          }
+        }
+      }
+    }
+    __syncthreads();                                  // stage s and s_r1 are free
+    if (threadIdx.x == 0 && t + kRgStages * G < nfull) {
+      fence_async_smem();
+      issue(t + kRgStages * G, s);
+    }
+  }
+  // block sums: one pair per warp and value (a warp lies in one row group; it
+  // contributes zero to the other groups' rows), then the eight warps in order
+  {
+    const df r0 = warp_sum(anorm(rho_re)), r1v = warp_sum(anorm(rho_im)), r2 = warp_sum(anorm(nu));
+    if (lane == 0) {
+      sw[0][warp] = r0;
+      sw[1][warp] = r1v;
+      sw[2][warp] = r2;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < RPG; ++j) {
+    const df a = warp_sum(anorm(pr[j])), b = warp_sum(anorm(pim[j]));
+#pragma unroll
+    for (int gg = 0; gg < kRowGroups; ++gg) {
+      const int l = gg + kRowGroups * j;
+      if (l < NP && lane == 0) {
+        sw[3 + 2 * l][warp] = gg == g ? a : azero<df>();
+        sw[4 + 2 * l][warp] = gg == g ? b : azero<df>();
+      }
+    }
+  }
+  __syncthreads();
+  df* partd = reinterpret_cast<df*>(part);
+  for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
+    df sum = sw[kk][0];
+    for (int w = 1; w < 8; ++w) sum = df_add(sum, sw[kk][w]);
+    partd[(size_t)blockIdx.x * n + kk] = sum;
+  }
+  if (!arrive_last(&st->cnt_seed)) return;
+  // last block: value kk by warp kk mod 8, its lanes striding over the blocks
+  for (int kk = warp; kk < n; kk += 8) {
+    df a = azero<df>();
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+      const float2 v = __ldcg(reinterpret_cast<const float2*>(partd + (size_t)b * n + kk));
+      a = df_add(a, df{v.x, v.y});
+    }
+    a = warp_sum(anorm(a));
+    if (lane == 0) red[kk] = a;
+  }
+  __syncthreads();
+  for (int kk = threadIdx.x; kk < n; kk += blockDim.x) all[kk] = df_to_double(red[kk]);
+  __syncthreads();
+  seed_finish<METHOD>(all, np, parity, st, w_out, s_sc[1]);   // CG reads rho = ||r||^2 from all[2]
 }
 
 // ================================================================ K3: shift scalars
@@ -2041,6 +2220,30 @@ static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   const void* rtn = parity ? w.rtB : w.rtA;
   void* rtm = parity ? w.rtA : w.rtB;
   const int ntiles = (int)((w.m + kSeedTile - 1) / kSeedTile);
+  // Row-group form (pair form, COCG and CG): by default above nine projection rows
+  if constexpr (P == PREC_DF && METHOD != KW_METHOD_BICG && NP > 0) {
+    if (w.seed_rg > 0 || (w.seed_rg < 0 && w.nproj > 9)) {
+      auto kern = k_seed_update_rg<NP, METHOD>;
+      const int dyn = kRgStages * (int)rg_stage_bytes(w.nproj);
+      static int attr_bytes = 0, occ_bytes = -1, per_sm = 1;
+      cudaError_t e;
+      if (dyn > attr_bytes) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess)
+          return e;
+        attr_bytes = dyn;
+      }
+      if (occ_bytes != dyn) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, dyn) != cudaSuccess || b < 1) b = 1;
+        per_sm = b;
+        occ_bytes = dyn;
+      }
+      const int grid = std::max(1, std::min(per_sm * w.num_sms, ntiles));
+      kern<<<grid, 256, dyn, w.stream>>>((int)w.m, (const dfc*)rn, (const dfc*)w.q, (dfc*)rm, (const df*)w.proj_rows,
+                                         w.proj_ld, w.nproj, parity, w.st, w.part, w.w, w.bulk == 2 ? 16u : 0u);
+      return cudaGetLastError();
+    }
+  }
   // Staged form: the FP32 and FP32-pair forms, whose update is bound by memory
   // latency, not by the FP64 pipe; the BiCG shadow keeps plain loads.
   if constexpr (P != PREC_F64 && METHOD != KW_METHOD_BICG) {

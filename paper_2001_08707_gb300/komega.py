@@ -123,6 +123,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_stream_overlap": (C.c_int, [P, C.c_int]),
         "kw_set_bulk_copy": (C.c_int, [P, C.c_int]),
         "kw_set_shift_storage": (C.c_int, [P, C.c_int]),
+        "kw_set_seed_update": (C.c_int, [P, C.c_int]),
         "kw_bilinear_c64": (C.c_int, [P, I64, I64, C.POINTER(kw_csr_term), I64, P, P, P]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
         "kw_resume": (C.c_int, [P, I64, P, C.POINTER(kw_solve_info)]),
@@ -586,6 +587,14 @@ class Solver:
             raise self._err(st, "kw_set_shift_storage")
         t = self._torch
         self.vec_dtype = t.complex64 if (fp32 or self.prec == KW_C32V_F64S) else t.complex128
+
+    def set_seed_update(self, mode: int):
+        """kw_set_seed_update: 1 = the row-group form of the three-term update
+        (pair form; many projection rows), 0 = one element per thread, -1 (the
+        default) = the row-group form above nine projection rows."""
+        st = self._lib.kw_set_seed_update(self._ctx, int(mode))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_seed_update")
 
     def set_bulk_copy(self, on):
         """kw_set_bulk_copy: stage the three-term update's tiles in shared memory

@@ -51,6 +51,7 @@ def _run(prec, m, nleft, full, bulk, maxiter=3000):
     left = np.stack([w.gaussian_unit(m, 22 + i) for i in range(nleft)]) if nleft else None
     z = w.shiftk_grid(-3, 3, 24, 0.04)
     s = kw.Solver(prec, tol=1e-9, maxiter=maxiter)
+    s.set_seed_update(0)          # the staged and plain loads of the one-element-per-thread update
     s.set_bulk_copy(bulk)
     s.set_csr(H.rowptr, H.col, H.val)
     r = s.solve(b, z, left=left, full=full, check=False)
@@ -89,6 +90,7 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
     b = w.gaussian_unit(H.m, 21)
     z = w.shiftk_grid(-3, 3, 8, 0.04)
     s = kw.Solver("df64", tol=1e-9, maxiter=3000)
+    s.set_seed_update(0)
     s.set_bulk_copy(1)
     s.set_csr(H.rowptr, H.col, H.val)
     good = s.solve(b, z)
@@ -104,8 +106,9 @@ def test_bounded_wait_reports_timeout_and_context_recovers():
 
 @pytest.mark.parametrize("nleft,staged", [(16, True), (9, True), (8, False), (4, False)])
 def test_default_stages_only_many_projection_rows(nleft, staged):
-    """The default (-1) runs the staged kernel above 9 projection rows (b and
-    nleft left vectors), the plain one otherwise: it equals that choice bit for bit."""
+    """With the row-group update off (kw_set_seed_update(0)), the default (-1)
+    runs the staged kernel above 9 projection rows (b and nleft left vectors),
+    the plain one otherwise: it equals that choice bit for bit."""
     m = 4113
     H = _chain(m)
     b = w.gaussian_unit(m, 21)
@@ -114,6 +117,7 @@ def test_default_stages_only_many_projection_rows(nleft, staged):
     out = {}
     for mode in (-1, 1 if staged else 0):
         s = kw.Solver("df64", tol=1e-9, maxiter=8)
+        s.set_seed_update(0)
         s.set_bulk_copy(mode)
         s.set_csr(H.rowptr, H.col, H.val)
         out[mode] = s.solve(b, z, left=left, check=False).proj
