@@ -377,7 +377,6 @@ def _spectrum_err(proj, ref):
     return float(np.abs(A - Ar).max() / np.abs(Ar).max())
 
 
-FORMS_FULL = ("df64+x32", "df64", "f64")     # full mode: FP32 shift storage on the pair form, then the plain forms
 
 
 def _form(form):
@@ -429,15 +428,16 @@ def measure_configs(args, kw, wl, device, stream, ws, peak, peak_kind, h_res, t_
     KM = sum(int(q.z.size) * q.H.m for q in probs)
     c3 = {"workload": "anderson_batch48_L16-48_W2-16_K32-512_delta0.02-0.1_full_tol1e-8", "instances": len(probs),
           "sum_K_M": KM, "M_range": [min(q.H.m for q in probs), max(q.H.m for q in probs)],
-          "note": "one warm-up call and one timed call per form; updates = sum over instances of their "
-                  "sum_n K_active(n) x M_i"}
+          "note": "FP32-pair seed form with FP32 shift storage: one warm-up call and one timed call; FP64 "
+                  "form: one call; updates = sum over instances of their sum_n K_active(n) x M_i"}
     ref3 = None
-    for form in FORMS_FULL:
+    for form in ("df64+x32", "f64"):
         prec, x32 = _form(form)
         s = kw.Solver(prec, tol=1e-8, maxiter=200000)
         s.set_shift_storage(x32)
         h = s.prepare_batch(problems)
-        s.run_batch(h)
+        if ref3 is None:
+            s.run_batch(h)          # warm-up: child contexts, workspaces (the FP64 call's ~27 s dwarf them)
         rr, t = _timed(stream, lambda: s.run_batch(h))
         upd = sum(r.updates * q.H.m for r, q in zip(rr, probs))
         es = 0.0
@@ -547,6 +547,37 @@ def measure_configs(args, kw, wl, device, stream, ws, peak, peak_kind, h_res, t_
     return out
 
 
+def profile_workload(args, kw, device):
+    """Profiling mode on the other workloads: one solve capped at --profile-iters
+    iterations with tol 0 (every shift active), host-driven loop (each kernel an
+    ordinary stream launch)."""
+    import torch
+
+    from paper_2001_08707_gb300 import workloads as wl
+
+    prec = args.profile_prec or HEADLINE
+    if args.profile_workload == "j1j2_N20_full":
+        jm = wl.j1j2_chain(20, 1.0, 0.4, 0.2, seed=wl.SEED_BASE + 3)
+        H = jm.assemble()
+        lo, hi = wl.chain_bounds(H)
+        z = wl.shiftk_grid(lo - 0.5, hi + 0.5, 256, 0.05)
+        b = torch.as_tensor(wl.gaussian_unit(H.m, wl.SEED_BASE + 3), device=device)
+        s = kw.Solver(prec, tol=0.0, maxiter=args.profile_iters, use_graph=0)
+        s.set_csr(H.rowptr, H.col, H.val)
+        s.set_shift_storage(args.profile_x32)
+        r = s.solve(b, z, full=True, check=False)
+    else:   # anderson_L160: the contour workload, projected with 16 left vectors
+        pa = wl.anderson_contour()
+        s = kw.Solver(prec, tol=0.0, maxiter=args.profile_iters, use_graph=0)
+        s.set_csr(pa.H.rowptr, pa.H.col, pa.H.val)
+        r = s.solve(torch.as_tensor(pa.b, device=device), pa.z, left=torch.as_tensor(pa.left, device=device),
+                    check=False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": prec, "workload": args.profile_workload, "iters": r.iters, "status": r.status,
+                      "spmv_config": list(s.spmv_config())}))
+    return 0
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -563,6 +594,8 @@ def run_ours(args):
     from paper_2001_08707_gb300 import komega as kw
 
     kwbuild.build()
+    if args.profile_iters and args.profile_workload != "heisenberg_N24":
+        return profile_workload(args, kw, device)
     p = make_problem()
     m, nnz = p.H.m, p.H.nnz
     nleft = p.left.shape[0]
@@ -913,6 +946,10 @@ def main(argv=None):
                     help="precision form of the profiling-mode solve (default: the headline form)")
     ap.add_argument("--profile-op", choices=["csr", "spin"], default="csr",
                     help="profiling mode: the CSR input (default) or the same chain generated on the fly")
+    ap.add_argument("--profile-workload", choices=["heisenberg_N24", "j1j2_N20_full", "anderson_L160"],
+                    default="heisenberg_N24", help="profiling mode: the workload (default: the headline's)")
+    ap.add_argument("--profile-x32", action="store_true",
+                    help="profiling mode, j1j2_N20_full: FP32 storage of the shifted x/p (kw_set_shift_storage)")
     ap.add_argument("--profile-lanes", type=int, default=1,
                     help="SpMV lanes per row in profiling mode (the autotuner's timings are not "
                          "meaningful under a profiler; 1 is its pick on this workload)")

@@ -291,6 +291,36 @@ template <> __device__ __forceinline__ double azero<double>() { return 0.0; }
 template <> __device__ __forceinline__ float azero<float>() { return 0.f; }
 template <> __device__ __forceinline__ df azero<df>() { return {0.f, 0.f}; }
 
+// ------------------------------------------------------------- packed FP32 pairs (sm_100 and later)
+// The real and imaginary parts of a complex FP32 pair travel together in the
+// packed two-lane FP32 instructions (add/mul/fma .f32x2, round to nearest), so
+// one instruction does the same error-free step on both parts.  A complex pair
+// in this layout is {hi = (re.hi, im.hi), lo = (re.lo, im.lo)}.
+struct cpk {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ cpk cpk_of(dfc v) { return {make_float2(v.re.hi, v.im.hi), make_float2(v.re.lo, v.im.lo)}; }
+__device__ __forceinline__ cpk cpk_zero() { return {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+// acc += a * r for a real pair a and a complex pair r (both parts at once):
+// the rounded leading products are added exactly (TwoSum), the product errors
+// and the trailing terms go to acc.lo (normalised at the end), as acc_prod.
+__device__ __forceinline__ void acc_proj_pk(cpk& acc, df a, const cpk& r) {
+  const float2 ah = make_float2(a.hi, a.hi), al = make_float2(a.lo, a.lo);
+  const float2 p = pk_mul(ah, r.hi);
+  float2 e = pk_fma(ah, r.hi, make_float2(-p.x, -p.y));
+  e = pk_fma(ah, r.lo, e);
+  e = pk_fma(al, r.hi, e);
+  const float2 s = pk_add(acc.hi, p);
+  const float2 bb = pk_sub(s, acc.hi);
+  const float2 err = pk_add(pk_sub(acc.hi, pk_sub(s, bb)), pk_sub(p, bb));
+  acc.hi = s;
+  acc.lo = pk_add(acc.lo, pk_add(err, e));
+}
+
 #define KW_FULL_MASK 0xffffffffu
 __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(KW_FULL_MASK, v, o); }
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(KW_FULL_MASK, v, o); }

@@ -1217,7 +1217,7 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
   __shared__ double2 s_cf[3];
   __shared__ float4 s_pp[3];
   __shared__ int s_fail;
-  __shared__ dfc s_r1[kSeedTile];
+  __shared__ cpk s_r1[kSeedTile];   // r_{n+1} of the tile, packed (re, im) layout
   __shared__ df sw[N][8];
   __shared__ df red[N];
   __shared__ double all[N];
@@ -1230,9 +1230,9 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = threadIdx.x / 64, e0 = threadIdx.x % 64;
   df rho_re = azero<df>(), rho_im = azero<df>(), nu = azero<df>();
-  df pr[RPG], pim[RPG];
+  cpk pacc[RPG];   // (w_l.re, w_l.im) of this group's rows, packed pairs
 #pragma unroll
-  for (int j = 0; j < RPG; ++j) pr[j] = pim[j] = azero<df>();
+  for (int j = 0; j < RPG; ++j) pacc[j] = cpk_zero();
   const int ntiles = (m + kSeedTile - 1) / kSeedTile, nfull = m / kSeedTile, G = gridDim.x;
   const uint32_t sbytes = rg_stage_bytes(np), tx = sbytes + tx_pad;
   if (threadIdx.x == 0) {
@@ -1262,7 +1262,7 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
       if constexpr (METHOD == KW_METHOD_CG) acc_nrm(nu, r1);
       else acc_rho_nrm(rho_re, rho_im, nu, r1);
     }
-    s_r1[threadIdx.x] = r1;
+    s_r1[threadIdx.x] = cpk_of(r1);
     const bool staged = t < nfull;
     const int s = k % kRgStages;
     const bool late = staged && !mbar_wait(&bars[s], (uint32_t)(k / kRgStages) & 1u);
@@ -1281,13 +1281,13 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
     for (int jj = 0; jj < kSeedTile / 64; ++jj) {    // phase B: this group's rows over the tile
       const int e = e0 + 64 * jj, ie = base + e;
       if (ie < m) {
-        const dfc rv = s_r1[e];
+        const cpk rv = s_r1[e];
 #pragma unroll
         for (int j = 0; j < RPG; ++j) {
           const int l = g + kRowGroups * j;
           if (l < np) {
             const df a = staged ? sa[l * kSeedTile + e] : proj[(size_t)l * ld + ie];
-            acc_proj(pr[j], pim[j], a, rv);
+            acc_proj_pk(pacc[j], a, rv);
           }
         }
       }
@@ -1310,7 +1310,7 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
   }
 #pragma unroll
   for (int j = 0; j < RPG; ++j) {
-    const df a = warp_sum(anorm(pr[j])), b = warp_sum(anorm(pim[j]));
+    const df a = warp_sum(anorm(df{pacc[j].hi.x, pacc[j].lo.x})), b = warp_sum(anorm(df{pacc[j].hi.y, pacc[j].lo.y}));
 #pragma unroll
     for (int gg = 0; gg < kRowGroups; ++gg) {
       const int l = gg + kRowGroups * j;
@@ -1689,7 +1689,7 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
     const int i = chunk * blockDim.x + threadIdx.x;
     if (i < m) {
       const V ri = to_x(r1[i], (V*)nullptr);
-#pragma unroll 4
+#pragma unroll (XP32 ? 8 : 4)
       for (int s = 0; s < nts; ++s) {
         const size_t o = (size_t)ks[s] * m + i;
         V x = X[o], p = Pv[o];
