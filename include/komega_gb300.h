@@ -492,6 +492,19 @@ kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
  * few seconds (the context stays usable).  Errors: KW_ERR_ARG. */
 kw_status kw_set_bulk_copy(kw_ctx* ctx, int on);
 
+/* Tile of the full-mode x/p update (Eq. 23-24): the number of shifts one block
+ * item updates for a chunk of 256 rows, reading r_{n+1} once for them.
+ * shifts = 4, 8 or 16 forces that tile; 0 (default) times the three on the
+ * solve's own x/p buffers before they are initialised, once per form, shift
+ * storage, K and M, and keeps the fastest (every tile gives the same results).
+ * Applies from the next full-mode solve (kw_solve_batched instances
+ * included).  Errors: KW_ERR_ARG. */
+kw_status kw_set_update_tile(kw_ctx* ctx, int shifts);
+
+/* The x/p update tile of the last full-mode solve (0 before any).  Errors:
+ * KW_ERR_ARG (NULL pointer). */
+kw_status kw_get_update_tile(kw_ctx* ctx, int* shifts);
+
 /* Form of the three-term update kernel (Eq. 16 with rho, nu and P r_{n+1} of
  * Eq. 26) in the KW_DF64 form with the COCG or CG solver.  mode 1: two phases
  * per 256-element tile, r_{n+1} of each element first, then four thread groups

@@ -148,6 +148,11 @@ struct kw_ctx {
   int bulk = -1;  // kw_set_bulk_copy (-1: auto)
   int xp32 = 0;   // kw_set_shift_storage: full-mode x/p as complex FP32
   int seed_rg = -1;  // kw_set_seed_update: K2 row-group form (-1 auto)
+  int force_xp_tile = 0;      // kw_set_update_tile: 0 = timed, else 4, 8 or 16 shifts per K4 tile
+  int xp_tile_pick = 0;       // the timed pick and what it was timed on
+  long long xp_key[4] = {-1, -1, -1, -1};
+  int last_xp_tile = 0;       // the tile of the last full-mode solve
+  DBuf xp_st;                 // scratch state of the K4 timing
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -274,7 +279,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->mv_r, &ctx->mv_q, &ctx->mv_r2, &ctx->mv_q2, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->sp_table, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_sptr, &ctx->u_scol, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
-                  &ctx->rc_flag, &ctx->tune_fp};
+                  &ctx->rc_flag, &ctx->tune_fp, &ctx->xp_st};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
   if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
@@ -1140,6 +1145,68 @@ static cudaError_t iteration_launch(kw::Work& w, int parity, int first, cudaEven
   }
 }
 
+// K4's shift tile (4, 8 or 16 shifts per block item): timed once per form,
+// storage, K and M, on the solve's own x/p buffers before they are initialised
+// (the tile only decides which block updates which (shift, element) pair, so
+// every pick gives the same bits).  A scratch state marks the update pending
+// for all K shifts (the list is the identity, the coefficients zero); each
+// pick runs once untimed and three times timed, and a later pick replaces the
+// current one only if it is more than 5% faster.
+static kw_status tune_xp_tile(kw_ctx* ctx, kw::Work& w) {
+  if (!w.full) return KW_OK;
+  if (ctx->force_xp_tile > 0) {
+    w.xp_tile = ctx->force_xp_tile;
+    return KW_OK;
+  }
+  const long long key[4] = {w.prec, w.xp32, w.K, (long long)w.m};
+  if (ctx->xp_tile_pick > 0 && std::equal(key, key + 4, ctx->xp_key)) {
+    w.xp_tile = ctx->xp_tile_pick;
+    return KW_OK;
+  }
+  KW_CUDA(ctx->xp_st.ensure(sizeof(kw::State)), "update tile: scratch");
+  kw::State hs;
+  memset(&hs, 0, sizeof(hs));
+  hs.xp_pending = 1;
+  hs.n_list = w.K;
+  std::vector<int> iota((size_t)w.K);
+  for (int k = 0; k < w.K; ++k) iota[k] = k;
+  cudaStream_t st = ctx->stream;
+  KW_CUDA(cudaMemcpyAsync(w.list, iota.data(), (size_t)w.K * 4, cudaMemcpyHostToDevice, st), "update tile: list");
+  KW_CUDA(cudaMemsetAsync(w.coef, 0, (size_t)w.K * 48, st), "update tile: coefficients");
+  KW_CUDA(cudaMemsetAsync(w.coef_pair, 0, (size_t)w.K * 48, st), "update tile: coefficients");
+  ScopedEvents tev;
+  KW_CUDA(tev.create(2, cudaEventDefault), "update tile: events");
+  kw::State* sst = (kw::State*)ctx->xp_st.p;
+  const int opts[3] = {4, 8, 16};
+  float best = 1e30f;
+  int best_ts = 8;
+  for (int ts : opts) {
+    w.xp_tile = ts;
+    float tot = 0.f;
+    for (int rep = 0; rep < 4; ++rep) {   // every launch clears the pending flag: set it again first
+      KW_CUDA(cudaMemcpyAsync(sst, &hs, sizeof(hs), cudaMemcpyHostToDevice, st), "update tile: state");
+      KW_CUDA(cudaEventRecord(tev[0], st), "update tile: event");
+      cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_update_xp<kw::PREC_C32>(w, w.rA, sst, st)
+                      : w.prec == kw::PREC_DF ? kw::launch_update_xp<kw::PREC_DF>(w, w.rA, sst, st)
+                                              : kw::launch_update_xp<kw::PREC_F64>(w, w.rA, sst, st);
+      KW_CUDA(e, "update tile: launch");
+      KW_CUDA(cudaEventRecord(tev[1], st), "update tile: event");
+      KW_CUDA(cudaEventSynchronize(tev[1]), "update tile: sync");
+      float ms = 0.f;
+      KW_CUDA(cudaEventElapsedTime(&ms, tev[0], tev[1]), "update tile: time");
+      if (rep > 0) tot += ms;
+    }
+    if (tot < 0.95f * best) {
+      best = tot;
+      best_ts = ts;
+    }
+  }
+  w.xp_tile = best_ts;
+  ctx->xp_tile_pick = best_ts;
+  std::copy(key, key + 4, ctx->xp_key);
+  return KW_OK;
+}
+
 // Phase 1 of a solve: validate, tune, allocate, upload and enqueue the
 // initialisation (no synchronisation).  The descriptor is kept in ctx->work.
 static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host, int64_t nleft,
@@ -1167,6 +1234,9 @@ static kw_status solve_begin(kw_ctx* ctx, const double* b_dev, int64_t nshift, c
   if (s != KW_OK) return s;
   s = prepare(ctx, ctx->work, b_dev, nshift, z_host, nleft, left_dev, x_out_dev);
   if (s != KW_OK) return s;
+  s = tune_xp_tile(ctx, ctx->work);
+  if (s != KW_OK) return s;
+  if (ctx->work.full) ctx->last_xp_tile = ctx->work.xp_tile;
   ctx->work_K = nshift;
   cudaError_t ie = init_launch(ctx->work);   // ends with the first K1, which may call the callback
   if (ie != cudaSuccess) {
@@ -1583,6 +1653,7 @@ kw_status kw_solve_batched(kw_ctx* ctx, int64_t n, const kw_instance* inst, kw_s
     c->bulk = ctx->bulk;
     c->xp32 = ctx->xp32;
     c->seed_rg = ctx->seed_rg;
+    c->force_xp_tile = ctx->force_xp_tile;
     if (inst[i].tol > 0.0) c->opt.tol = inst[i].tol;
     c->run_maxiter = c->opt.maxiter;
     KW_CUDA(cudaStreamWaitEvent(c->stream, ev[n], 0), "batch wait");
@@ -1946,6 +2017,18 @@ kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user) {
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return KW_ERR_ARG;
   ctx->overlap = on;
+  return KW_OK;
+}
+
+kw_status kw_set_update_tile(kw_ctx* ctx, int shifts) {
+  if (!ctx || !(shifts == 0 || shifts == 4 || shifts == 8 || shifts == 16)) return KW_ERR_ARG;
+  ctx->force_xp_tile = shifts;
+  return KW_OK;
+}
+
+kw_status kw_get_update_tile(kw_ctx* ctx, int* shifts) {
+  if (!ctx || !shifts) return KW_ERR_ARG;
+  *shifts = ctx->last_xp_tile;
   return KW_OK;
 }
 

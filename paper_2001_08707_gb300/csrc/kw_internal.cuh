@@ -122,6 +122,7 @@ struct Work {
   int* list;
   void* X;           // full mode [K][m]
   void* P;           // full mode [K][m]
+  int xp_tile = 8;   // shifts per tile of K4 (4, 8 or 16; picked by the autotuner)
   int xp32 = 0;      // full mode: X and P stored as complex FP32 (float2) whatever the form; the
                      // projections then come from the projected recurrences (nproj = nout)
   // operator kind: CSR arrays (spmv_lanes picks the layout), callback, or generated on the fly
@@ -188,6 +189,9 @@ template <int P> cudaError_t launch_iteration(Work& w, int parity, int first, cu
 template <int P> cudaError_t launch_finish_x(Work& w);
 template <int P> cudaError_t launch_unfinish_x(Work& w);
 template <int P> cudaError_t launch_k1(Work& w, void* r, void* rt);
+// K4 on the Work's X, P for the compacted list, with the given state (the
+// solve's, or a scratch state when the autotuner times the tiles).
+template <int P> cudaError_t launch_update_xp(Work& w, const void* r1, State* st, cudaStream_t s);
 template <int P> cudaError_t launch_project_x(Work& w, double2* out);
 template <int P>
 cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, float4 zs_pair, double2* t_dev);

@@ -1689,7 +1689,7 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
     const int i = chunk * blockDim.x + threadIdx.x;
     if (i < m) {
       const V ri = to_x(r1[i], (V*)nullptr);
-#pragma unroll (XP32 ? 8 : 4)
+#pragma unroll (XP32 ? TS : 4)
       for (int s = 0; s < nts; ++s) {
         const size_t o = (size_t)ks[s] * m + i;
         V x = X[o], p = Pv[o];
@@ -2339,6 +2339,36 @@ static cudaError_t k1_dispatch(Work& w, void* r, void* rt) {
   return cudaGetLastError();
 }
 
+// K4 with w.xp_tile shifts per tile (4, 8 or 16; the autotuner's pick) on the
+// form's or the FP32 shift storage.  No more blocks than (shift tile, row
+// chunk) items at full activity: every block takes part in the arrival count,
+// so idle blocks would only add to it.
+template <int P, int TS, bool XP32>
+static cudaError_t update_xp_launch(Work& w, const void* r1, State* st, cudaStream_t s) {
+  typedef typename XT<P, XP32>::V XV;
+  typedef typename PT<P>::V V;
+  static int nblk_per_sm = 0;
+  const long long items = (long long)((w.K + TS - 1) / TS) * ((w.m + 255) / 256);
+  const int nblk = (int)std::max<long long>(
+      1, std::min<long long>(resident_blocks(nblk_per_sm, k_update_xp<P, TS, XP32>, 256, w.num_sms), items));
+  k_update_xp<P, TS, XP32><<<nblk, 256, 0, s>>>((int)w.m, w.list, w.coef, w.coef_pair, (XV*)w.X, (XV*)w.P,
+                                                  (const V*)r1, st);
+  return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_update_xp(Work& w, const void* r1, State* st, cudaStream_t s) {
+  const int ts = w.xp_tile;
+  if (w.xp32) {
+    if (ts == 4) return update_xp_launch<P, 4, true>(w, r1, st, s);
+    if (ts == 16) return update_xp_launch<P, 16, true>(w, r1, st, s);
+    return update_xp_launch<P, 8, true>(w, r1, st, s);
+  }
+  if (ts == 4) return update_xp_launch<P, 4, false>(w, r1, st, s);
+  if (ts == 16) return update_xp_launch<P, 16, false>(w, r1, st, s);
+  return update_xp_launch<P, 8, false>(w, r1, st, s);
+}
+
 // One iteration n on two streams (K1(n) was enqueued by the previous
 // iteration or by launch_init):
 //   stream:  [wait K3(n-1)] K2(n) [record ev_k2] K1(n+1)
@@ -2409,23 +2439,7 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   KW_MARK(4, s2);
   *launches += (w.mv_fn && P == PREC_DF) ? 4 : 3;
   if (w.full) {
-    static int nblk_xp_per_sm = 0;
-    // no more blocks than (shift tile, row chunk) items at full activity: every block takes part
-    // in the arrival count, so idle blocks would only add to it
-    const long long items = (long long)((w.K + 7) / 8) * ((w.m + 255) / 256);
-    if (w.xp32) {
-      static int nblk_xp32_per_sm = 0;
-      const int nblk_xp = (int)std::max<long long>(
-          1, std::min<long long>(resident_blocks(nblk_xp32_per_sm, k_update_xp<P, 8, true>, 256, w.num_sms), items));
-      k_update_xp<P, 8, true><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (float2*)w.X,
-                                                       (float2*)w.P, (const V*)rm, w.st);
-    } else {
-      const int nblk_xp = (int)std::max<long long>(
-          1, std::min<long long>(resident_blocks(nblk_xp_per_sm, k_update_xp<P, 8>, 256, w.num_sms), items));
-      k_update_xp<P, 8><<<nblk_xp, 256, 0, s2>>>((int)w.m, w.list, w.coef, w.coef_pair, (V*)w.X, (V*)w.P,
-                                                 (const V*)rm, w.st);
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_update_xp<P>(w, rm, w.st, s2)) != cudaSuccess) return e;
     *launches += 1;
   }
   KW_MARK(5, s2);

@@ -124,6 +124,8 @@ def load_library(path: str = LIB_PATH):
         "kw_set_bulk_copy": (C.c_int, [P, C.c_int]),
         "kw_set_shift_storage": (C.c_int, [P, C.c_int]),
         "kw_set_seed_update": (C.c_int, [P, C.c_int]),
+        "kw_set_update_tile": (C.c_int, [P, C.c_int]),
+        "kw_get_update_tile": (C.c_int, [P, C.POINTER(C.c_int)]),
         "kw_bilinear_c64": (C.c_int, [P, I64, I64, C.POINTER(kw_csr_term), I64, P, P, P]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
         "kw_resume": (C.c_int, [P, I64, P, C.POINTER(kw_solve_info)]),
@@ -587,6 +589,21 @@ class Solver:
             raise self._err(st, "kw_set_shift_storage")
         t = self._torch
         self.vec_dtype = t.complex64 if (fp32 or self.prec == KW_C32V_F64S) else t.complex128
+
+    def set_update_tile(self, shifts: int):
+        """kw_set_update_tile: shifts per tile of the x/p update (4, 8, 16), or 0
+        to time the three at the next full-mode solve (the default)."""
+        st = self._lib.kw_set_update_tile(self._ctx, int(shifts))
+        if st != KW_OK:
+            raise self._err(st, "kw_set_update_tile")
+
+    def update_tile(self) -> int:
+        """kw_get_update_tile: the x/p update tile of the last full-mode solve."""
+        v = C.c_int()
+        st = self._lib.kw_get_update_tile(self._ctx, C.byref(v))
+        if st != KW_OK:
+            raise self._err(st, "kw_get_update_tile")
+        return v.value
 
     def set_seed_update(self, mode: int):
         """kw_set_seed_update: 1 = the row-group form of the three-term update

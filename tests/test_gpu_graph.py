@@ -72,7 +72,11 @@ def test_device_loop_parity_with_oracle():
     s = kw.Solver("f64", tol=1e-10, use_graph=1)
     r, _, _, x = _solve(s, H, b, left, z, True)
     ref = oc.shifted_cocg(H.to_scipy(), b, z, left=left, tol=1e-10, full=True)
-    assert r.status == "KW_OK" and abs(r.iters - ref.iters) <= max(2, ref.iters // 50)
+    # about 420 iterations on a 216-row matrix: far past the loss of orthogonality,
+    # where the convergence delay depends on the rounding of every step (a change of
+    # FMA contraction in the FP64 scalars moves it by tens of iterations), so the
+    # count agrees within 5%; the error bound below is the parity check
+    assert r.status == "KW_OK" and abs(r.iters - ref.iters) <= max(2, ref.iters // 20)
     # both stop within tol of the exact solution: |x - x*| <= tol ||b|| / dist(z, spectrum) each
     err = np.abs(x - ref.x).max(axis=1) * np.abs(z.imag)
     assert err.max() < 4e-10, err.max()
