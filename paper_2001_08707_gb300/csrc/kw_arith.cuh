@@ -321,6 +321,68 @@ __device__ __forceinline__ void acc_proj_pk(cpk& acc, df a, const cpk& r) {
   acc.lo = pk_add(acc.lo, pk_add(err, e));
 }
 
+// A complex pair coefficient c in the two forms a packed product needs:
+// c * v = re * v + im * swap(v) with re = (c.re, c.re), im = (-c.im, c.im)
+// (lane 0 the real part, lane 1 the imaginary part).  pair: (re.hi, re.lo,
+// im.hi, im.lo); sign = -1 gives the coefficient of -c.
+struct cpk_coef {
+  cpk re, im;
+};
+__device__ __forceinline__ cpk_coef cpk_coef_of(float4 pair, float sign) {
+  const float rh = sign * pair.x, rl = sign * pair.y, ih = sign * pair.z, il = sign * pair.w;
+  return {{make_float2(rh, rh), make_float2(rl, rl)}, {make_float2(-ih, ih), make_float2(-il, il)}};
+}
+__device__ __forceinline__ cpk cpk_swap(const cpk& v) {
+  return {make_float2(v.hi.y, v.hi.x), make_float2(v.lo.y, v.lo.x)};
+}
+__device__ __forceinline__ dfc dfc_of(const cpk& v) { return {{v.hi.x, v.lo.x}, {v.hi.y, v.lo.y}}; }
+
+// One term x * y of a packed pair sum kept as (S exact sum of the rounded
+// leading products, L every error and trailing term): TwoProd of the leading
+// parts, TwoSum into S, the cross terms into L (Dekker's form with one
+// normalisation at the end, as the sums of dfc products elsewhere).
+__device__ __forceinline__ void pk_term(float2& S, float2& L, const cpk& x, const cpk& y) {
+  const float2 p = pk_mul(x.hi, y.hi);
+  const float2 e = pk_fma(x.hi, y.hi, make_float2(-p.x, -p.y));
+  const float2 s = pk_add(S, p);
+  const float2 bb = pk_sub(s, S);
+  const float2 t = pk_add(pk_sub(S, pk_sub(s, bb)), pk_sub(p, bb));
+  S = s;
+  L = pk_add(L, pk_add(t, e));
+  L = pk_fma(x.hi, y.lo, L);
+  L = pk_fma(x.lo, y.hi, L);
+}
+
+// r_{n+1} = a r_n - b q - c r_{n-1} (Eq. 16) for complex pairs in one packed
+// sum of six products (na = a, nb = -b, nc = -c as cpk_coef), normalised once.
+__device__ __forceinline__ cpk three_term_pk(const cpk_coef& na, const cpk_coef& nb, const cpk_coef& nc,
+                                             const cpk& rn, const cpk& q, const cpk& rm) {
+  float2 S = pk_mul(na.re.hi, rn.hi);
+  float2 L = pk_fma(na.re.hi, rn.hi, make_float2(-S.x, -S.y));
+  L = pk_fma(na.re.hi, rn.lo, L);
+  L = pk_fma(na.re.lo, rn.hi, L);
+  pk_term(S, L, na.im, cpk_swap(rn));
+  pk_term(S, L, nb.re, q);
+  pk_term(S, L, nb.im, cpk_swap(q));
+  pk_term(S, L, nc.re, rm);
+  pk_term(S, L, nc.im, cpk_swap(rm));
+  const float2 h = pk_add(S, L);
+  return {h, pk_sub(L, pk_sub(h, S))};   // Fast2Sum: (h, error)
+}
+
+// acc += (x.re^2, x.im^2) for a complex pair x (lanes: the squares of the two parts)
+__device__ __forceinline__ void acc_sq_pk(cpk& acc, const cpk& x) {
+  const float2 p = pk_mul(x.hi, x.hi);
+  float2 e = pk_fma(x.hi, x.hi, make_float2(-p.x, -p.y));
+  const float2 two_lo = pk_add(x.lo, x.lo);
+  e = pk_fma(x.hi, two_lo, e);                       // 2 hi lo
+  const float2 s = pk_add(acc.hi, p);
+  const float2 bb = pk_sub(s, acc.hi);
+  const float2 err = pk_add(pk_sub(acc.hi, pk_sub(s, bb)), pk_sub(p, bb));
+  acc.hi = s;
+  acc.lo = pk_add(acc.lo, pk_add(err, e));
+}
+
 #define KW_FULL_MASK 0xffffffffu
 __device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(KW_FULL_MASK, v, o); }
 __device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(KW_FULL_MASK, v, o); }

@@ -1012,8 +1012,50 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
   for (int i = 0; i < N; ++i) chunk[i] = tot[i] = azero<A>();
   int in_chunk = 0;
   const int stride = gridDim.x * blockDim.x;
+  // The pair form (COCG, CG) runs the update in packed FP32x2 pair arithmetic:
+  // Eq. 16 as one six-product sum with one normalisation, (re^2, im^2) for rho
+  // and nu, re*im for Im rho, and (re, im) of every projection at once.  The
+  // coefficients' packed forms sit in shared memory and are re-read per element.
+  constexpr bool PK = P == PREC_DF && METHOD != KW_METHOD_BICG;
+  __shared__ float4 s_ck[PK ? 6 : 1];     // cpk_coef of a, -b, -c: (re.hi, re.lo, im.hi, im.lo) per part
+  if constexpr (PK) {
+    if (threadIdx.x < 3) {
+      const cpk_coef ck = cpk_coef_of(s_pp[threadIdx.x], threadIdx.x == 0 ? 1.f : -1.f);
+      s_ck[2 * threadIdx.x] = make_float4(ck.re.hi.x, ck.re.hi.y, ck.re.lo.x, ck.re.lo.y);
+      s_ck[2 * threadIdx.x + 1] = make_float4(ck.im.hi.x, ck.im.hi.y, ck.im.lo.x, ck.im.lo.y);
+    }
+    __syncthreads();
+  }
+  const volatile float4* vck = s_ck;
+  cpk sq = cpk_zero();            // packed: (sum re^2, sum im^2)
+  df x2 = azero<df>();            // sum re * im
+  cpk pp[PK && NP > 0 ? NP : 1];  // packed (re, im) of each projection
+#pragma unroll
+  for (int l = 0; l < (PK && NP > 0 ? NP : 1); ++l) pp[l] = cpk_zero();
+  auto element_pk = [&](const V& rnv, const V& qvv, const V& rmv, const R* av, int i, bool has) {
+    if constexpr (PK) {
+      cpk_coef ck[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float4 a = make_float4(vck[2 * c].x, vck[2 * c].y, vck[2 * c].z, vck[2 * c].w);
+        const float4 b = make_float4(vck[2 * c + 1].x, vck[2 * c + 1].y, vck[2 * c + 1].z, vck[2 * c + 1].w);
+        ck[c] = {{make_float2(a.x, a.y), make_float2(a.z, a.w)}, {make_float2(b.x, b.y), make_float2(b.z, b.w)}};
+      }
+      const cpk r1 = three_term_pk(ck[0], ck[1], ck[2], cpk_of(rnv), cpk_of(qvv), cpk_of(rmv));   // Eq. 16
+      if (has) rm_buf[i] = dfc_of(r1);
+      acc_sq_pk(sq, r1);
+      if constexpr (METHOD != KW_METHOD_CG) acc_prod(x2, df{r1.hi.x, r1.lo.x}, df{r1.hi.y, r1.lo.y});
+#pragma unroll
+      for (int l = 0; l < NP; ++l)
+        if (l < np) acc_proj_pk(pp[l], av[l], r1);
+    }
+  };
   // Eq. 16 for element i and its contributions to the dots (nothing stored when !has).
   auto element = [&](const V& rnv, const V& qvv, const V& rmv, const R* av, int i, bool has) {
+    if constexpr (PK) {
+      element_pk(rnv, qvv, rmv, av, i, has);
+      return;
+    }
     float4 pa, pb, pc;
     if constexpr (P == PREC_DF) {
       pa = make_float4(vpp[0].x, vpp[0].y, vpp[0].z, vpp[0].w);
@@ -1144,6 +1186,17 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
       close_chunk(ILP);
     }
   }
+  if constexpr (PK) {   // the packed sums in the layout of the reduction below
+    const df re2 = anorm(df{sq.hi.x, sq.lo.x}), im2 = anorm(df{sq.hi.y, sq.lo.y});
+    chunk[0] = df_sub(re2, im2);                       // Re r^T r
+    chunk[1] = df{2.f * x2.hi, 2.f * x2.lo};           // Im r^T r
+    chunk[2] = df_add(re2, im2);                       // ||r||^2
+#pragma unroll
+    for (int l = 0; l < NP; ++l) {
+      chunk[3 + 2 * l] = df{pp[l].hi.x, pp[l].lo.x};
+      chunk[4 + 2 * l] = df{pp[l].hi.y, pp[l].lo.y};
+    }
+  }
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     if (CHUNKED) aadd(tot[k], chunk[k]);
@@ -1224,12 +1277,13 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
   seed_coefficients(st, parity, s_sc, s_cf, s_pp, &s_fail);
   __syncthreads();
   if (s_fail) return;
-  const dfc ca = vscalar<dfc>(s_cf[0], s_pp[0]), cb = vscalar<dfc>(s_cf[1], s_pp[1]);
-  const dfc cc = vscalar<dfc>(s_cf[2], s_pp[2]);
+  // packed forms of the three coefficients a, -b, -c (cpk_coef), in registers
+  const cpk_coef na = cpk_coef_of(s_pp[0], 1.f), nb = cpk_coef_of(s_pp[1], -1.f), nc = cpk_coef_of(s_pp[2], -1.f);
   const int n = 3 + 2 * np;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = threadIdx.x / 64, e0 = threadIdx.x % 64;
-  df rho_re = azero<df>(), rho_im = azero<df>(), nu = azero<df>();
+  cpk sq = cpk_zero();            // packed (sum re^2, sum im^2)
+  df x2 = azero<df>();            // sum re * im
   cpk pacc[RPG];   // (w_l.re, w_l.im) of this group's rows, packed pairs
 #pragma unroll
   for (int j = 0; j < RPG; ++j) pacc[j] = cpk_zero();
@@ -1254,15 +1308,14 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
   for (int t = blockIdx.x; t < ntiles; t += G, ++k) {
     const int base = t * kSeedTile;
     const int i = base + (int)threadIdx.x;
-    dfc r1 = vzero<dfc>();
-    if (i < m) {                                      // phase A: Eq. 16 for one element
-      const dfc rnv = rn_buf[i], qv = q[i], rmv = rm_buf[i];
-      r1 = csub(csub(cmul(ca, rnv), cmul(cb, qv)), cmul(cc, rmv));
-      rm_buf[i] = r1;
-      if constexpr (METHOD == KW_METHOD_CG) acc_nrm(nu, r1);
-      else acc_rho_nrm(rho_re, rho_im, nu, r1);
+    cpk r1 = cpk_zero();
+    if (i < m) {                                      // phase A: Eq. 16 for one element (packed pairs)
+      r1 = three_term_pk(na, nb, nc, cpk_of(rn_buf[i]), cpk_of(q[i]), cpk_of(rm_buf[i]));
+      rm_buf[i] = dfc_of(r1);
+      acc_sq_pk(sq, r1);
+      if constexpr (METHOD != KW_METHOD_CG) acc_prod(x2, df{r1.hi.x, r1.lo.x}, df{r1.hi.y, r1.lo.y});
     }
-    s_r1[threadIdx.x] = cpk_of(r1);
+    s_r1[threadIdx.x] = r1;
     const bool staged = t < nfull;
     const int s = k % kRgStages;
     const bool late = staged && !mbar_wait(&bars[s], (uint32_t)(k / kRgStages) & 1u);
@@ -1301,7 +1354,9 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
   // block sums: one pair per warp and value (a warp lies in one row group; it
   // contributes zero to the other groups' rows), then the eight warps in order
   {
-    const df r0 = warp_sum(anorm(rho_re)), r1v = warp_sum(anorm(rho_im)), r2 = warp_sum(anorm(nu));
+    const df re2 = anorm(df{sq.hi.x, sq.lo.x}), im2 = anorm(df{sq.hi.y, sq.lo.y});
+    const df r0 = warp_sum(anorm(df_sub(re2, im2))), r1v = warp_sum(anorm(df{2.f * x2.hi, 2.f * x2.lo}));
+    const df r2 = warp_sum(anorm(df_add(re2, im2)));
     if (lane == 0) {
       sw[0][warp] = r0;
       sw[1][warp] = r1v;
