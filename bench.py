@@ -527,6 +527,8 @@ def measure_configs(args, kw, wl, device, stream, ws, peak, peak_kind, h_res, t_
         vb, rb = PREC_BYTES[prec]
         k1b = survey_spmv_bytes(pa.H.m, pa.H.nnz, vb, 4 if prec == "c32" else 8)
         k2b = seed_bytes(pa.H.m, vb, rb, pa.left.shape[0] + 1)
+        if prec == "df64":
+            c5["df64_seed_update_traffic"] = recorded_traffic("k_seed_update_rg<df64>:anderson_L160")
         c5[f"{prec}_iteration_sample"] = {
             "iterations": ra.iters, "us_per_iteration": 1e3 * ta / ra.iters,
             "updates_per_s_at_full_activity": ws * ra.updates * pa.H.m / (ta * 1e-3),
@@ -835,6 +837,8 @@ def run_ours(args):
         xp_bytes = 4 * es * 256 * Hj.m + PREC_BYTES[prec][0] * Hj.m * (256 // 8)
         gbs = xp_bytes / (k[3] * 1e-3) / 1e9
         ent = {"k_update_xp_us": 1e3 * k[3], "bytes": xp_bytes, "gbs": gbs, "sampled_iterations": ti}
+        if form == "df64+x32":
+            ent["traffic"] = recorded_traffic("k_update_xp<df64x32>:j1j2_N20")
         if form == "f64":   # complex FP64: x += alpha p (8 flops), p = r (1/pi) + beta p (14 flops)
             tf = 22 * 256 * Hj.m / (k[3] * 1e-3) / 1e12
             ent["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
