@@ -311,6 +311,28 @@ ORACLE_ITERS = 12          # oracle iterations per step of the reference arm
 BASELINE_ITERS = 30        # oracle iterations in the cpu_baseline sample (about 10-30 s)
 
 
+def conventional_context():
+    """Table 2's first row on the Anderson cube L=10 (M=1000, K=64, full x): the oracle's
+    shifted solve of all 64 shifts against the conventional approach, 64 independent
+    single-shift solves (timed on 8 of them, scaled to 64), one core."""
+    from oracle import shifted_cocg as oc
+    from paper_2001_08707_gb300 import workloads as wl
+
+    p1 = wl.anderson_small()
+    Hs = p1.H.to_scipy()
+    t0 = time.perf_counter()
+    r = oc.shifted_cocg(Hs, p1.b, p1.z, tol=p1.tol, full=True)
+    shifted = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prods = 0
+    for zk in p1.z[::8]:
+        prods += oc.shifted_cocg(Hs, p1.b, np.array([zk]), tol=p1.tol, full=True).iters
+    conv = (time.perf_counter() - t0) * 8
+    return {"workload": "anderson_L10_M1000_K64_full_tol1e-10", "oracle_shifted_solve_s": shifted,
+            "oracle_shifted_products": int(r.iters), "oracle_64_single_shift_solves_s_est": conv,
+            "oracle_single_shift_products_est": int(prods * 8), "cores": 1}
+
+
 def cpu_baseline(p):
     cores = host_cores()
     r = oracle_timing(p, BASELINE_ITERS, 1, cores)[0]
@@ -318,7 +340,8 @@ def cpu_baseline(p):
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {r['iters']} iterations of the same workload (all {p.z.size} shifts active) in "
                       f"{cores} concurrent oracle processes, one per host core (numpy/scipy FP64, BLAS threads 1 "
-                      f"each); {r['seconds']:.1f} s wall for all of them"}
+                      f"each); {r['seconds']:.1f} s wall for all of them",
+            "conventional_context": conventional_context()}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -420,6 +443,26 @@ def measure_configs(args, kw, wl, device, stream, ws, peak, peak_kind, h_res, t_
         c1[form] = {"value": ws * r.updates * p1.H.m / (t * 1e-3), "ms": t, "iters": r.iters,
                     "us_per_iteration": 1e3 * t / r.iters, "status": r.status,
                     "spectrum_rel_err_vs_f64": _spectrum_err(r.proj, ref1)}
+    # Table 2's first row as context: the conventional approach, K independent single-shift solves
+    # (one product per shift per iteration), on the GPU (FP32 pairs, all 64) and in the oracle on one
+    # host core (8 of the 64 shifts, scaled to 64), beside the oracle's shifted solve of all 64
+    s = kw.Solver("df64", tol=p1.tol, maxiter=200000, use_graph=1)
+    s.set_csr(p1.H.rowptr, p1.H.col, p1.H.val)
+    x1 = torch.empty((1, p1.H.m), dtype=s.vec_dtype, device=device)
+    s.solve(b1, p1.z[:1], full=True, x_out=x1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its = 0
+    for zk in p1.z:
+        its += s.solve(b1, [zk], full=True, x_out=x1).iters
+    torch.cuda.synchronize()
+    conv_gpu = time.perf_counter() - t0
+    s.close()
+    c1["conventional_context"] = {
+        "gpu_df64_64_single_shift_solves_s": conv_gpu, "gpu_products": its,
+        "gpu_df64_shifted_solve_s": c1["df64"]["ms"] * 1e-3, "gpu_shifted_products": c1["df64"]["iters"],
+        "note": "Table 2 row 1 (K independent solves: one product per shift per iteration) against the "
+                "shifted solve (one product per iteration); the oracle's two timings are in cpu_baseline"}
     out["1_anderson_L10"] = c1
 
     # -- 3: 48 uneven Anderson cubes, full x, tol 1e-8, one kw_solve_batched call (one CUDA graph)
