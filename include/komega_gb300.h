@@ -607,6 +607,21 @@ kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* 
 kw_status kw_bilinear_c64(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms_host, int64_t nshift,
                           const void* X_dev, const void* Y_dev, kw_c128* out_host);
 
+/* Linear combinations of the full-mode solutions over the shifts:
+ *     S[k][i] = sum_j W[k][j] x_j[i],   k < nk, j < nshift,
+ * the form of the contour moments of Sec. 4.1, s_k = sum_j w_j (z_j - gamma)^k x_j
+ * (trapezoid rule on the circle), formed on the device so that only the nk
+ * moment vectors, not the nshift solutions, need to leave it.
+ *   X_dev: [nshift][m] device solutions, element x_elem (KW_ELEM_C128, or
+ *   KW_ELEM_C64 for complex FP32 from the FP32 form or FP32 shift storage);
+ *   W_host: kw_c128 [nk][nshift] weights (1 <= nk <= 16);
+ *   S_dev: kw_c128 [nk][m] device output.
+ * FP64 sums in a fixed order; returns after synchronising the context's
+ * stream.  Errors: KW_ERR_ARG (sizes, element type, NULL pointers), KW_ERR_OOM,
+ * KW_ERR_CUDA. */
+kw_status kw_shift_combine(kw_ctx* ctx, int64_t m, int64_t nshift, const void* X_dev, int x_elem, int64_t nk,
+                           const kw_c128* W_host, kw_c128* S_dev);
+
 /* Most thread blocks kw_spmv_dot_noalloc launches; its static scratch holds
  * one FP64 complex partial per block (64 KiB) plus a counter and the result. */
 #define KW_NOALLOC_MAX_BLOCKS 4096

@@ -153,6 +153,7 @@ struct kw_ctx {
   long long xp_key[4] = {-1, -1, -1, -1};
   int last_xp_tile = 0;       // the tile of the last full-mode solve
   DBuf xp_st;                 // scratch state of the K4 timing
+  DBuf comb_w;                // weights of kw_shift_combine
   kw_stats stats = {};
   // phases of a solve
   kw::Work work;
@@ -279,7 +280,7 @@ void kw_destroy(kw_ctx* ctx) {
                   &ctx->mv_r, &ctx->mv_q, &ctx->mv_r2, &ctx->mv_q2, &ctx->rtA, &ctx->rtB, &ctx->qt, &ctx->sp_binom, &ctx->sp_basis, &ctx->sp_bond, &ctx->sp_J,
                   &ctx->sp_h, &ctx->sp_val, &ctx->sp_table, &ctx->g_diag64, &ctx->g_diag32, &ctx->g_diagpair, &ctx->u_fm, &ctx->u_dcount, &ctx->u_scratch, &ctx->u_rowptr,
                   &ctx->u_col, &ctx->u_sptr, &ctx->u_scol, &ctx->u_diag64, &ctx->u_diag32, &ctx->u_diagpair, &ctx->klog, &ctx->rc_log, &ctx->rc_w0, &ctx->rc_z, &ctx->rc_proj, &ctx->rc_conv, &ctx->rc_res,
-                  &ctx->rc_flag, &ctx->tune_fp, &ctx->xp_st};
+                  &ctx->rc_flag, &ctx->tune_fp, &ctx->xp_st, &ctx->comb_w};
   for (DBuf* b : bufs) b->release();
   for (kw_ctx* c : ctx->children) kw_destroy(c);
   if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
@@ -1877,6 +1878,22 @@ kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* 
 kw_status kw_bilinear_c64(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms, int64_t nshift,
                           const void* X_dev, const void* Y_dev, kw_c128* out_host) {
   return bilinear(ctx, "kw_bilinear_c64", m, nterm, terms, nshift, X_dev, Y_dev, 1, out_host);
+}
+
+kw_status kw_shift_combine(kw_ctx* ctx, int64_t m, int64_t nshift, const void* X_dev, int x_elem, int64_t nk,
+                           const kw_c128* W_host, kw_c128* S_dev) {
+  if (!ctx) return KW_ERR_ARG;
+  if (m < 1 || m > KW_MAX_ROWS || nshift < 1 || nshift > 0x7fffffffLL || nk < 1 || nk > kw::kMaxCombine || !X_dev ||
+      !W_host || !S_dev || (x_elem != KW_ELEM_C128 && x_elem != KW_ELEM_C64))
+    return fail(ctx, KW_ERR_ARG, "kw_shift_combine: invalid sizes, element type or NULL pointer");
+  KW_CUDA(ctx->comb_w.ensure((size_t)nk * nshift * 16), "kw_shift_combine: weights");
+  KW_CUDA(cudaMemcpyAsync(ctx->comb_w.p, W_host, (size_t)nk * nshift * 16, cudaMemcpyHostToDevice, ctx->stream),
+          "kw_shift_combine: upload");
+  KW_CUDA(kw::launch_shift_combine((int)m, (int)nshift, (int)nk, X_dev, x_elem == KW_ELEM_C64 ? 1 : 0,
+                                   (const double2*)ctx->comb_w.p, (double2*)S_dev, ctx->num_sms, ctx->stream),
+          "kw_shift_combine: launch");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_shift_combine: sync");
+  return KW_OK;
 }
 
 kw_status kw_set_krylov_log(kw_ctx* ctx, int64_t max_iters) {

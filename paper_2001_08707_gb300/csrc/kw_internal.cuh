@@ -253,6 +253,11 @@ cudaError_t launch_loop_cond(const int* count, int target, unsigned* loop, cudaG
 
 // Adjoint bilinear forms (kw_bilinear): shifts per tile and the launcher.
 constexpr int kBilinearTile = 8;
+// Combinations over the shifts (kw_shift_combine): S [nk][m] = W [nk][K] X [K][m],
+// X kw_c128 (x32 = 0) or complex FP32 (x32 = 1), W and S FP64 complex; nk <= kMaxCombine.
+constexpr int kMaxCombine = 16;
+cudaError_t launch_shift_combine(int m, int K, int nk, const void* X, int x32, const double2* W, double2* S,
+                                 int num_sms, cudaStream_t s);
 // X, Y: [K][m] kw_c128 (x32 = 0) or complex FP32 (x32 = 1).
 cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val, const void* X,
                             const void* Y, int x32, int nblk, double2* part, int term, int nterm, double2* out,

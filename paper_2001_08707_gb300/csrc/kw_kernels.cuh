@@ -1831,6 +1831,50 @@ __global__ void k_bilinear_reduce(int K, int nblk, int term, int nterm, const do
   out[(size_t)k * nterm + term] = s;
 }
 
+// ================================================================ combinations over the shifts
+// S[k][i] = sum_j W[k][j] x_j[i] for k < nk <= NK (the contour moments of
+// Sec. 4.1 are such combinations): one thread per element i (grid-stride),
+// the weights staged in shared memory 64 shifts at a time, x_j[i] read
+// coalesced and widened to FP64, FP64 complex sums in a fixed order.
+constexpr int kCombineChunk = 64;
+
+template <int NK, class XV>
+__global__ void __launch_bounds__(256)
+k_shift_combine(int m, int K, int nk, const XV* __restrict__ X, const double2* __restrict__ W,
+                double2* __restrict__ S) {
+  __shared__ double2 sw[NK][kCombineChunk];
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < m; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    double2 acc[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int j0 = 0; j0 < K; j0 += kCombineChunk) {
+      const int nj = min(kCombineChunk, K - j0);
+      __syncthreads();
+      for (int t = threadIdx.x; t < NK * kCombineChunk; t += blockDim.x) {
+        const int k = t / kCombineChunk, j = t % kCombineChunk;
+        sw[k][j] = (k < nk && j < nj) ? W[(size_t)k * K + j0 + j] : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      if (i < m) {
+        for (int j = 0; j < nj; ++j) {
+          const double2 x = wide(X[(size_t)(j0 + j) * m + i]);
+#pragma unroll
+          for (int k = 0; k < NK; ++k) {
+            const double2 w = sw[k][j];
+            acc[k].x = fma(w.x, x.x, fma(-w.y, x.y, acc[k].x));
+            acc[k].y = fma(w.x, x.y, fma(w.y, x.x, acc[k].y));
+          }
+        }
+      }
+    }
+    if (i < m)
+#pragma unroll
+      for (int k = 0; k < NK; ++k)
+        if (k < nk) S[(size_t)k * m + i] = acc[k];
+  }
+}
+
 // ================================================================ initialisation
 template <int P>
 __global__ void k_init_vectors(int m, int np, const double* __restrict__ b, const double* __restrict__ left,

@@ -120,6 +120,19 @@ cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col,
   return cudaGetLastError();
 }
 
+cudaError_t launch_shift_combine(int m, int K, int nk, const void* X, int x32, const double2* W, double2* S,
+                                 int num_sms, cudaStream_t s) {
+  const int grid = std::max(1, std::min(8 * num_sms, (m + 255) / 256));
+  if (nk <= 8) {
+    if (x32) k_shift_combine<8, float2><<<grid, 256, 0, s>>>(m, K, nk, (const float2*)X, W, S);
+    else k_shift_combine<8, double2><<<grid, 256, 0, s>>>(m, K, nk, (const double2*)X, W, S);
+  } else {
+    if (x32) k_shift_combine<kMaxCombine, float2><<<grid, 256, 0, s>>>(m, K, nk, (const float2*)X, W, S);
+    else k_shift_combine<kMaxCombine, double2><<<grid, 256, 0, s>>>(m, K, nk, (const double2*)X, W, S);
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- uniform off-diagonal layout
 // fm[0]: smallest index of an off-diagonal entry (ULLONG_MAX if none);
 // fm[1]: off-diagonal entries whose value differs bitwise from that entry's.

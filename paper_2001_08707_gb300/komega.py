@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
         "kw_set_shift_storage": (C.c_int, [P, C.c_int]),
         "kw_set_seed_update": (C.c_int, [P, C.c_int]),
         "kw_set_update_tile": (C.c_int, [P, C.c_int]),
+        "kw_shift_combine": (C.c_int, [P, I64, I64, P, C.c_int, I64, P, P]),
         "kw_get_update_tile": (C.c_int, [P, C.POINTER(C.c_int)]),
         "kw_bilinear_c64": (C.c_int, [P, I64, I64, C.POINTER(kw_csr_term), I64, P, P, P]),
         "kw_set_method": (C.c_int, [P, C.c_int, P]),
@@ -742,6 +743,25 @@ class Solver:
         rowptr, col, val arrays), b, z and optionally left, full (default True) and
         tol.  Returns one SolveResult per problem."""
         return self.run_batch(self.prepare_batch(problems), check)
+
+    def shift_combine(self, X, W):
+        """kw_shift_combine: S = W X on the device for X a [K, m] complex128 or
+        complex64 CUDA tensor and W a [nk, K] complex array (nk <= 16); returns the
+        [nk, m] complex128 CUDA tensor S."""
+        t = self._torch
+        if X.dtype not in (t.complex128, t.complex64) or not X.is_cuda or not X.is_contiguous() or X.dim() != 2:
+            raise ValueError("X must be a contiguous [K, m] complex128 or complex64 CUDA tensor")
+        K, m = X.shape
+        Wh = np.ascontiguousarray(np.asarray(W, dtype=np.complex128))
+        if Wh.ndim != 2 or Wh.shape[1] != K:
+            raise ValueError(f"W must be [nk, {K}]")
+        S = t.empty((Wh.shape[0], m), dtype=t.complex128, device=X.device)
+        elem = KW_ELEM_C64 if X.dtype == t.complex64 else KW_ELEM_C128
+        st = self._lib.kw_shift_combine(self._ctx, m, K, C.c_void_p(X.data_ptr()), elem, Wh.shape[0],
+                                        Wh.ctypes.data_as(C.c_void_p), C.c_void_p(S.data_ptr()))
+        if st != KW_OK:
+            raise self._err(st, "kw_shift_combine")
+        return S
 
     def bilinear(self, terms, X, Y=None) -> np.ndarray:
         """kw_bilinear / kw_bilinear_c64: out[k][t] = y_k^T H_t x_k for device CSR terms
