@@ -141,8 +141,8 @@ struct kw_ctx {
   int64_t timing_every = 0;
   cudaEvent_t kev[2][6] = {};
   // second stream of a solve (shift scalars and x/p update) and its ordering events
-  cudaStream_t stream2 = nullptr;
-  cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr;
+  cudaStream_t stream2 = nullptr, stream3 = nullptr;
+  cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr, ev_k4[2] = {nullptr, nullptr};
   DBuf part_k1;   // K1's block partials (K1 overlaps K3, which uses part)
   int overlap = 1;
   int bulk = -1;  // kw_set_bulk_copy (-1: auto)
@@ -302,7 +302,10 @@ void kw_destroy(kw_ctx* ctx) {
   }
   if (ctx->ev_k2) cudaEventDestroy(ctx->ev_k2);
   if (ctx->ev_k3) cudaEventDestroy(ctx->ev_k3);
+  for (cudaEvent_t e : ctx->ev_k4)
+    if (e) cudaEventDestroy(e);
   if (ctx->stream2) cudaStreamDestroy(ctx->stream2);
+  if (ctx->stream3) cudaStreamDestroy(ctx->stream3);
   delete ctx;
 }
 
@@ -1029,14 +1032,14 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
       {&ctx->active, Ks * 4},
       {&ctx->conv_iter, Ks * 8},
       {&ctx->final_res, Ks * 8},
-      {&ctx->coef, Ks * 48},
-      {&ctx->coef_pair, Ks * 48},
+      {&ctx->coef, 2 * Ks * 48},        // two parity slots: K4(n) reads one while K3(n+1) writes the other
+      {&ctx->coef_pair, 2 * Ks * 48},
       {&ctx->Y, Ks * npw * 16},
       {&ctx->U, Ks * npw * 16},
       {&ctx->w, (size_t)KW_MAX_PROJ * 16},
       {&ctx->w0, (size_t)KW_MAX_PROJ * 16},
       {&ctx->hist, std::max<size_t>((size_t)nrecmax * Ks, 1) * 8},
-      {&ctx->list, Ks * 4},
+      {&ctx->list, 2 * Ks * 4},
       {&ctx->P, w.full ? Ks * Ms * (w.xp32 ? 8 : vs) : 16},
       {&ctx->part, part_d * 8},
       {&ctx->part_k1, part_d * 8},
@@ -1090,11 +1093,22 @@ static kw_status prepare(kw_ctx* ctx, kw::Work& w, const double* b_dev, int64_t 
     KW_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
     KW_CUDA(cudaStreamCreateWithPriority(&ctx->stream2, cudaStreamNonBlocking, hi), "second stream");
   }
+  if (!ctx->stream3) {   // lowest priority: K4 fills the SMs that the next iteration's K2 and K1 leave free
+    int lo = 0, hi = 0;
+    KW_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities");
+    KW_CUDA(cudaStreamCreateWithPriority(&ctx->stream3, cudaStreamNonBlocking, lo), "third stream");
+  }
   if (!ctx->ev_k2) KW_CUDA(cudaEventCreateWithFlags(&ctx->ev_k2, cudaEventDisableTiming), "stream events");
   if (!ctx->ev_k3) KW_CUDA(cudaEventCreateWithFlags(&ctx->ev_k3, cudaEventDisableTiming), "stream events");
+  for (cudaEvent_t& e : ctx->ev_k4)
+    if (!e) KW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "stream events");
   w.stream2 = ctx->stream2;
+  w.stream3 = ctx->stream3;
   w.ev_k2 = ctx->ev_k2;
   w.ev_k3 = ctx->ev_k3;
+  w.ev_k4[0] = ctx->ev_k4[0];
+  w.ev_k4[1] = ctx->ev_k4[1];
+  w.k4_mask = 0;
   w.overlap = ctx->rci_active ? 0 : ctx->overlap;   // one step per call under reverse communication
 
   KW_CUDA(cudaMemcpyAsync(w.z, z_host, K * 16, cudaMemcpyHostToDevice, ctx->stream), "upload shifts");
@@ -1167,8 +1181,8 @@ static kw_status tune_xp_tile(kw_ctx* ctx, kw::Work& w) {
   KW_CUDA(ctx->xp_st.ensure(sizeof(kw::State)), "update tile: scratch");
   kw::State hs;
   memset(&hs, 0, sizeof(hs));
-  hs.xp_pending = 1;
-  hs.n_list = w.K;
+  hs.xp_pending[0] = 1;
+  hs.n_list[0] = w.K;
   std::vector<int> iota((size_t)w.K);
   for (int k = 0; k < w.K; ++k) iota[k] = k;
   cudaStream_t st = ctx->stream;
@@ -1187,9 +1201,9 @@ static kw_status tune_xp_tile(kw_ctx* ctx, kw::Work& w) {
     for (int rep = 0; rep < 4; ++rep) {   // every launch clears the pending flag: set it again first
       KW_CUDA(cudaMemcpyAsync(sst, &hs, sizeof(hs), cudaMemcpyHostToDevice, st), "update tile: state");
       KW_CUDA(cudaEventRecord(tev[0], st), "update tile: event");
-      cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_update_xp<kw::PREC_C32>(w, w.rA, sst, st)
-                      : w.prec == kw::PREC_DF ? kw::launch_update_xp<kw::PREC_DF>(w, w.rA, sst, st)
-                                              : kw::launch_update_xp<kw::PREC_F64>(w, w.rA, sst, st);
+      cudaError_t e = w.prec == kw::PREC_C32 ? kw::launch_update_xp<kw::PREC_C32>(w, w.rA, sst, 0, st)
+                      : w.prec == kw::PREC_DF ? kw::launch_update_xp<kw::PREC_DF>(w, w.rA, sst, 0, st)
+                                              : kw::launch_update_xp<kw::PREC_F64>(w, w.rA, sst, 0, st);
       KW_CUDA(e, "update tile: launch");
       KW_CUDA(cudaEventRecord(tev[1], st), "update tile: event");
       KW_CUDA(cudaEventSynchronize(tev[1]), "update tile: sync");

@@ -49,8 +49,11 @@ struct State {
   int done;
   int status;
   int n_active;
-  int n_list;        // shifts processed in the current iteration (compacted list length)
-  int xp_pending;    // full-mode x/p update of the current iteration not yet applied
+  // shifts processed in an iteration (compacted list length) and whether its
+  // full-mode x/p update is pending, by iteration parity: K4(n) may still run
+  // while K2(n+1) and K3(n+1) use the other slot
+  int n_list[2];
+  int xp_pending[2];
   int n_seed_switch;
   int pad0;
   long long iter, maxiter, updates;
@@ -171,15 +174,27 @@ struct Work {
   // second stream for K3/K4 and the events that order the two streams
   cudaStream_t stream2 = nullptr;
   cudaEvent_t ev_k2 = nullptr, ev_k3 = nullptr;
+  // K4 on a third stream: K4(n) overlaps K2(n+1), K1(n+2) and K3(n+1);
+  // ev_k4[n & 1] marks K4(n)'s end.  k4_mask: the parities whose ev_k4 was
+  // recorded since the last join (a wait only ever names an event recorded
+  // in the same launch sequence, which a stream capture requires).
+  cudaStream_t stream3 = nullptr;
+  cudaEvent_t ev_k4[2] = {nullptr, nullptr};
+  int k4_mask = 0;
   int overlap = 1;   // 0: K3/K4 on the work stream after K1(n+1), no events
   State* st;
   cudaStream_t stream;
   int num_sms;
 };
 
-// Make the work stream wait for the shift stream (end of a chunk of iterations).
+// Make the work stream wait for the shift and update streams (end of a chunk of iterations).
 inline cudaError_t join_streams(Work& w) {
-  return w.overlap ? cudaStreamWaitEvent(w.stream, w.ev_k3, 0) : cudaSuccess;
+  if (!w.overlap) return cudaSuccess;
+  cudaError_t e = cudaStreamWaitEvent(w.stream, w.ev_k3, 0);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (w.k4_mask & (1 << i)) e = cudaStreamWaitEvent(w.stream, w.ev_k4[i], 0);
+  w.k4_mask = 0;
+  return e;
 }
 
 // Launchers implemented per precision (kw_kernels_f64.cu / kw_kernels_c32.cu).
@@ -189,9 +204,10 @@ template <int P> cudaError_t launch_iteration(Work& w, int parity, int first, cu
 template <int P> cudaError_t launch_finish_x(Work& w);
 template <int P> cudaError_t launch_unfinish_x(Work& w);
 template <int P> cudaError_t launch_k1(Work& w, void* r, void* rt);
-// K4 on the Work's X, P for the compacted list, with the given state (the
-// solve's, or a scratch state when the autotuner times the tiles).
-template <int P> cudaError_t launch_update_xp(Work& w, const void* r1, State* st, cudaStream_t s);
+// K4 on the Work's X, P for the compacted list of iteration parity `parity`
+// (its coefficient and list slots), with the given state (the solve's, or a
+// scratch state when the autotuner times the tiles).
+template <int P> cudaError_t launch_update_xp(Work& w, const void* r1, State* st, int parity, cudaStream_t s);
 template <int P> cudaError_t launch_project_x(Work& w, double2* out);
 template <int P>
 cudaError_t launch_spmv_dot(Work& w, const void* r, void* q, double2 zs, float4 zs_pair, double2* t_dev);

@@ -938,7 +938,7 @@ __device__ __forceinline__ void seed_coefficients(State* st, int parity, double2
         st->c = c;
         st->inv_rho = inv_rho;                   // beta_n = rho_{n+1} / rho_n below
         st->inv_rho_alpha = inv_rho_alpha;       // 1/(rho_n alpha_n): beta_n/alpha_n in K3 and the next K1
-        st->n_list = 0;
+        st->n_list[parity] = 0;
       }
     }
     // FP64 form: the coefficients themselves (the pair images carry them otherwise)
@@ -1402,13 +1402,14 @@ k_seed_update_rg(int m, const dfc* __restrict__ rn_buf, const dfc* __restrict__ 
 // ================================================================ K3: shift scalars
 struct ShiftArgs {
   int K, np, full;
+  int parity;        // iteration parity: the slots of coef, coef_pair, list, n_list, xp_pending
   const double2* z;
   double2* pi1;      // pi_n on entry, pi_{n+1} on exit
   double2* pi0;      // pi_{n-1} on entry, pi_n on exit
   int* active;
   long long* conv_iter;
   double* final_res;
-  double2* coef;     // full mode [K][3]: alpha^k, beta^k, 1/pi^k_{n+1}
+  double2* coef;     // this parity's slot, full mode [K][3]: alpha^k, beta^k, 1/pi^k_{n+1}
   float4* coef_pair; // the same as FP32 pairs (read by K4 in the FP32 and FP32-pair forms)
   double2* Y;
   double2* U;
@@ -1506,7 +1507,7 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   {
     const unsigned bal = __ballot_sync(KW_FULL_MASK, in_list);
     int basepos = 0;
-    if (lane == 0 && bal) basepos = atomicAdd(&st->n_list, __popc(bal));
+    if (lane == 0 && bal) basepos = atomicAdd(&st->n_list[a.parity], __popc(bal));
     basepos = __shfl_sync(KW_FULL_MASK, basepos, 0);
     if (in_list) a.list[basepos + __popc(bal & ((1u << lane) - 1))] = k;
   }
@@ -1553,7 +1554,7 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   if (lrow)
     for (int l = lane; l < a.np; l += 32) lrow[KW_LOG_FIXED + l] = a.w[l];
   if (lane != 0) return;
-  const int nl = *((volatile int*)&st->n_list);
+  const int nl = *((volatile int*)&st->n_list[a.parity]);
   const bool do_switch = st->seed_switch && n_still > 0 && gb < 1.0;
   const double2 rho1_in = st->rho1;
   const long long upd = st->updates, maxiter = st->maxiter;
@@ -1568,7 +1569,7 @@ __global__ void __launch_bounds__(32) k_shift(ShiftArgs a, State* st) {
   st->pi_rescale_pending = 0;
   if (rec) st->n_rec = rec_row + 1;
   st->updates = upd + nl;
-  st->xp_pending = (a.full && nl > 0 && !any_brk) ? 1 : 0;
+  st->xp_pending[a.parity] = (a.full && nl > 0 && !any_brk) ? 1 : 0;
   st->n_active = (int)n_still;
   if (any_brk) {                                        // pi_{n+1} = 0 (Eq. 20)
     set_fail(st, KW_ERR_BREAKDOWN);
@@ -1721,10 +1722,11 @@ template <int P, int TS, bool XP32 = false>
 __global__ void __launch_bounds__(256)
 k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coef,
             const float4* __restrict__ coef_pair, typename XT<P, XP32>::V* __restrict__ X,
-            typename XT<P, XP32>::V* __restrict__ Pv, const typename PT<P>::V* __restrict__ r1, State* st) {
+            typename XT<P, XP32>::V* __restrict__ Pv, const typename PT<P>::V* __restrict__ r1, State* st,
+            int parity) {
   typedef typename XT<P, XP32>::V V;
-  if (!st->xp_pending) return;
-  const int nl = st->n_list;
+  if (!st->xp_pending[parity]) return;
+  const int nl = st->n_list[parity];
   const int ntile = (nl + TS - 1) / TS;
   const int nchunk = (m + blockDim.x - 1) / blockDim.x;
   __shared__ V cs[TS][3];
@@ -1758,7 +1760,7 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
   if (!arrive_last(&st->cnt_xp)) return;
   if (threadIdx.x == 0) {
     st->cnt_xp = 0;
-    st->xp_pending = 0;
+    st->xp_pending[parity] = 0;
   }
 }
 
@@ -2443,44 +2445,51 @@ static cudaError_t k1_dispatch(Work& w, void* r, void* rt) {
 // chunk) items at full activity: every block takes part in the arrival count,
 // so idle blocks would only add to it.
 template <int P, int TS, bool XP32>
-static cudaError_t update_xp_launch(Work& w, const void* r1, State* st, cudaStream_t s) {
+static cudaError_t update_xp_launch(Work& w, const void* r1, State* st, int parity, cudaStream_t s) {
   typedef typename XT<P, XP32>::V XV;
   typedef typename PT<P>::V V;
   static int nblk_per_sm = 0;
   const long long items = (long long)((w.K + TS - 1) / TS) * ((w.m + 255) / 256);
   const int nblk = (int)std::max<long long>(
       1, std::min<long long>(resident_blocks(nblk_per_sm, k_update_xp<P, TS, XP32>, 256, w.num_sms), items));
-  k_update_xp<P, TS, XP32><<<nblk, 256, 0, s>>>((int)w.m, w.list, w.coef, w.coef_pair, (XV*)w.X, (XV*)w.P,
-                                                  (const V*)r1, st);
+  const size_t c0 = (size_t)parity * 3 * w.K;
+  k_update_xp<P, TS, XP32><<<nblk, 256, 0, s>>>((int)w.m, w.list + (size_t)parity * w.K, w.coef + c0,
+                                                  w.coef_pair + c0, (XV*)w.X, (XV*)w.P, (const V*)r1, st, parity);
   return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t launch_update_xp(Work& w, const void* r1, State* st, cudaStream_t s) {
+cudaError_t launch_update_xp(Work& w, const void* r1, State* st, int parity, cudaStream_t s) {
   const int ts = w.xp_tile;
   if (w.xp32) {
-    if (ts == 4) return update_xp_launch<P, 4, true>(w, r1, st, s);
-    if (ts == 16) return update_xp_launch<P, 16, true>(w, r1, st, s);
-    return update_xp_launch<P, 8, true>(w, r1, st, s);
+    if (ts == 4) return update_xp_launch<P, 4, true>(w, r1, st, parity, s);
+    if (ts == 16) return update_xp_launch<P, 16, true>(w, r1, st, parity, s);
+    return update_xp_launch<P, 8, true>(w, r1, st, parity, s);
   }
-  if (ts == 4) return update_xp_launch<P, 4, false>(w, r1, st, s);
-  if (ts == 16) return update_xp_launch<P, 16, false>(w, r1, st, s);
-  return update_xp_launch<P, 8, false>(w, r1, st, s);
+  if (ts == 4) return update_xp_launch<P, 4, false>(w, r1, st, parity, s);
+  if (ts == 16) return update_xp_launch<P, 16, false>(w, r1, st, parity, s);
+  return update_xp_launch<P, 8, false>(w, r1, st, parity, s);
 }
 
-// One iteration n on two streams (K1(n) was enqueued by the previous
+// One iteration n on three streams (K1(n) was enqueued by the previous
 // iteration or by launch_init):
-//   stream:  [wait K3(n-1)] K2(n) [record ev_k2] K1(n+1)
-//   stream2: [wait ev_k2] K3(n) K4(n) [record ev_k3]
-// K1(n+1) needs only r_{n+1}; K3(n)/K4(n) need only K2(n)'s scalars and
-// r_{n+1}.  K2(n+1) waits for both; a seed switch decided by K3(n) reaches
-// K1(n+1)'s product through K2(n+1)'s correction.  If ev is not NULL, ev[0..5]
-// are recorded around K2 and K1 (stream) and K3 and K4 (stream2).
+//   stream:  [wait K3(n-1)] [wait K4(n-2)] K2(n) [record ev_k2] K1(n+1)
+//   stream2: [wait ev_k2] K3(n) [record ev_k3]
+//   stream3: [wait ev_k3] K4(n) [record ev_k4[n & 1]]
+// K1(n+1) needs only r_{n+1}; K3(n) needs only K2(n)'s scalars; K4(n) needs
+// K3(n)'s coefficients and list and r_{n+1}.  K2(n+1) waits for K3(n) only: a
+// seed switch decided by K3(n) reaches K1(n+1)'s product through K2(n+1)'s
+// correction, and K4(n) runs beside K2(n+1), K3(n+1) and K1(n+2).  K4(n)'s
+// inputs stay intact until K2(n+2): its r_{n+1} is the buffer K2(n+2)
+// overwrites, and its coefficients, list and list length are in the slots of
+// parity n & 1, which K2(n+2) (the length) and K3(n+2) write next.  So K2(n+2)
+// waits for K4(n).  If ev is not NULL, ev[0..5] are recorded around K2 and K1
+// (stream), K3 (stream2) and K4 (stream3).
 template <int P>
 cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, int64_t* launches) {
   typedef typename PT<P>::V V;
   if (!w.st || !w.part || !w.part_k1 || !w.rA || !w.rB || !w.q || !w.z || !w.list || !w.stream2 || !w.ev_k2 ||
-      !w.ev_k3)
+      !w.ev_k3 || !w.stream3 || !w.ev_k4[0] || !w.ev_k4[1])
     return cudaErrorInvalidValue;
   // parity 0: r_n in rA, r_{n-1} in rB; parity 1: swapped.  K2 writes r_{n+1} over r_{n-1}.
   void* rn = parity ? w.rB : w.rA;
@@ -2489,7 +2498,10 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
 #define KW_MARK(i, s) \
   if (ev && (e = cudaEventRecord(ev[i], s)) != cudaSuccess) return e;
   cudaStream_t s2 = w.overlap ? w.stream2 : w.stream;
+  cudaStream_t s3 = w.overlap ? w.stream3 : w.stream;
   if (w.overlap && !first && (e = cudaStreamWaitEvent(w.stream, w.ev_k3, 0)) != cudaSuccess) return e;
+  if (w.overlap && (w.k4_mask & (1 << parity)) && (e = cudaStreamWaitEvent(w.stream, w.ev_k4[parity], 0)) != cudaSuccess)
+    return e;
   KW_MARK(0, w.stream);
   if ((e = seed_dispatch<P>(w, rn, rm, parity)) != cudaSuccess) return e;
   KW_MARK(1, w.stream);
@@ -2504,19 +2516,20 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   a.K = w.K;
   a.np = w.nproj;
   a.full = w.full ? 1 : 0;
+  a.parity = parity;
   a.z = w.z;
   a.pi1 = w.pi1;
   a.pi0 = w.pi0;
   a.active = w.active;
   a.conv_iter = w.conv_iter;
   a.final_res = w.final_res;
-  a.coef = w.coef;
-  a.coef_pair = w.coef_pair;
+  a.coef = w.coef + (size_t)parity * 3 * w.K;
+  a.coef_pair = w.coef_pair + (size_t)parity * 3 * w.K;
   a.Y = w.Y;
   a.U = w.U;
   a.w = w.w;
   a.hist = w.hist;
-  a.list = w.list;
+  a.list = w.list + (size_t)parity * w.K;
   a.part = w.part;
   a.log = w.log;
   a.log_max = w.log_max;
@@ -2536,13 +2549,18 @@ cudaError_t launch_iteration(Work& w, int parity, int first, cudaEvent_t* ev, in
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   KW_MARK(4, s2);
+  if (w.overlap && (e = cudaEventRecord(w.ev_k3, s2)) != cudaSuccess) return e;
   *launches += (w.mv_fn && P == PREC_DF) ? 4 : 3;
   if (w.full) {
-    if ((e = launch_update_xp<P>(w, rm, w.st, s2)) != cudaSuccess) return e;
+    if (w.overlap && (e = cudaStreamWaitEvent(s3, w.ev_k3, 0)) != cudaSuccess) return e;
+    if ((e = launch_update_xp<P>(w, rm, w.st, parity, s3)) != cudaSuccess) return e;
+    KW_MARK(5, s3);
+    if (w.overlap) {
+      if ((e = cudaEventRecord(w.ev_k4[parity], s3)) != cudaSuccess) return e;
+      w.k4_mask |= 1 << parity;
+    }
     *launches += 1;
   }
-  KW_MARK(5, s2);
-  if (w.overlap && (e = cudaEventRecord(w.ev_k3, s2)) != cudaSuccess) return e;
 #undef KW_MARK
   return cudaSuccess;
 }

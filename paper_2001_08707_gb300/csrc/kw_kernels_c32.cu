@@ -8,7 +8,7 @@ template cudaError_t launch_iteration<PREC_C32>(Work&, int, int, cudaEvent_t*, i
 template cudaError_t launch_finish_x<PREC_C32>(Work&);
 template cudaError_t launch_unfinish_x<PREC_C32>(Work&);
 template cudaError_t launch_k1<PREC_C32>(Work&, void*, void*);
-template cudaError_t launch_update_xp<PREC_C32>(Work&, const void*, State*, cudaStream_t);
+template cudaError_t launch_update_xp<PREC_C32>(Work&, const void*, State*, int, cudaStream_t);
 template cudaError_t launch_project_x<PREC_C32>(Work&, double2*);
 template cudaError_t launch_spmv_dot<PREC_C32>(Work&, const void*, void*, double2, float4, double2*);
 

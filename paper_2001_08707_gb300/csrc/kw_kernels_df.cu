@@ -9,7 +9,7 @@ template cudaError_t launch_iteration<PREC_DF>(Work&, int, int, cudaEvent_t*, in
 template cudaError_t launch_finish_x<PREC_DF>(Work&);
 template cudaError_t launch_unfinish_x<PREC_DF>(Work&);
 template cudaError_t launch_k1<PREC_DF>(Work&, void*, void*);
-template cudaError_t launch_update_xp<PREC_DF>(Work&, const void*, State*, cudaStream_t);
+template cudaError_t launch_update_xp<PREC_DF>(Work&, const void*, State*, int, cudaStream_t);
 template cudaError_t launch_project_x<PREC_DF>(Work&, double2*);
 template cudaError_t launch_spmv_dot<PREC_DF>(Work&, const void*, void*, double2, float4, double2*);
 
