@@ -583,6 +583,9 @@ typedef struct {
     const double* val_dev;
 } kw_csr_term;
 
+/* Most shifts of one kw_bilinear call (65535 tiles of 8 shifts). */
+#define KW_BILINEAR_MAX_SHIFTS 524280LL
+
 /* Adjoint bilinear forms for the parameter derivative of the Green's function.
  * With G(z) = (z I - H)^{-1} (Eq. 2) and H = sum_t theta_t H_t,
  * dG/dtheta_t = G H_t G, and G^T = G for real symmetric H, so
@@ -593,8 +596,13 @@ typedef struct {
  *   X_dev, Y_dev: [nshift][m] kw_c128 device arrays (x_k from kw_solve in full
  *   mode with KW_F64 or KW_DF64); Y_dev NULL means Y = X.
  *   out_host: kw_c128 [nshift][nterm].
- * FP64 arithmetic; uses the context's stream and workspace.  Errors:
- * KW_ERR_ARG (sizes, NULL pointers), KW_ERR_OOM, KW_ERR_CUDA. */
+ * Terms whose every row holds at most one entry, on the diagonal (field and
+ * on-site terms), are found by a scan of their structure and handled together:
+ * y_k[i] x_k[i] is formed once per shift and row and applied to up to 16 such
+ * terms in one pass over X and Y; the other terms take a pass each.
+ * FP64 arithmetic; uses the context's stream and workspace (nterm x m doubles
+ * for the diagonals).  Errors: KW_ERR_ARG (sizes, nshift > KW_BILINEAR_MAX_SHIFTS,
+ * NULL pointers), KW_ERR_OOM, KW_ERR_CUDA. */
 kw_status kw_bilinear(kw_ctx* ctx, int64_t m, int64_t nterm, const kw_csr_term* terms_host, int64_t nshift,
                       const kw_c128* X_dev, const kw_c128* Y_dev, kw_c128* out_host);
 

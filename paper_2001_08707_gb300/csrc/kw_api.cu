@@ -132,6 +132,7 @@ struct kw_ctx {
   DBuf h_rowptr, h_col, h_val, h_b, h_left, h_x;
   // workspace
   DBuf bil_part, bil_out;     // kw_bilinear scratch and result
+  DBuf bil_diag, bil_flag;    // kw_bilinear: the terms' diagonals [nterm][m] and diagonal-only flags
   DBuf rA, rB, q, proj_rows, z, pi1, pi0, active, conv_iter, final_res, coef, coef_pair, Y, U, w, w0, hist, list,
       X, P, part, st, projx, tdot;
   kw::State* st_host = nullptr;   // pinned
@@ -272,7 +273,7 @@ kw_status kw_create(kw_ctx** out, const kw_options* opt, void* cuda_stream) {
 void kw_destroy(kw_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);   // the caller's stream (possibly the legacy one) may hold our work
-  DBuf* bufs[] = {&ctx->bil_part, &ctx->bil_out, &ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->sell_perm, &ctx->sell_len,
+  DBuf* bufs[] = {&ctx->bil_part, &ctx->bil_out, &ctx->bil_diag, &ctx->bil_flag, &ctx->val32, &ctx->valpair, &ctx->coef_pair, &ctx->inexact, &ctx->sell_perm, &ctx->sell_len,
                   &ctx->sell_slen, &ctx->sell_ptr, &ctx->sell_col, &ctx->sell_val, &ctx->h_rowptr, &ctx->h_col, &ctx->h_val, &ctx->h_b, &ctx->h_left, &ctx->h_x,
                   &ctx->rA, &ctx->rB, &ctx->q, &ctx->proj_rows, &ctx->z, &ctx->pi1, &ctx->pi0, &ctx->active,
                   &ctx->conv_iter, &ctx->final_res, &ctx->coef, &ctx->Y, &ctx->U, &ctx->w, &ctx->w0,
@@ -1862,7 +1863,8 @@ kw_status kw_get_residual_history(kw_ctx* ctx, double* hist_host, int64_t* n_rec
 static kw_status bilinear(kw_ctx* ctx, const char* name, int64_t m, int64_t nterm, const kw_csr_term* terms,
                           int64_t nshift, const void* X_dev, const void* Y_dev, int x32, kw_c128* out_host) {
   if (!ctx) return KW_ERR_ARG;
-  if (m < 1 || m > KW_MAX_ROWS || nterm < 1 || nshift < 1 || nshift > 0x7fffffffLL || !terms || !X_dev || !out_host)
+  if (m < 1 || m > KW_MAX_ROWS || nterm < 1 || nshift < 1 || nshift > KW_BILINEAR_MAX_SHIFTS || !terms || !X_dev ||
+      !out_host)
     return fail(ctx, KW_ERR_ARG, "%s: invalid sizes or NULL pointer", name);
   for (int64_t t = 0; t < nterm; ++t)
     if (!terms[t].rowptr_dev || terms[t].nnz < 0 || terms[t].nnz > KW_MAX_NNZ ||
@@ -1870,14 +1872,49 @@ static kw_status bilinear(kw_ctx* ctx, const char* name, int64_t m, int64_t nter
       return fail(ctx, KW_ERR_ARG, "%s: term %lld is invalid", name, (long long)t);
   const int nblk = 2 * ctx->num_sms;
   const int64_t ntile = (nshift + kw::kBilinearTile - 1) / kw::kBilinearTile;
-  KW_CUDA(ctx->bil_part.ensure((size_t)ntile * nblk * kw::kBilinearTile * 16), "kw_bilinear: scratch");
+  // diagonal path: blocks per shift so that all shifts together fill the device about four times
+  const int dblk = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (4 * ctx->num_sms + nshift - 1) / nshift));
+  const size_t part_bytes = std::max((size_t)ntile * nblk * kw::kBilinearTile, (size_t)nshift * dblk * kw::kDiagGroup) * 16;
+  KW_CUDA(ctx->bil_part.ensure(part_bytes), "kw_bilinear: scratch");
   KW_CUDA(ctx->bil_out.ensure((size_t)nshift * nterm * 16), "kw_bilinear: result");
-  const void* Y = Y_dev ? Y_dev : X_dev;
+  KW_CUDA(ctx->bil_diag.ensure((size_t)nterm * m * 8), "kw_bilinear: diagonals");
+  KW_CUDA(ctx->bil_flag.ensure((size_t)nterm * 4), "kw_bilinear: flags");
+  // which terms hold only diagonal entries (each such term then costs one FMA pair per shift and row
+  // in a shared pass over X and Y, instead of a pass of its own)
+  KW_CUDA(cudaMemsetAsync(ctx->bil_flag.p, 1, (size_t)nterm * 4, ctx->stream), "kw_bilinear: flags");
+  double* dg = (double*)ctx->bil_diag.p;
+  int* flag = (int*)ctx->bil_flag.p;
   for (int64_t t = 0; t < nterm; ++t)
+    KW_CUDA(kw::launch_diag_scan((int)m, terms[t].rowptr_dev, terms[t].col_dev, terms[t].val_dev, dg + t * m,
+                                 flag + t, ctx->num_sms, ctx->stream),
+            "kw_bilinear: structure");
+  std::vector<int> is_diag((size_t)nterm);
+  KW_CUDA(cudaMemcpyAsync(is_diag.data(), flag, (size_t)nterm * 4, cudaMemcpyDeviceToHost, ctx->stream),
+          "kw_bilinear: flags");
+  KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_bilinear: flags");
+  const void* Y = Y_dev ? Y_dev : X_dev;
+  kw::DiagGroup g;
+  g.n = 0;
+  auto flush = [&]() -> cudaError_t {
+    if (g.n == 0) return cudaSuccess;
+    cudaError_t e = kw::launch_bilinear_diag((int)m, (int)nshift, dg, g, X_dev, Y, x32, dblk,
+                                             (double2*)ctx->bil_part.p, (int)nterm, (double2*)ctx->bil_out.p,
+                                             ctx->stream);
+    g.n = 0;
+    return e;
+  };
+  for (int64_t t = 0; t < nterm; ++t) {
+    if (is_diag[(size_t)t]) {
+      g.idx[g.n++] = (int)t;
+      if (g.n == kw::kDiagGroup) KW_CUDA(flush(), "kw_bilinear launch");
+      continue;
+    }
     KW_CUDA(kw::launch_bilinear((int)m, (int)nshift, terms[t].rowptr_dev, terms[t].col_dev, terms[t].val_dev, X_dev,
                                 Y, x32, nblk, (double2*)ctx->bil_part.p, (int)t, (int)nterm,
                                 (double2*)ctx->bil_out.p, ctx->stream),
             "kw_bilinear launch");
+  }
+  KW_CUDA(flush(), "kw_bilinear launch");
   KW_CUDA(cudaMemcpyAsync(out_host, ctx->bil_out.p, (size_t)nshift * nterm * 16, cudaMemcpyDeviceToHost, ctx->stream),
           "kw_bilinear read");
   KW_CUDA(cudaStreamSynchronize(ctx->stream), "kw_bilinear sync");

@@ -278,6 +278,21 @@ cudaError_t launch_shift_combine(int m, int K, int nk, const void* X, int x32, c
 cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col, const double* val, const void* X,
                             const void* Y, int x32, int nblk, double2* part, int term, int nterm, double2* out,
                             cudaStream_t s);
+// Diagonal terms of kw_bilinear.  launch_diag_scan: d[i] = the row's diagonal
+// entry (0 for an empty row); *flag is cleared if some row holds anything else
+// (an entry off the diagonal, or more than one entry).  launch_bilinear_diag:
+// out[k * nterm + idx[t]] = sum_i d_t[i] y_k[i] x_k[i] for the n <= kDiagGroup
+// terms of one group (d_t = d + idx[t] * m), all shifts in one pass over X and
+// Y; part holds K * nblk * kDiagGroup double2.
+constexpr int kDiagGroup = 16;
+struct DiagGroup {
+  int n;
+  int idx[kDiagGroup];
+};
+cudaError_t launch_diag_scan(int m, const int64_t* rowptr, const int* col, const double* val, double* d, int* flag,
+                             int num_sms, cudaStream_t s);
+cudaError_t launch_bilinear_diag(int m, int K, const double* d, const DiagGroup& g, const void* X, const void* Y,
+                                 int x32, int nblk, double2* part, int nterm, double2* out, cudaStream_t s);
 
 // Recalculation at new shifts (kw_recalc): threads per block, log rows per
 // shared-memory chunk, and the launcher (flag: set to 1 on breakdown).

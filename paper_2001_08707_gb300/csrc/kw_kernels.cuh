@@ -1817,6 +1817,77 @@ k_bilinear(int m, int K, const int64_t* __restrict__ rowptr, const int* __restri
   }
 }
 
+// Structure of one term for the diagonal path: d[i] = its entry in row i if
+// that is the row's only entry and sits on the diagonal, 0 for an empty row;
+// any other row clears *flag (several threads may store the same 0).
+static __global__ void k_diag_scan(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, double* __restrict__ d, int* flag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const int64_t b = rowptr[i], e = rowptr[i + 1];
+    double v = 0.0;
+    if (e - b == 1 && col[b] == i) v = val[b];
+    else if (e != b) *flag = 0;
+    d[i] = v;
+  }
+}
+
+// out[k][idx[t]] = sum_i d_t[i] y_k[i] x_k[i] for a group of diagonal terms:
+// block (bx, k - k0) takes shift k over a grid-stride share of the rows, forms
+// y_k[i] x_k[i] once per row and applies it to every term of the group (the
+// diagonals, a few MB, are re-read from L2 for each shift).  FP64 sums; the
+// per-block partials part[(k * gridDim.x + bx) * DT + t] are summed by
+// k_bilinear_diag_reduce.
+template <int DT, class XV>
+__global__ void __launch_bounds__(256)
+k_bilinear_diag(int m, int k0, const double* __restrict__ d, DiagGroup g, const XV* __restrict__ X,
+                const XV* __restrict__ Y, double2* __restrict__ part) {
+  const int k = k0 + (int)blockIdx.y;
+  const XV* xk = X + (size_t)k * m;
+  const XV* yk = Y + (size_t)k * m;
+  double re[DT], im[DT];
+#pragma unroll
+  for (int t = 0; t < DT; ++t) re[t] = im[t] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const double2 x = wide(xk[i]), y = wide(yk[i]);
+    const double pr = fma(y.x, x.x, -y.y * x.y), pi = fma(y.x, x.y, y.y * x.x);   // y_k[i] x_k[i]
+#pragma unroll
+    for (int t = 0; t < DT; ++t)
+      if (t < g.n) {
+        const double dv = d[(size_t)g.idx[t] * m + i];
+        re[t] = fma(dv, pr, re[t]);
+        im[t] = fma(dv, pi, im[t]);
+      }
+  }
+  __shared__ double red[2 * DT];
+  double v[2 * DT];
+#pragma unroll
+  for (int t = 0; t < DT; ++t) {
+    v[2 * t] = re[t];
+    v[2 * t + 1] = im[t];
+  }
+  block_sum<2 * DT, double>(v, 2 * DT, red);
+  if (threadIdx.x < g.n) {
+    const size_t o = ((size_t)k * gridDim.x + blockIdx.x) * DT + threadIdx.x;
+    part[o] = make_double2(red[2 * threadIdx.x], red[2 * threadIdx.x + 1]);
+  }
+}
+
+// out[k * nterm + idx[t]] = sum over the nblk blocks of shift k, fixed order.
+template <int DT>
+__global__ void k_bilinear_diag_reduce(int K, int nblk, DiagGroup g, int nterm, const double2* __restrict__ part,
+                                       double2* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= K * g.n) return;
+  const int k = j / g.n, t = j % g.n;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = 0; b < nblk; ++b) {
+    const double2 p = part[((size_t)k * nblk + b) * DT + t];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  out[(size_t)k * nterm + g.idx[t]] = s;
+}
+
 // out[k * nterm + term] = sum over blocks of the partials, fixed order.
 template <int BT>
 __global__ void k_bilinear_reduce(int K, int nblk, int term, int nterm, const double2* __restrict__ part,

@@ -120,6 +120,29 @@ cudaError_t launch_bilinear(int m, int K, const int64_t* rowptr, const int* col,
   return cudaGetLastError();
 }
 
+cudaError_t launch_diag_scan(int m, const int64_t* rowptr, const int* col, const double* val, double* d, int* flag,
+                             int num_sms, cudaStream_t s) {
+  const int grid = std::max(1, std::min(4 * num_sms, (m + 255) / 256));
+  k_diag_scan<<<grid, 256, 0, s>>>(m, rowptr, col, val, d, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bilinear_diag(int m, int K, const double* d, const DiagGroup& g, const void* X, const void* Y,
+                                 int x32, int nblk, double2* part, int nterm, double2* out, cudaStream_t s) {
+  for (int k0 = 0; k0 < K; k0 += 65535) {   // the grid's y extent
+    const dim3 grid(nblk, std::min(K - k0, 65535));
+    if (x32)
+      k_bilinear_diag<kDiagGroup, float2><<<grid, 256, 0, s>>>(m, k0, d, g, (const float2*)X, (const float2*)Y, part);
+    else
+      k_bilinear_diag<kDiagGroup, double2><<<grid, 256, 0, s>>>(m, k0, d, g, (const double2*)X, (const double2*)Y,
+                                                                 part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_bilinear_diag_reduce<kDiagGroup><<<(K * g.n + 127) / 128, 128, 0, s>>>(K, nblk, g, nterm, part, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_shift_combine(int m, int K, int nk, const void* X, int x32, const double2* W, double2* S,
                                  int num_sms, cudaStream_t s) {
   const int grid = std::max(1, std::min(8 * num_sms, (m + 255) / 256));

@@ -176,3 +176,51 @@ def test_spectrum_gradient_with_fp32_shift_storage():
     g = theta.grad.numpy()
     print(f"max gradient error {np.abs(g - grad_o).max() / np.abs(grad_o).max():.2e}")
     assert np.abs(g - grad_o).max() <= 1e-5 * np.abs(grad_o).max()
+
+
+def _csr_dev(A):
+    A = A.tocsr()
+    return (torch.as_tensor(A.indptr.astype(np.int64), device="cuda"),
+            torch.as_tensor(A.indices.astype(np.int32), device="cuda"),
+            torch.as_tensor(A.data.astype(np.float64), device="cuda"))
+
+
+@pytest.mark.parametrize("dtype", [np.complex128, np.complex64])
+def test_bilinear_diagonal_path_edge_terms(dtype):
+    """kw_bilinear finds the terms whose rows hold at most one entry, on the
+    diagonal, and sums up to 16 of them in one pass over X and Y.  Mixed here:
+    19 diagonal terms (two groups) with empty rows, a term with one entry off
+    the diagonal, a term with a diagonal entry stored twice in one row, an
+    empty term (nnz 0) and a general term, at a ragged shift count; against
+    numpy's y_k^T H_t x_k, with Y = X and Y given."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(8)
+    m, K = 1031, 19
+    terms = []
+    for t in range(19):
+        dvals = rng.standard_normal(m)
+        dvals[rng.random(m) < 0.2] = 0.0
+        terms.append(sp.diags(dvals).tocsr())
+        terms[-1].eliminate_zeros()                     # some rows empty
+    off = sp.diags(rng.standard_normal(m)).tolil()
+    off[5, 9] = 0.75                                   # one entry off the diagonal
+    terms.insert(3, off.tocsr())
+    dup = sp.diags(rng.standard_normal(m)).tocsr()
+    r0 = dup.indptr[7]
+    dup = sp.csr_matrix((np.insert(dup.data, r0, 0.5), np.insert(dup.indices, r0, 7),
+                         np.concatenate([dup.indptr[:8], dup.indptr[8:] + 1])), shape=(m, m))
+    assert dup.indptr[8] - dup.indptr[7] == 2 and not dup.has_canonical_format
+    terms.insert(11, dup)                              # (7, 7) stored twice
+    terms.append(sp.csr_matrix((m, m)))                # empty
+    terms.append(sp.random(m, m, density=0.01, random_state=3, format="csr"))
+    X = (rng.standard_normal((K, m)) + 1j * rng.standard_normal((K, m))).astype(dtype)
+    Y = (rng.standard_normal((K, m)) + 1j * rng.standard_normal((K, m))).astype(dtype)
+    Xd, Yd = torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")
+    dev = [_csr_dev(A) for A in terms]
+    s = kw.Solver("f64")
+    X64, Y64 = X.astype(np.complex128), Y.astype(np.complex128)
+    for y_is_x in (True, False):
+        out = s.bilinear(dev, Xd, None if y_is_x else Yd)
+        YY = X64 if y_is_x else Y64
+        ref = np.stack([np.sum(YY * (A @ X64.T).T, axis=1) for A in terms], axis=1)
+        np.testing.assert_allclose(out, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
