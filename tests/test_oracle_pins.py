@@ -8,6 +8,9 @@ not by re-running the oracle's own formulas.
 * SPD special case: real shifts above the spectrum make z I - H symmetric
   positive definite; the iterates must equal scipy's textbook CG iterates.
 * Converged solutions: dense LU (Eq. 4-5) and the spectral sum (Eq. 3).
+* Freezing (Eq. 7 with Eq. 19): a shift stops at the first iteration whose
+  true residual ||b - (z I - H) x_n|| of the Galerkin iterate is <= tol ||b||,
+  keeps that iterate, and reports that residual.
 * Sum rule, large-|z| moments, polarization identity (Sec. 3.2.2),
   degenerate inputs with closed forms.
 """
@@ -245,3 +248,48 @@ def test_maxiter_reports_not_converged():
     assert r.status == oc.STATUS_NOT_CONVERGED and r.iters == 5
     assert np.all(r.conv_iter == -1)
     assert r.hist.shape == (5, 8)
+
+
+def _krylov_basis(Hd, b, n):
+    """Orthonormal basis of K_n(H, b) by Gram-Schmidt, twice per vector (stable
+    where the power basis of _galerkin is not)."""
+    M = b.size
+    Q = np.zeros((M, n))
+    v = b / np.linalg.norm(b)
+    for i in range(n):
+        Q[:, i] = v
+        if i + 1 == n:
+            break
+        u = Hd @ v
+        for _ in range(2):
+            u -= Q[:, :i + 1] @ (Q[:, :i + 1].T @ u)
+        v = u / np.linalg.norm(u)
+    return Q
+
+
+@pytest.mark.parametrize("switch", [True, False])
+def test_freeze_rule_against_galerkin_residuals(switch):
+    """Each shift is frozen at the first n whose Galerkin iterate has true
+    residual <= tol ||b|| (here 12 to 21 iterations, every crossing at least 8%
+    away from tol on both sides), keeps that iterate as x, and reports that
+    residual in final_res."""
+    Hd, b = _random_symmetric(30, 4)
+    z = np.array([0.5 + 3j, -2 + 2.5j, 3 + 4j, 1 + 6j, -4 + 3.5j, 6 + 5j])
+    tol = 1e-4
+    r = oc.shifted_cocg(Hd, b, z, tol=tol, maxiter=30, full=True, seed_switch=switch)
+    assert r.status == oc.STATUS_OK
+    Q = _krylov_basis(Hd, b, 30)
+    for k, zk in enumerate(z):
+        A = zk * np.eye(b.size) - Hd
+        xs, ts = [], []
+        for n in range(1, 31):
+            Qn = Q[:, :n]
+            x = Qn @ np.linalg.solve(Qn.T @ A @ Qn, Qn.T @ b)
+            xs.append(x)
+            ts.append(np.linalg.norm(b - A @ x))
+        ts = np.array(ts)
+        c = int(np.argmax(ts <= tol)) + 1
+        assert ts[c - 1] <= 0.92 * tol and (c == 1 or ts[c - 2] >= 1.05 * tol)
+        assert r.conv_iter[k] == c, (k, r.conv_iter[k], c)
+        assert np.linalg.norm(r.x[k] - xs[c - 1]) <= 1e-9 * np.linalg.norm(xs[c - 1])
+        assert abs(r.final_res[k] - ts[c - 1]) <= 1e-9 * ts[c - 1]
