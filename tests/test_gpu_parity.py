@@ -415,3 +415,35 @@ def test_anderson_contour_projected_16_left(prec):
     # b^T x stays well inside the bound (its superconvergence is weakened here: the
     # solve runs ~2.4 M iterations, past the loss of orthogonality)
     assert np.abs(g.proj[:, 0] - orc.proj[:, 0]).max() <= 1e-8 * np.abs(orc.proj[:, 0]).max()
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_freeze_iterations_exact_on_clear_crossings(prec):
+    """The freeze rule (Eq. 7 with Eq. 19) to the iteration.  (1) Every shift
+    stops at the first iteration whose own residual estimate is <= tol ||b||,
+    and reports that residual.  (2) Where the GPU's and the oracle's residual
+    histories agree (to 1e-6 through the crossing, i.e. before the loss of
+    orthogonality lets the two roundings drift) and cross tol with a 1% margin,
+    the stopping iteration equals the oracle's exactly: a freeze one iteration
+    early or late would move every such shift."""
+    p = w.anderson_small(L=8, K=24, delta=0.5, tol=1e-7)
+    orc = oc.shifted_cocg(p.H.to_scipy(), p.b, p.z, tol=p.tol, full=True, hist_stride=1)
+    thresh = p.tol * np.linalg.norm(p.b)
+    s = _solver(p.H, prec, tol=p.tol, hist_stride=1, hist_max=100000)
+    g = s.solve(p.b, p.z, full=True)
+    assert g.status == "KW_OK"
+    ci, fr = s.shift_status(p.z.size)
+    h = s.residual_history(p.z.size)
+    ho = np.asarray(orc.hist)
+    exact = 0
+    for k in range(p.z.size):
+        c = int(np.argmax(h[:, k] <= thresh)) + 1           # first crossing of the GPU's own estimate
+        assert ci[k] == c and fr[k] == h[c - 1, k]
+        co = orc.conv_iter[k]
+        n = max(c, co)
+        before = ho[co - 2, k] if co >= 2 else np.inf
+        if (n <= min(len(h), len(ho)) and np.all(np.abs(h[:n, k] - ho[:n, k]) <= 1e-6 * ho[:n, k])
+                and ho[co - 1, k] <= 0.99 * thresh and before >= 1.01 * thresh):
+            assert ci[k] == co
+            exact += 1
+    assert exact >= 8
