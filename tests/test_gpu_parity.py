@@ -447,3 +447,38 @@ def test_freeze_iterations_exact_on_clear_crossings(prec):
             assert ci[k] == co
             exact += 1
     assert exact >= 8
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64", "c32"])
+def test_edge_zero_rhs_is_a_breakdown_with_zero_solution(prec):
+    """b = 0: rho_0 = 0, so alpha_0 (Eq. 17) is undefined; like the oracle, the
+    solve stops before the first iteration with a breakdown and x = 0."""
+    H = w.anderson_3d(4, 1.0, seed=1)
+    z = np.array([1 + 1j, 2 + 0.5j])
+    orc = oc.shifted_cocg(H.to_scipy(), np.zeros(H.m), z, tol=1e-10, full=True)
+    assert orc.status == oc.STATUS_BREAKDOWN and orc.iters == 0
+    s = _solver(H, prec, tol=1e-10)
+    g = s.solve(np.zeros(H.m), z, full=True, check=False)
+    assert g.status == "KW_ERR_BREAKDOWN" and g.iters == 0
+    assert not np.any(g.x.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_edge_duplicate_shifts(prec):
+    """Repeated shifts: each copy gets the same iterates (the same arithmetic on
+    the same inputs) and stops at the same iteration; ties in the seed choice
+    go to the lowest index, as in the oracle."""
+    H = w.anderson_3d(4, 1.0, seed=1)
+    b = w.gaussian_unit(H.m, 3)
+    z = np.array([1 + 1j, 1 + 1j, -2 + 0.3j, -2 + 0.3j, 0.5 + 0.05j, 0.5 + 0.05j])
+    orc = oc.shifted_cocg(H.to_scipy(), b, z, tol=1e-10, full=True)
+    s = _solver(H, prec, tol=1e-10)
+    g = s.solve(b, z, full=True)
+    ci, fr = s.shift_status(z.size)
+    x = g.x.cpu().numpy()
+    for k in range(0, z.size, 2):
+        np.testing.assert_array_equal(x[k], x[k + 1])
+        assert ci[k] == ci[k + 1] and fr[k] == fr[k + 1]
+    assert g.status == "KW_OK" and abs(g.iters - orc.iters) <= 2
+    err = np.abs(x - orc.x).max(axis=1) * np.abs(z.imag)
+    assert err.max() < 4e-10
