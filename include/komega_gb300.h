@@ -244,7 +244,10 @@ kw_status kw_set_lattice3d(kw_ctx* ctx, int64_t nx, int64_t ny, int64_t nz, cons
  * Returns KW_OK when every shift met the tolerance, KW_NOT_CONVERGED at
  * maxiter (outputs then hold the last iterates), KW_ERR_BREAKDOWN /
  * KW_ERR_NONFINITE with the outputs of the last completed iteration, or an
- * argument/CUDA error.  kw_set_csr must have been called. */
+ * argument/CUDA error.  A right-hand side with ||b|| = 0 (where rho_0 = 0 and
+ * Eq. 17 has no alpha_0) or a non-finite norm is found on the device before the
+ * first iteration and returns KW_ERR_ARG with 0 iterations and x = 0.
+ * kw_set_csr must have been called. */
 kw_status kw_solve(kw_ctx* ctx, const double* b_dev, int64_t nshift, const kw_c128* z_host,
                    int64_t nleft, const double* left_dev, void* x_out_dev,
                    kw_c128* proj_out_host, kw_solve_info* info);
