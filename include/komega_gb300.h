@@ -84,7 +84,7 @@ typedef struct {
     int64_t hist_max;    /* records kept at most */
     int use_graph;       /* 0: the host enqueues the iterations in chunks and polls the stop flag;
                             1: the iterations loop on the device in one CUDA graph (a WHILE node whose
-                            body runs a chunk of iterations and then tests the stop flag), with no host
+                            body runs a chunk of 32 iterations and then tests the stop flag), with no host
                             work per chunk; n >= 2: the same with n iterations per body (rounded up to
                             even).  The graph is kept and relaunched while the solve's descriptor is
                             unchanged.  Solves with a matrix-vector callback, or with kernel timing on

@@ -1313,7 +1313,11 @@ static kw_status run_loop(kw_ctx* ctx, int64_t start = 0) {
   return KW_OK;
 }
 
-static const int kGraphChunk = 8;   // iterations per trip of the device-side loop (even)
+// Iterations per trip of the device-side loop (even).  Each trip ends with a
+// join of the streams and the loop-condition kernel; 32 against 8 cut the small
+// Anderson workload's iteration by 4% and the N=24 chain's by 0.6%; at most 31
+// iterations after the stop then launch and return at once.
+static const int kGraphChunk = 32;
 
 // Iterations per trip of the device-side loop: 0 when the host loop runs (the
 // option is off, kernel timing samples events per chunk, or a callback's work
