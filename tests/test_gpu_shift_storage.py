@@ -124,3 +124,30 @@ def test_host_path_and_edges(prec):
     g1 = s1.solve(np.array([1.0]), [2.0 + 1.0j], full=True)
     assert abs(complex(g1.x.cpu().numpy()[0, 0]) - 1.0 / (1.5 + 1.0j)) <= 1e-7
     assert abs(g1.proj[0, 0] - 1.0 / (1.5 + 1.0j)) <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["f64", "df64"])
+def test_paired_and_single_element_updates_agree(prec):
+    """With FP32 storage the x/p update takes two adjacent elements per thread
+    (16-byte accesses) when m is even and x starts 16-byte aligned, one element
+    otherwise.  The arithmetic per element is the same, so an x at an 8-byte
+    offset (single elements) gives the same bits as an aligned one (pairs); an
+    odd m (single elements) meets the oracle's bound."""
+    p = w.anderson_small(L=8, K=20, delta=0.1, tol=1e-9)          # m = 512
+    s = _solver(p.H, prec, True, tol=p.tol)
+    a = s.solve(p.b, p.z, full=True)
+    buf = torch.zeros(p.z.size * p.H.m + 1, dtype=torch.complex64, device="cuda")
+    xv = buf[1:].view(p.z.size, p.H.m)
+    assert xv.data_ptr() % 16 == 8
+    g = s.solve(p.b, p.z, full=True, x_out=xv)
+    assert g.iters == a.iters
+    assert torch.equal(xv, a.x)
+    q = w.anderson_small(L=7, K=16, delta=0.1, tol=1e-9)          # m = 343
+    Hs = q.H.to_scipy()
+    orc = oc.shifted_cocg(Hs, q.b, q.z, tol=q.tol, full=True)
+    r = _solver(q.H, prec, True, tol=q.tol).solve(q.b, q.z, full=True)
+    assert r.status == "KW_OK"
+    xg = r.x.cpu().numpy().astype(np.complex128)
+    dist = dense.spectrum_distance(Hs.toarray(), q.z)
+    err = np.linalg.norm(xg - orc.x, axis=1)
+    assert np.all(err <= 5e-5 * np.linalg.norm(orc.x, axis=1) + 2 * q.tol / dist)
