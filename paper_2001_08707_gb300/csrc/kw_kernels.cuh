@@ -1728,8 +1728,9 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
   if (!st->xp_pending[parity]) return;
   const int nl = st->n_list[parity];
   const int ntile = (nl + TS - 1) / TS;
-  // pairs (FP32 storage, m even): each thread takes two adjacent elements with
-  // one 16-byte load and store per row of x and p (rows start 16-byte aligned)
+  // pairs (complex FP32 x and p, m even): each thread takes two adjacent
+  // elements with one 16-byte load and store per row of x and p (rows start
+  // 16-byte aligned)
   const int span = pairs ? 2 * (int)blockDim.x : (int)blockDim.x;
   const int nchunk = (m + span - 1) / span;
   __shared__ V cs[TS][3];
@@ -1746,7 +1747,7 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
       for (int j = 0; j < 3; ++j) cs[threadIdx.x][j] = vscalar<V>(coef[3 * k + j], coef_pair[3 * k + j]);
     }
     __syncthreads();
-    if constexpr (XP32) {
+    if constexpr (std::is_same<V, float2>::value) {
       if (pairs) {
         const int i = chunk * span + 2 * (int)threadIdx.x;
         if (i < m) {   // m even: i + 1 < m as well
@@ -2545,9 +2546,9 @@ static cudaError_t update_xp_launch(Work& w, const void* r1, State* st, int pari
   typedef typename XT<P, XP32>::V XV;
   typedef typename PT<P>::V V;
   static int nblk_per_sm = 0;
-  // two FP32 elements per thread (workloads 3 and 4: K4 1-5% faster): rows of x and p must start 16-byte
-  // aligned, so m even and both bases 16-byte aligned (x may be the caller's memory)
-  const int pairs = XP32 && w.m % 2 == 0 && (reinterpret_cast<uintptr_t>(w.X) & 15) == 0 &&
+  // two complex FP32 elements per thread (FP32 storage, or the FP32 form): rows of x and p must start
+  // 16-byte aligned, so m even and both bases 16-byte aligned (x may be the caller's memory)
+  const int pairs = std::is_same<XV, float2>::value && w.m % 2 == 0 && (reinterpret_cast<uintptr_t>(w.X) & 15) == 0 &&
                     (reinterpret_cast<uintptr_t>(w.P) & 15) == 0;
   const long long span = pairs ? 512 : 256;
   const long long items = (long long)((w.K + TS - 1) / TS) * ((w.m + span - 1) / span);
