@@ -1728,11 +1728,14 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
   if (!st->xp_pending[parity]) return;
   const int nl = st->n_list[parity];
   const int ntile = (nl + TS - 1) / TS;
-  // pairs (complex FP32 x and p, m even): each thread takes two adjacent
-  // elements with one 16-byte load and store per row of x and p (rows start
-  // 16-byte aligned)
-  const int span = pairs ? 2 * (int)blockDim.x : (int)blockDim.x;
-  const int nchunk = (m + span - 1) / span;
+  // pairs (complex FP32 x and p, both 16-byte aligned): thread t of a chunk
+  // takes pair t, elements 2t - o and 2t - o + 1 of a row whose offset k m has
+  // parity o, so that the pair starts 16-byte aligned, with one 16-byte load
+  // and store per row of x and p; an element whose partner falls outside the
+  // row (element 0 of an odd row, element m - 1 of an even row when m is odd)
+  // is taken alone.  Pair indices 0 .. m/2 cover every element of both parities.
+  const int nunit = pairs ? m / 2 + 1 : m;
+  const int nchunk = (nunit + (int)blockDim.x - 1) / (int)blockDim.x;
   __shared__ V cs[TS][3];
   __shared__ int ks[TS];
   const long long nitem = (long long)ntile * nchunk;
@@ -1749,21 +1752,42 @@ k_update_xp(int m, const int* __restrict__ list, const double2* __restrict__ coe
     __syncthreads();
     if constexpr (std::is_same<V, float2>::value) {
       if (pairs) {
-        const int i = chunk * span + 2 * (int)threadIdx.x;
-        if (i < m) {   // m even: i + 1 < m as well
-          const V ra = to_x(r1[i], (V*)nullptr), rb = to_x(r1[i + 1], (V*)nullptr);
+        const int e = 2 * (chunk * (int)blockDim.x + (int)threadIdx.x);   // first element of pair t when o = 0
+        if (e <= m) {
+          // r_{n+1} at e - 1, e, e + 1 (inside the row): the pair's elements for either parity
+          const V rm1 = e >= 1 ? to_x(r1[e - 1], (V*)nullptr) : V{};
+          const V r0 = e < m ? to_x(r1[e], (V*)nullptr) : V{};
+          const V rp1 = e + 1 < m ? to_x(r1[e + 1], (V*)nullptr) : V{};
 #pragma unroll TS
           for (int s = 0; s < nts; ++s) {
-            const size_t o = (size_t)ks[s] * m + i;
-            float4 xx = *reinterpret_cast<const float4*>(X + o), pp = *reinterpret_cast<const float4*>(Pv + o);
-            V xa = make_float2(xx.x, xx.y), xb = make_float2(xx.z, xx.w);
-            V pa = make_float2(pp.x, pp.y), pb = make_float2(pp.z, pp.w);
-            xa = cadd(xa, cmul(cs[s][0], pa));                   // Eq. 23
-            xb = cadd(xb, cmul(cs[s][0], pb));
-            pa = cadd(cmul(ra, cs[s][2]), cmul(cs[s][1], pa));   // Eq. 24
-            pb = cadd(cmul(rb, cs[s][2]), cmul(cs[s][1], pb));
-            *reinterpret_cast<float4*>(X + o) = make_float4(xa.x, xa.y, xb.x, xb.y);
-            *reinterpret_cast<float4*>(Pv + o) = make_float4(pa.x, pa.y, pb.x, pb.y);
+            const size_t base = (size_t)ks[s] * m;
+            const int par = (int)(base & 1);
+            const int e0 = e - par;                          // base + e0 is even
+            const V ra = par ? rm1 : r0, rb = par ? r0 : rp1;
+            if (e0 >= 0 && e0 + 1 < m) {
+              const size_t o = base + e0;
+              float4 xx = *reinterpret_cast<const float4*>(X + o), pp = *reinterpret_cast<const float4*>(Pv + o);
+              V xa = make_float2(xx.x, xx.y), xb = make_float2(xx.z, xx.w);
+              V pa = make_float2(pp.x, pp.y), pb = make_float2(pp.z, pp.w);
+              xa = cadd(xa, cmul(cs[s][0], pa));                   // Eq. 23
+              xb = cadd(xb, cmul(cs[s][0], pb));
+              pa = cadd(cmul(ra, cs[s][2]), cmul(cs[s][1], pa));   // Eq. 24
+              pb = cadd(cmul(rb, cs[s][2]), cmul(cs[s][1], pb));
+              *reinterpret_cast<float4*>(X + o) = make_float4(xa.x, xa.y, xb.x, xb.y);
+              *reinterpret_cast<float4*>(Pv + o) = make_float4(pa.x, pa.y, pb.x, pb.y);
+            } else {
+              // the element of this pair that lies in the row (if any) alone
+              const int i = e0 < 0 ? e0 + 1 : e0;
+              if (i >= 0 && i < m) {
+                const V ri = e0 < 0 ? rb : ra;
+                const size_t o = base + i;
+                V x = X[o], p = Pv[o];
+                x = cadd(x, cmul(cs[s][0], p));
+                p = cadd(cmul(ri, cs[s][2]), cmul(cs[s][1], p));
+                X[o] = x;
+                Pv[o] = p;
+              }
+            }
           }
         }
         continue;
@@ -2546,12 +2570,12 @@ static cudaError_t update_xp_launch(Work& w, const void* r1, State* st, int pari
   typedef typename XT<P, XP32>::V XV;
   typedef typename PT<P>::V V;
   static int nblk_per_sm = 0;
-  // two complex FP32 elements per thread (FP32 storage, or the FP32 form): rows of x and p must start
-  // 16-byte aligned, so m even and both bases 16-byte aligned (x may be the caller's memory)
-  const int pairs = std::is_same<XV, float2>::value && w.m % 2 == 0 && (reinterpret_cast<uintptr_t>(w.X) & 15) == 0 &&
+  // two complex FP32 elements per thread (FP32 storage, or the FP32 form) when both bases are 16-byte
+  // aligned (x may be the caller's memory)
+  const int pairs = std::is_same<XV, float2>::value && (reinterpret_cast<uintptr_t>(w.X) & 15) == 0 &&
                     (reinterpret_cast<uintptr_t>(w.P) & 15) == 0;
-  const long long span = pairs ? 512 : 256;
-  const long long items = (long long)((w.K + TS - 1) / TS) * ((w.m + span - 1) / span);
+  const long long nunit = pairs ? w.m / 2 + 1 : w.m;
+  const long long items = (long long)((w.K + TS - 1) / TS) * ((nunit + 255) / 256);
   const int nblk = (int)std::max<long long>(
       1, std::min<long long>(resident_blocks(nblk_per_sm, k_update_xp<P, TS, XP32>, 256, w.num_sms), items));
   const size_t c0 = (size_t)parity * 3 * w.K;

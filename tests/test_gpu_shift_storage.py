@@ -127,15 +127,17 @@ def test_host_path_and_edges(prec):
 
 
 @pytest.mark.parametrize("prec", ["f64", "df64", "c32"])
-def test_paired_and_single_element_updates_agree(prec):
+@pytest.mark.parametrize("L", [8, 7])
+def test_paired_and_single_element_updates_agree(prec, L):
     """With complex FP32 x and p (FP32 storage, or the FP32 form) the x/p
-    update takes two adjacent elements per thread (16-byte accesses) when m is
-    even and x starts 16-byte aligned, one element otherwise.  The arithmetic
-    per element is the same, so an x at an 8-byte offset (single elements)
-    gives the same bits as an aligned one (pairs); an odd m (single elements)
-    meets the oracle's bound (FP64-class seed forms)."""
+    update takes two adjacent elements per thread (16-byte accesses, each row's
+    pairs aligned by the parity of its offset k m) when x starts 16-byte
+    aligned, one element otherwise.  The arithmetic per element is the same, so
+    an x at an 8-byte offset (single elements) gives the same bits as an
+    aligned one (pairs), for even m (512) and odd m (343, where the rows
+    alternate parity); the FP64-class seed forms also meet the oracle's bound."""
     tol = 1e-6 if prec == "c32" else 1e-9
-    p = w.anderson_small(L=8, K=20, delta=0.1, tol=tol)           # m = 512
+    p = w.anderson_small(L=L, K=20, delta=0.1, tol=tol)
     s = _solver(p.H, prec, True, tol=p.tol)
     a = s.solve(p.b, p.z, full=True)
     buf = torch.zeros(p.z.size * p.H.m + 1, dtype=torch.complex64, device="cuda")
@@ -146,12 +148,10 @@ def test_paired_and_single_element_updates_agree(prec):
     assert torch.equal(xv, a.x)
     if prec == "c32":
         return
-    q = w.anderson_small(L=7, K=16, delta=0.1, tol=1e-9)          # m = 343
-    Hs = q.H.to_scipy()
-    orc = oc.shifted_cocg(Hs, q.b, q.z, tol=q.tol, full=True)
-    r = _solver(q.H, prec, True, tol=q.tol).solve(q.b, q.z, full=True)
-    assert r.status == "KW_OK"
-    xg = r.x.cpu().numpy().astype(np.complex128)
-    dist = dense.spectrum_distance(Hs.toarray(), q.z)
+    Hs = p.H.to_scipy()
+    orc = oc.shifted_cocg(Hs, p.b, p.z, tol=p.tol, full=True)
+    assert a.status == "KW_OK"
+    xg = a.x.cpu().numpy().astype(np.complex128)
+    dist = dense.spectrum_distance(Hs.toarray(), p.z)
     err = np.linalg.norm(xg - orc.x, axis=1)
-    assert np.all(err <= 5e-5 * np.linalg.norm(orc.x, axis=1) + 2 * q.tol / dist)
+    assert np.all(err <= 5e-5 * np.linalg.norm(orc.x, axis=1) + 2 * p.tol / dist)
