@@ -33,6 +33,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <utility>
 #include <type_traits>
 
 #include "kw_arith.cuh"
@@ -169,6 +170,19 @@ __device__ __forceinline__ void set_fail(State* st, int status) {
   st->done = 1;
 }
 
+// Programmatic dependent launch for small problems: K1 and K2 follow each
+// other on the work stream; when their grids are small (less than one block
+// per SM, where the iteration is bound by launch latency) they are launched
+// with programmatic stream serialization, so that the next one's blocks are
+// placed while this one's last blocks still reduce.  Each waits at entry for
+// its predecessor's completion and memory before touching anything, then lets
+// its own successor launch; both instructions are no-ops for an ordinary
+// launch.  (On large grids the early blocks cost more than they save.)
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ================================================================ K1: SpMV + first dot
 struct SpmvMode {
   int solver;        // 1: inside the solve (reads z_s, computes alpha)
@@ -238,6 +252,7 @@ k_spmv_dot(int m, const int64_t* __restrict__ rowptr, const int* __restrict__ co
            typename PT<P>::V* __restrict__ q, State* st, double* __restrict__ part, SpmvMode mode) {
   typedef typename PT<P>::V V;
   typedef typename PT<P>::A A;
+  pdl_entry();
   V zsv;
   if (mode.solver) {
     if (st->done) return;
@@ -994,6 +1009,7 @@ k_seed_update(int m, const typename PT<P>::V* __restrict__ rn_buf, const typenam
   typedef typename PT<P>::A A;
   constexpr int N = 3 + 2 * NP;
   constexpr bool CHUNKED = PT<P>::CHUNK < (1 << 30);
+  pdl_entry();
   if (st->done) return;
   __shared__ double2 s_sc[2];   // c_n, 1/rho_n
   __shared__ double2 s_cf[3];   // the three coefficients in FP64
@@ -2174,6 +2190,23 @@ static __global__ void k_f64_to_pair(const double* __restrict__ in, df* __restri
 // Blocks that fit on the device at once for a kernel with the given block size.
 // per_sm caches the occupancy of the kernel (a property of the kernel and the
 // architecture); the SM count is the current context's.
+// Launch of K1 or K2 on the work stream, with programmatic stream
+// serialization when the grid is below one block per SM (see pdl_entry).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k12(void (*kernel)(KArgs...), int grid, int num_sms, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = grid < num_sms ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <class F>
 static int resident_blocks(int& per_sm, F kernel, int threads, int num_sms) {
   if (per_sm == 0) {
@@ -2191,9 +2224,8 @@ static cudaError_t spmv_launch(Work& w, const void* r, void* q, SpmvMode mode) {
   const int nblk = resident_blocks(nblk_per_sm, k_spmv_dot<P, RV, G>, 256, w.num_sms);
   const int need = (int)((w.m * G + 255) / 256);   // no more blocks than rows need
   const int grid = std::max(1, std::min(nblk, need));
-  k_spmv_dot<P, RV, G><<<grid, 256, 0, w.stream>>>((int)w.m, w.rowptr, w.col, (const RV*)w.val,
-                                                   (const V*)r, (V*)q, w.st, w.part_k1, mode);
-  return cudaGetLastError();
+  return launch_k12(k_spmv_dot<P, RV, G>, grid, w.num_sms, w.stream, (int)w.m, w.rowptr, w.col, (const RV*)w.val,
+                    (const V*)r, (V*)q, w.st, w.part_k1, mode);
 }
 
 template <int P, class RV>
@@ -2499,10 +2531,9 @@ static cudaError_t seed_launch(Work& w, void* rn, void* rm, int parity) {
   static int nblk_per_sm = 0;
   const int nblk = resident_blocks(nblk_per_sm, k_seed_update<P, NP, METHOD, false>, 256, w.num_sms);
   const int grid = std::max(1, std::min(nblk, ntiles));
-  k_seed_update<P, NP, METHOD, false><<<grid, 256, 0, w.stream>>>(
-      (int)w.m, (const V*)rn, (const V*)w.q, (V*)rm, (const R*)w.proj_rows, w.proj_ld, w.nproj, parity, w.st,
-      w.part, w.w, (const V*)rtn, (const V*)w.qt, (V*)rtm, 1, 0u);
-  return cudaGetLastError();
+  return launch_k12(k_seed_update<P, NP, METHOD, false>, grid, w.num_sms, w.stream, (int)w.m, (const V*)rn,
+                    (const V*)w.q, (V*)rm, (const R*)w.proj_rows, w.proj_ld, w.nproj, parity, w.st, w.part, w.w,
+                    (const V*)rtn, (const V*)w.qt, (V*)rtm, 1, 0u);
 }
 
 template <int P, int METHOD>
