@@ -132,7 +132,7 @@ def spmv_bytes(m, nnz, vec_bytes, val_bytes):
     return nnz * (4 + val_bytes) + 8 * (m + 1) + 2 * vec_bytes * m
 
 
-def survey_spmv_bytes(m, nnz, vec_bytes, val_bytes):
+def csr_spmv_bytes(m, nnz, vec_bytes, val_bytes):
     """Algorithmic bytes of one seed SpMV by the accounting fixed for this path:
     the CSR as given (int32 column and val_bytes value per non-zero, 4-byte row
     offsets), r read once and q written once."""
@@ -568,14 +568,14 @@ def measure_configs(args, kw, wl, device, stream, ws, peak, peak_kind, h_res, t_
         ti = max(st_["timed_iters"], 1)
         k = [x / ti for x in st_["kernel_ms"]]
         vb, rb = PREC_BYTES[prec]
-        k1b = survey_spmv_bytes(pa.H.m, pa.H.nnz, vb, 4 if prec == "c32" else 8)
+        k1b = csr_spmv_bytes(pa.H.m, pa.H.nnz, vb, 4 if prec == "c32" else 8)
         k2b = seed_bytes(pa.H.m, vb, rb, pa.left.shape[0] + 1)
         if prec == "df64":
             c5["df64_seed_update_traffic"] = recorded_traffic("k_seed_update_rg<df64>:anderson_L160")
         c5[f"{prec}_iteration_sample"] = {
             "iterations": ra.iters, "us_per_iteration": 1e3 * ta / ra.iters,
             "updates_per_s_at_full_activity": ws * ra.updates * pa.H.m / (ta * 1e-3),
-            "spmv_us": 1e3 * k[0], "spmv_survey_bytes": k1b, "spmv_frac": k1b / (k[0] * 1e-3) / 1e9 / peak,
+            "spmv_us": 1e3 * k[0], "spmv_csr_bytes": k1b, "spmv_frac": k1b / (k[0] * 1e-3) / 1e9 / peak,
             "seed_update_us": 1e3 * k[1], "seed_update_bytes": k2b,
             "seed_update_frac": k2b / (k[1] * 1e-3) / 1e9 / peak, "shift_us": 1e3 * k[2], "spmv_config": cfg}
     c5["peak_kind"] = hbm
@@ -899,7 +899,7 @@ def run_ours(args):
     k1_layout = "uniform off-diagonal layout" if h_cfg[0] > UNIFORM_LANES else "CSR"
     # achieved = the CSR-as-given bytes of one product (FP32 values: the chain's +-1/4, 1/2 are exact)
     # over the average launch time; the layout's own bytes and the measured DRAM traffic beside it
-    sv_bytes = survey_spmv_bytes(m, nnz, PREC_BYTES[HEADLINE][0], 4)
+    sv_bytes = csr_spmv_bytes(m, nnz, PREC_BYTES[HEADLINE][0], 4)
     sv_gbs = sv_bytes / (kh["spmv_us"] * 1e-6) / 1e9
     traffic = recorded_traffic(f"{k1}<{HEADLINE}>:heisenberg_N24")
     roofline = {"kernel": f"{k1} (seed SpMV + r^T q, {k1_layout}), {HEADLINE}", "bound": "hbm",
