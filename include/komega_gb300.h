@@ -470,12 +470,14 @@ kw_status kw_set_method(kw_ctx* ctx, int method, const double* btilde_dev);
 kw_status kw_set_matvec_adjoint(kw_ctx* ctx, kw_matvec_fn fn, void* user);
 
 /* Schedule of an iteration (the steps of Sec. 2.2: Eq. 16-17, then Eq. 20-26).
- * on = 1 (the default): the shift scalars of
- * iteration n (and the full-mode x/p update) run on a second stream while the
- * product of iteration n+1 runs, since neither needs the other's results (a
- * seed switch reaches that product through the next three-term update, by
- * linearity); on = 0: one stream, in the order K2(n), K1(n+1), K3(n), K4(n).
- * Both give the same numbers.  Errors: KW_ERR_ARG. */
+ * on = 1 (the default): the shift scalars of iteration n run on a second stream
+ * while the product of iteration n+1 runs, since neither needs the other's
+ * results (a seed switch reaches that product through the next three-term
+ * update, by linearity), and the full-mode x/p update of iteration n runs on a
+ * third stream beside the next three-term update (its coefficients and shift
+ * list sit in slots of the iteration's parity); on = 0: one stream, in the
+ * order K2(n), K1(n+1), K3(n), K4(n).  Both give the same numbers.  Errors:
+ * KW_ERR_ARG. */
 kw_status kw_set_stream_overlap(kw_ctx* ctx, int on);
 
 /* Loads of the three-term update (Eq. 16) in the FP32 and FP32-pair forms.
