@@ -576,7 +576,8 @@ class Solver:
 
     def set_stream_overlap(self, on: bool):
         """kw_set_stream_overlap: run the shift scalars of iteration n beside the
-        product of iteration n+1 (True, the default) or on one stream."""
+        product of iteration n+1 and the x/p update of iteration n beside the next
+        three-term update (True, the default: three streams), or all on one stream."""
         st = self._lib.kw_set_stream_overlap(self._ctx, 1 if on else 0)
         if st != KW_OK:
             raise self._err(st, "kw_set_stream_overlap")
